@@ -1,0 +1,216 @@
+/*
+ * tt_rbki.h - C ABI of the GB300 (sm_103a) randomized block Krylov
+ * tensor-train library.
+ *
+ * The library computes the TT approximation of Alg. 3 (TT-rBKI) of
+ * "A Randomized Block Krylov Method for Tensor Train Approximation"
+ * (Yu, Feng, Chen, Cai, Qi): for each mode k = 1..d-1 it unfolds the
+ * remainder to C = reshape(R, [r_{k-1} I_k, I_{k+1}...I_d]) (Alg. 3 step 2),
+ * builds an orthonormal basis Q of the block Krylov space
+ * [C W, (C C^T) C W, ..., (C C^T)^q C W] with a Gaussian W of r_k + p
+ * columns (Alg. 3 steps 3-5, left-side reading), takes the top-r_k left
+ * singular vectors of Q^T C by Rayleigh-Ritz (Alg. 3 steps 6-8), stores
+ * them as core k (step 9) and carries U^T C forward (step 10).  The last
+ * remainder is core d (step 12).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Tensors are dense, row-major, i_1 slowest (the unfolding at mode k is a
+ *    free view).  Cores are row-major [r_{k-1}][I_k][r_k] float32.
+ *  - Pointers documented as "device" must be device-accessible CUDA memory
+ *    of the current device; "host" pointers are ordinary host memory.
+ *  - The caller owns every buffer: the input tensor, the cores, the
+ *    workspace.  No entry point allocates device memory, and none keeps a
+ *    pointer after it returns.
+ *  - All device work is enqueued on `stream` (a cudaStream_t passed as
+ *    void*, NULL = legacy default stream).  Entry points do not synchronise
+ *    the stream; results are ready once the stream has reached that point.
+ *    A call enqueues a fixed sequence of kernels with no host round trip,
+ *    so it may be captured into a CUDA graph.
+ *  - Errors are returned as tt_status.  Argument errors are detected on the
+ *    host before anything is enqueued.  Numerical conditions found on the
+ *    device (non-finite input) are written to a status word inside the
+ *    workspace and read with tt_rbki_device_status().  Device code never
+ *    traps.  tt_rbki_last_error() returns a message for the last failing
+ *    call of the calling thread.
+ *  - Ranks larger than feasible are clamped, not rejected:
+ *    r_k' = min(r_k, r_{k-1}' I_k, I_{k+1}...I_d), r_0' = r_d' = 1.
+ */
+#ifndef TT_RBKI_H
+#define TT_RBKI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define TT_API __attribute__((visibility("default")))
+#else
+#define TT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TT_OK = 0,
+  TT_EINVAL = 1,        /* bad argument (shape, rank, pointer, size)          */
+  TT_ENOMEM = 2,        /* workspace smaller than tt_rbki_workspace_size()   */
+  TT_ECUDA = 3,         /* a CUDA runtime call failed                         */
+  TT_EBREAKDOWN = 4,    /* (device status) a basis block could not be made
+                           orthonormal even after random replacement         */
+  TT_ENONFINITE = 5,    /* (device status) NaN or Inf found in the input      */
+  TT_EUNSUPPORTED = 6   /* shape outside the supported envelope               */
+} tt_status;
+
+typedef enum {
+  TT_F32 = 0,           /* IEEE binary32                                      */
+  TT_BF16 = 1           /* bfloat16, round-to-nearest-even from binary32      */
+} tt_dtype;
+
+/* Options; a NULL pointer means all defaults (the zero-initialised struct
+ * is NOT the default: use tt_rbki_default_options). */
+typedef struct {
+  int32_t storage;      /* tt_dtype of the input tensor and of the streamed
+                           unfoldings.  TT_F32: FP32 storage, FP32 arithmetic
+                           (the plain FP32 form).  TT_BF16: BF16 storage with
+                           BF16 tensor-core products accumulated in FP32 (the
+                           precision form).  Default TT_F32.                  */
+  int32_t remainder;    /* tt_dtype of the remainders R_1..R_{d-1};
+                           default = storage.                                 */
+  int32_t exhaust_gram; /* 1 (default): when the Krylov basis of a mode would
+                           reach all m = r_{k-1} I_k rows (exhaustion), form
+                           the m x m Gram C C^T in one pass instead of the
+                           sketch + Krylov passes; the result is the same
+                           exact truncated SVD.  0: always run the Krylov
+                           passes with the dimension cap.                     */
+  int32_t reserved[5];  /* must be zero                                       */
+} tt_options;
+
+/* Fills *opts with the defaults described above. */
+TT_API tt_status tt_rbki_default_options(tt_options* opts);
+
+/*
+ * Rank clamp and core sizes (Def. 2; Alg. 3 input).
+ *   dims       host, d mode sizes I_1..I_d, each >= 1; d >= 2.
+ *   ranks      host, d-1 target ranks r_1..r_{d-1}, each >= 1.
+ *   ranks_out  host, d+1 entries: r_0' = 1, r_1'..r_{d-1}', r_d' = 1.
+ *   core_elems host, d entries: r_{k-1}' I_k r_k' (may be NULL).
+ * Errors: TT_EINVAL on d < 2, a dimension or rank < 1, or overflow.
+ */
+TT_API tt_status tt_rbki_core_sizes(const int64_t* dims, int d, const int64_t* ranks,
+                             int64_t* ranks_out, int64_t* core_elems);
+
+/*
+ * Workspace bytes needed by tt_rbki_decompose / _omega for this problem.
+ * oversample = p >= 0, q >= 0 (Alg. 3 input).  opts may be NULL.
+ */
+TT_API tt_status tt_rbki_workspace_size(const int64_t* dims, int d, const int64_t* ranks,
+                                 int oversample, int q, const tt_options* opts,
+                                 size_t* bytes);
+
+/*
+ * TT-rBKI decomposition (Alg. 3) with Omega drawn on the device.
+ *   tensor     device, prod(dims) elements of opts->storage, row-major.
+ *   omega_seed 64-bit seed.  Omega_k (n_k x (r_k' + p), n_k = I_{k+1}..I_d)
+ *              has entry (i, c) = the (c mod 4)-th output of the Box-Muller
+ *              transform applied to Philox4x32-10 (Salmon et al., SC'11) with
+ *              counter (i mod 2^32, i >> 32, c / 4, k) and key
+ *              (seed mod 2^32, seed >> 32); outputs (x0,x1) and (x2,x3) give
+ *              the cosine/sine pairs with uniforms ((x >> 9) + 1/2) 2^-23.
+ *              Evaluated in binary32 on the device.
+ *   cores_out  host array of d device pointers; core k receives
+ *              r_{k-1}' I_k r_k' float32 values [r_{k-1}'][I_k][r_k'].
+ *   ranks_out  host, d+1 entries (as tt_rbki_core_sizes); may be NULL.
+ *   workspace  device, ws_bytes >= tt_rbki_workspace_size(); 256-byte
+ *              aligned.  Holds intermediates and the device status word.
+ *   stream     cudaStream_t.
+ * Errors: TT_EINVAL, TT_ENOMEM (workspace too small), TT_EUNSUPPORTED,
+ *         TT_ECUDA (launch failure).  Device-side conditions: see
+ *         tt_rbki_device_status.
+ */
+TT_API tt_status tt_rbki_decompose(const void* tensor, const int64_t* dims, int d,
+                            const int64_t* ranks, int oversample, int q,
+                            uint64_t omega_seed, float* const* cores_out,
+                            int64_t* ranks_out, void* workspace, size_t ws_bytes,
+                            void* stream, const tt_options* opts);
+
+/*
+ * As tt_rbki_decompose, with explicit Gaussian test matrices (Alg. 3 step 3):
+ *   omegas     host array of d-1 device pointers; omegas[k] holds
+ *              n_k x (r_k' + p) float32 values, row-major.
+ * Used to give the GPU and a reference implementation identical Omega.
+ */
+TT_API tt_status tt_rbki_decompose_omega(const void* tensor, const int64_t* dims, int d,
+                                  const int64_t* ranks, int oversample, int q,
+                                  const float* const* omegas, float* const* cores_out,
+                                  int64_t* ranks_out, void* workspace, size_t ws_bytes,
+                                  void* stream, const tt_options* opts);
+
+/*
+ * Reads the device status word of the last decomposition that used
+ * `workspace` (synchronises `stream`).  *device_status receives TT_OK,
+ * TT_ENONFINITE or TT_EBREAKDOWN.
+ */
+TT_API tt_status tt_rbki_device_status(const void* workspace, void* stream, int* device_status);
+
+/* Message describing the last error returned on the calling thread. */
+TT_API const char* tt_rbki_last_error(void);
+
+/* ------------------------------------------------------------------------
+ * Step-level entry points.  Each runs one kernel family of the path on
+ * caller-owned device buffers; tests use them to check kernels one by one.
+ * ---------------------------------------------------------------------- */
+
+/*
+ * Canonicalise a strided tensor into a dense row-major one, optionally
+ * permuting modes and converting FP32 -> BF16 (round-to-nearest-even).
+ * The free unfolding of Alg. 3 step 2 and Def. 1 needs i_1 slowest; the
+ * paper permutes the modes of its colour video before decomposing (Sec. 4.1).
+ *   src        device, elements of src_dtype at offsets sum_j i_j src_strides[j]
+ *              (strides in elements, >= 0), for the SOURCE mode order.
+ *   dims       host, d source mode sizes.
+ *   perm       host, d entries: destination mode j is source mode perm[j]
+ *              (NULL = identity).
+ *   dst        device, prod(dims) elements of dst_dtype, dense row-major in
+ *              the destination order.  Must not overlap src.
+ * Conversions: F32->F32, F32->BF16, BF16->BF16, BF16->F32.  d <= 8.
+ */
+TT_API tt_status tt_permute_convert(const void* src, int src_dtype, const int64_t* dims,
+                             const int64_t* src_strides, const int* perm, int d,
+                             void* dst, int dst_dtype, void* stream);
+
+/*
+ * Gaussian test matrix of mode k from a seed (Alg. 3 step 3), with the
+ * Philox4x32-10 / Box-Muller definition given at tt_rbki_decompose.
+ *   out        device, n x b values of out_dtype (TT_F32 or TT_BF16),
+ *              row-major with row stride ld >= b.
+ */
+TT_API tt_status tt_omega_generate(uint64_t seed, int mode, int64_t n, int b, void* out,
+                            int out_dtype, int64_t ld, void* stream);
+
+/*
+ * One streaming pass over an unfolding C (m x n, row-major, dtype c_dtype).
+ *   op = TT_PASS_SKETCH   : Y = C W          W = x: n x b FP32 (device)
+ *   op = TT_PASS_GRAMAPPLY: Y = C (C^T X)    X = x: m x b FP32 (device)
+ *   op = TT_PASS_PROJECT  : Y = X^T C        X = x: m x b FP32; Y is b x n,
+ *                                            written in y_dtype (F32/BF16)
+ *   op = TT_PASS_GRAM     : Y = C C^T        x unused; Y is m x m
+ * For SKETCH/GRAMAPPLY/GRAM, y is m x b (m x m) FP32.  The pass needs the
+ * workspace size returned by tt_pass_workspace_size for the same arguments.
+ * These are Alg. 3 steps 4 (sketch and Krylov powers), 10 (projection) and
+ * the Gram route taken at exhaustion.
+ */
+enum { TT_PASS_SKETCH = 0, TT_PASS_GRAMAPPLY = 1, TT_PASS_PROJECT = 2, TT_PASS_GRAM = 3 };
+
+TT_API tt_status tt_pass_workspace_size(int op, int64_t m, int64_t n, int b, int c_dtype,
+                                 size_t* bytes);
+TT_API tt_status tt_pass(int op, const void* C, int c_dtype, int64_t m, int64_t n, int b,
+                  const float* x, void* y, int y_dtype, void* workspace, size_t ws_bytes,
+                  void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TT_RBKI_H */

@@ -1,0 +1,96 @@
+"""ctypes declarations of the C ABI in include/tt_rbki.h.
+
+Loading fails loudly when the library has not been built: there is no CPU
+fallback.  Build it with ``python -m paper_2308_01480_gb300.build`` or
+``__graft_entry__.build()``.
+"""
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libtt_rbki.so")
+
+TT_OK, TT_EINVAL, TT_ENOMEM, TT_ECUDA, TT_EBREAKDOWN, TT_ENONFINITE, TT_EUNSUPPORTED = range(7)
+TT_F32, TT_BF16 = 0, 1
+TT_PASS_SKETCH, TT_PASS_GRAMAPPLY, TT_PASS_PROJECT, TT_PASS_GRAM = range(4)
+
+STATUS_NAMES = {0: "TT_OK", 1: "TT_EINVAL", 2: "TT_ENOMEM", 3: "TT_ECUDA", 4: "TT_EBREAKDOWN",
+                5: "TT_ENONFINITE", 6: "TT_EUNSUPPORTED"}
+
+
+class TTOptions(ctypes.Structure):
+    _fields_ = [("storage", ctypes.c_int32), ("remainder", ctypes.c_int32),
+                ("exhaust_gram", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+
+
+class TTError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+_lib = None
+
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_vp = ctypes.c_void_p
+_vpp = ctypes.POINTER(ctypes.c_void_p)
+
+_SIGNATURES = {
+    "tt_rbki_default_options": ([ctypes.POINTER(TTOptions)], ctypes.c_int),
+    "tt_rbki_core_sizes": ([_i64p, ctypes.c_int, _i64p, _i64p, _i64p], ctypes.c_int),
+    "tt_rbki_workspace_size": ([_i64p, ctypes.c_int, _i64p, ctypes.c_int, ctypes.c_int,
+                                ctypes.POINTER(TTOptions), ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "tt_rbki_decompose": ([_vp, _i64p, ctypes.c_int, _i64p, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                           _vpp, _i64p, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(TTOptions)], ctypes.c_int),
+    "tt_rbki_decompose_omega": ([_vp, _i64p, ctypes.c_int, _i64p, ctypes.c_int, ctypes.c_int, _vpp,
+                                 _vpp, _i64p, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(TTOptions)],
+                                ctypes.c_int),
+    "tt_rbki_device_status": ([_vp, _vp, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "tt_rbki_last_error": ([], ctypes.c_char_p),
+    "tt_permute_convert": ([_vp, ctypes.c_int, _i64p, _i64p, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                            _vp, ctypes.c_int, _vp], ctypes.c_int),
+    "tt_omega_generate": ([ctypes.c_uint64, ctypes.c_int, ctypes.c_int64, ctypes.c_int, _vp, ctypes.c_int,
+                           ctypes.c_int64, _vp], ctypes.c_int),
+    "tt_pass_workspace_size": ([ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "tt_pass": ([ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, _vp, _vp,
+                 ctypes.c_int, _vp, ctypes.c_size_t, _vp], ctypes.c_int),
+}
+
+
+def exported_names():
+    """Names the header declares (every one must be exported by the library)."""
+    return sorted(_SIGNATURES)
+
+
+def lib():
+    """The loaded library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"CUDA library not built: {LIB_PATH} is missing. Run "
+                "`python -m paper_2308_01480_gb300.build` (there is no CPU fallback).")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGNATURES.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def check(status):
+    if status != TT_OK:
+        msg = lib().tt_rbki_last_error()
+        raise TTError(status, msg.decode() if msg else "")
+    return status
+
+
+def i64_array(values):
+    arr = (ctypes.c_int64 * len(values))(*[int(v) for v in values])
+    return arr
+
+
+def ptr_array(ptrs):
+    return (ctypes.c_void_p * len(ptrs))(*[ctypes.c_void_p(int(p)) for p in ptrs])

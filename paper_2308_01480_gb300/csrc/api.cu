@@ -1,0 +1,446 @@
+// Host side of the C ABI: argument checks, the per-mode plan, the workspace
+// layout and the mode loop of Alg. 3.  Everything is enqueued on the
+// caller's stream without a host round trip.
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+tt_status fail(tt_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+#define TTR_CUDA(expr)                                                                  \
+  do {                                                                                  \
+    cudaError_t e_ = (expr);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(TT_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_));        \
+  } while (0)
+
+size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+size_t esize(int dt) { return dt == TT_BF16 ? 2 : 4; }
+
+struct ModePlan {
+  int64_t m = 0, n = 0, D = 0;
+  int r_in = 1, r_out = 1, b = 0, kq = 0;
+  std::vector<int> blocks;   // columns of X_0, X_1, ... (Krylov dimension cap applied)
+  bool gram_route = false;   // exhaustion with D == m: one Gram pass
+  bool fused_ga = false;     // Gram-apply fused in one pass over C
+};
+
+struct Plan {
+  int d = 0, p = 0, q = 0;
+  std::vector<int64_t> dims, rr;
+  tt_options o{};
+  int storage = TT_F32, remainder = TT_F32;
+  std::vector<ModePlan> modes;
+  // workspace offsets in bytes
+  size_t off_status = 0, off_R0 = 0, off_R1 = 0, off_S = 0, off_T = 0, off_part = 0, off_Y = 0,
+         off_Q = 0, off_W = 0, off_U = 0, off_G = 0, off_small = 0, total = 0;
+};
+
+tt_status resolve_options(const tt_options* in, tt_options* out) {
+  tt_rbki_default_options(out);
+  if (in) *out = *in;
+  if (out->storage != TT_F32 && out->storage != TT_BF16) return fail(TT_EINVAL, "options.storage must be TT_F32 or TT_BF16");
+  if (out->remainder < 0) out->remainder = out->storage;
+  if (out->remainder != TT_F32 && out->remainder != TT_BF16) return fail(TT_EINVAL, "options.remainder must be TT_F32 or TT_BF16");
+  for (int i = 0; i < 5; ++i)
+    if (out->reserved[i] != 0) return fail(TT_EINVAL, "options.reserved must be zero");
+  return TT_OK;
+}
+
+tt_status clamp(const int64_t* dims, int d, const int64_t* ranks, std::vector<int64_t>& rr) {
+  if (!dims || !ranks) return fail(TT_EINVAL, "dims and ranks must not be NULL");
+  if (d < 2 || d > 64) return fail(TT_EINVAL, "order d must be in [2, 64]");
+  for (int k = 0; k < d; ++k)
+    if (dims[k] < 1) return fail(TT_EINVAL, "mode sizes must be >= 1");
+  for (int k = 0; k < d - 1; ++k)
+    if (ranks[k] < 1) return fail(TT_EINVAL, "ranks must be >= 1");
+  int64_t total = 1;
+  for (int k = 0; k < d; ++k) {
+    if (total > (int64_t(1) << 46) / dims[k]) return fail(TT_EINVAL, "tensor too large");
+    total *= dims[k];
+  }
+  rr.assign(d + 1, 1);
+  int64_t n = total;
+  for (int k = 0; k < d - 1; ++k) {
+    n /= dims[k];
+    const int64_t m = rr[k] * dims[k];
+    rr[k + 1] = std::min(ranks[k], std::min(m, n));
+  }
+  rr[d] = 1;
+  return TT_OK;
+}
+
+tt_status build_plan(const int64_t* dims, int d, const int64_t* ranks, int p, int q, const tt_options* opts,
+                     Plan& P) {
+  tt_status s = resolve_options(opts, &P.o);
+  if (s != TT_OK) return s;
+  if (p < 0 || q < 0) return fail(TT_EINVAL, "oversample and q must be >= 0");
+  s = clamp(dims, d, ranks, P.rr);
+  if (s != TT_OK) return s;
+  P.d = d;
+  P.p = p;
+  P.q = q;
+  P.dims.assign(dims, dims + d);
+  P.storage = P.o.storage;
+  P.remainder = P.o.remainder;
+  P.modes.resize(d - 1);
+  int64_t total = 1;
+  for (int k = 0; k < d; ++k) total *= dims[k];
+  int64_t n = total;
+  size_t maxR = 0, maxS = 0, maxT = 0, maxPart = 0, maxY = 0, maxQ = 0, maxU = 0, maxG = 0, maxSmall = 0;
+  for (int k = 0; k < d - 1; ++k) {
+    ModePlan& M = P.modes[k];
+    n /= dims[k];
+    M.m = P.rr[k] * dims[k];
+    M.n = n;
+    M.r_in = (int)P.rr[k];
+    M.r_out = (int)P.rr[k + 1];
+    M.D = std::min(M.m, M.n);
+    const int64_t b64 = (int64_t)M.r_out + p;
+    if (b64 > 64) return fail(TT_EUNSUPPORTED, "r_k + p must be <= 64");
+    M.b = (int)b64;
+    int64_t cols = ttr::imin(M.b, M.D);
+    M.blocks.assign(1, (int)cols);
+    for (int j = 1; j <= q; ++j) {
+      if (cols >= M.D) break;
+      const int64_t c = ttr::imin(M.b, M.D - cols);
+      M.blocks.push_back((int)c);
+      cols += c;
+    }
+    M.kq = (int)cols;
+    M.gram_route = P.o.exhaust_gram && cols == M.D && M.D == M.m && M.m <= 128;
+    M.fused_ga = ttr::simt_ga_fused_ok(M.m, M.b);
+    if (!M.gram_route && M.kq > 256) return fail(TT_EUNSUPPORTED, "Krylov basis larger than 256 columns");
+    // sizes
+    maxR = std::max(maxR, (size_t)(M.r_out * M.n) * esize(P.remainder));
+    if (M.gram_route) {
+      maxPart = std::max(maxPart, (size_t)ttr::simt_gram_partials(M.m, M.n));
+      maxG = std::max(maxG, (size_t)(M.m * M.m));
+      maxSmall = std::max(maxSmall, ttr::rr_scratch_floats((int)M.m));
+    } else {
+      maxS = std::max(maxS, (size_t)(M.b * M.n));
+      maxPart = std::max(maxPart, (size_t)ttr::simt_cs_partials(M.m, M.n, M.b));
+      if (M.fused_ga)
+        maxPart = std::max(maxPart, (size_t)ttr::simt_ga_partials(M.m, M.n, M.b));
+      else
+        maxT = std::max(maxT, (size_t)(M.b * M.n));
+      maxY = std::max(maxY, (size_t)(M.m * M.b));
+      maxQ = std::max(maxQ, (size_t)(M.m * M.kq));
+      maxSmall = std::max(maxSmall, ttr::orth_scratch_floats(M.m, M.b, M.kq));
+      maxSmall = std::max(maxSmall, ttr::rr_scratch_floats(M.kq));
+    }
+    maxU = std::max(maxU, (size_t)(M.m * M.r_out));
+  }
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + std::max<size_t>(bytes, 1)); return o; };
+  P.off_status = take(256);
+  P.off_R0 = take(maxR);
+  P.off_R1 = take(maxR);
+  P.off_S = take(maxS * 4);
+  P.off_T = take(maxT * 4);
+  P.off_part = take(maxPart * 4);
+  P.off_Y = take(maxY * 4);
+  P.off_Q = take(maxQ * 4);
+  P.off_W = take(maxQ * 4);
+  P.off_U = take(maxU * 4);
+  P.off_G = take(maxG * 4);
+  P.off_small = take(maxSmall * 4);
+  P.total = off;
+  return TT_OK;
+}
+
+template <typename TIn>
+tt_status run_mode(const Plan& P, int k, const TIn* C, char* ws, const float* omega_explicit, uint64_t seed,
+                   float* core, cudaStream_t st) {
+  const ModePlan& M = P.modes[k];
+  float* part = (float*)(ws + P.off_part);
+  float* U = (float*)(ws + P.off_U);
+  float* small = (float*)(ws + P.off_small);
+  int* status = (int*)(ws + P.off_status);
+  const int r = M.r_out;
+  if (M.gram_route) {
+    float* G = (float*)(ws + P.off_G);
+    TTR_CUDA(ttr::simt_gram<TIn>(C, M.m, M.n, part, G, st));
+    TTR_CUDA(ttr::launch_rayleigh_ritz(nullptr, G, M.m, M.m, (int)M.m, r, 1, small, U, core, st));
+  } else {
+    float* S = (float*)(ws + P.off_S);
+    float* T = (float*)(ws + P.off_T);
+    float* Y = (float*)(ws + P.off_Y);
+    float* Q = (float*)(ws + P.off_Q);
+    float* W = (float*)(ws + P.off_W);
+    const int kq = M.kq;
+    // Alg. 3 step 3: Omega_k, stored transposed (b x n)
+    if (omega_explicit)
+      TTR_CUDA(ttr::launch_omega_transpose_any(omega_explicit, M.n, M.b, S, TT_F32, st));
+    else
+      TTR_CUDA(ttr::launch_omega(seed, k, M.n, M.b, S, TT_F32, 1, M.n, st));
+    // sketch Y = C Omega, first basis block
+    TTR_CUDA(ttr::simt_cs<TIn>(C, M.m, M.n, S, M.n, M.b, part, Y, M.b, st));
+    const uint64_t rseed = 0x5EEDull * (uint64_t)(k + 1);
+    TTR_CUDA(ttr::launch_orth_block(Y, M.b, M.m, M.b, Q, kq, 0, M.blocks[0], small, rseed, status, st));
+    int col = 0;
+    for (size_t j = 0; j < M.blocks.size(); ++j) {
+      const int cj = M.blocks[j];
+      const float* Xj = Q + col;
+      float* Wj = W + col;
+      // one Krylov power: W_j = C C^T X_j (also the Rayleigh-Ritz data)
+      if (M.fused_ga) {
+        TTR_CUDA(ttr::simt_ga<TIn>(C, M.m, M.n, Xj, kq, cj, part, Wj, kq, st));
+      } else {
+        TTR_CUDA((ttr::simt_proj<TIn, float>(C, M.m, M.n, Xj, kq, cj, T, M.n, st)));
+        TTR_CUDA(ttr::simt_cs<TIn>(C, M.m, M.n, T, M.n, cj, part, Wj, kq, st));
+      }
+      if (j + 1 < M.blocks.size())
+        TTR_CUDA(ttr::launch_orth_block(Wj, kq, M.m, cj, Q, kq, col + cj, M.blocks[j + 1], small,
+                                        rseed + 7919ull * (j + 1), status, st));
+      col += cj;
+    }
+    TTR_CUDA(ttr::launch_rayleigh_ritz(Q, W, kq, M.m, kq, r, 0, small, U, core, st));
+  }
+  // Alg. 3 step 10: next remainder R = U^T C (r x n)
+  char* Rout = ws + ((k % 2 == 0) ? P.off_R0 : P.off_R1);
+  if (P.remainder == TT_BF16)
+    TTR_CUDA((ttr::simt_proj<TIn, __nv_bfloat16>(C, M.m, M.n, U, r, r, (__nv_bfloat16*)Rout, M.n, st)));
+  else
+    TTR_CUDA((ttr::simt_proj<TIn, float>(C, M.m, M.n, U, r, r, (float*)Rout, M.n, st)));
+  return TT_OK;
+}
+
+tt_status decompose_impl(const void* tensor, const int64_t* dims, int d, const int64_t* ranks, int oversample,
+                         int q, const float* const* omegas, uint64_t seed, float* const* cores_out,
+                         int64_t* ranks_out, void* workspace, size_t ws_bytes, void* stream,
+                         const tt_options* opts) {
+  Plan P;
+  tt_status s = build_plan(dims, d, ranks, oversample, q, opts, P);
+  if (s != TT_OK) return s;
+  if (!tensor) return fail(TT_EINVAL, "tensor is NULL");
+  if (!cores_out) return fail(TT_EINVAL, "cores_out is NULL");
+  for (int k = 0; k < d; ++k)
+    if (!cores_out[k]) return fail(TT_EINVAL, "cores_out[k] is NULL");
+  if (!workspace) return fail(TT_EINVAL, "workspace is NULL");
+  if (((uintptr_t)workspace & 255) != 0) return fail(TT_EINVAL, "workspace must be 256-byte aligned");
+  if (ws_bytes < P.total) return fail(TT_ENOMEM, "workspace too small");
+  if (omegas)
+    for (int k = 0; k < d - 1; ++k)
+      if (!omegas[k] && !P.modes[k].gram_route) return fail(TT_EINVAL, "omegas[k] is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  char* ws = (char*)workspace;
+  int* status = (int*)(ws + P.off_status);
+  TTR_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
+  for (int k = 0; k < d - 1; ++k) {
+    const void* C;
+    int dt;
+    if (k == 0) {
+      C = tensor;
+      dt = P.storage;
+    } else {
+      C = ws + (((k - 1) % 2 == 0) ? P.off_R0 : P.off_R1);
+      dt = P.remainder;
+    }
+    const float* om = omegas ? omegas[k] : nullptr;
+    if (dt == TT_BF16)
+      s = run_mode<__nv_bfloat16>(P, k, (const __nv_bfloat16*)C, ws, om, seed, cores_out[k], st);
+    else
+      s = run_mode<float>(P, k, (const float*)C, ws, om, seed, cores_out[k], st);
+    if (s != TT_OK) return s;
+  }
+  // Alg. 3 step 12: last core = last remainder
+  const char* Rlast = ws + (((d - 2) % 2 == 0) ? P.off_R0 : P.off_R1);
+  const int64_t last = P.rr[d - 1] * P.dims[d - 1];
+  TTR_CUDA(ttr::launch_last_core(Rlast, P.remainder, last, cores_out[d - 1], status, st));
+  for (int k = 0; k < d; ++k)
+    TTR_CUDA(ttr::launch_check_finite(cores_out[k], P.rr[k] * P.dims[k] * P.rr[k + 1], status, st));
+  if (ranks_out)
+    for (int k = 0; k <= d; ++k) ranks_out[k] = P.rr[k];
+  return TT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tt_status tt_rbki_default_options(tt_options* o) {
+  if (!o) return fail(TT_EINVAL, "opts is NULL");
+  std::memset(o, 0, sizeof(*o));
+  o->storage = TT_F32;
+  o->remainder = -1;
+  o->exhaust_gram = 1;
+  return TT_OK;
+}
+
+tt_status tt_rbki_core_sizes(const int64_t* dims, int d, const int64_t* ranks, int64_t* ranks_out,
+                             int64_t* core_elems) {
+  std::vector<int64_t> rr;
+  tt_status s = clamp(dims, d, ranks, rr);
+  if (s != TT_OK) return s;
+  if (!ranks_out) return fail(TT_EINVAL, "ranks_out is NULL");
+  for (int k = 0; k <= d; ++k) ranks_out[k] = rr[k];
+  if (core_elems)
+    for (int k = 0; k < d; ++k) core_elems[k] = rr[k] * dims[k] * rr[k + 1];
+  return TT_OK;
+}
+
+tt_status tt_rbki_workspace_size(const int64_t* dims, int d, const int64_t* ranks, int oversample, int q,
+                                 const tt_options* opts, size_t* bytes) {
+  if (!bytes) return fail(TT_EINVAL, "bytes is NULL");
+  Plan P;
+  tt_status s = build_plan(dims, d, ranks, oversample, q, opts, P);
+  if (s != TT_OK) return s;
+  *bytes = P.total;
+  return TT_OK;
+}
+
+tt_status tt_rbki_decompose(const void* tensor, const int64_t* dims, int d, const int64_t* ranks, int oversample,
+                            int q, uint64_t omega_seed, float* const* cores_out, int64_t* ranks_out,
+                            void* workspace, size_t ws_bytes, void* stream, const tt_options* opts) {
+  return decompose_impl(tensor, dims, d, ranks, oversample, q, nullptr, omega_seed, cores_out, ranks_out,
+                        workspace, ws_bytes, stream, opts);
+}
+
+tt_status tt_rbki_decompose_omega(const void* tensor, const int64_t* dims, int d, const int64_t* ranks,
+                                  int oversample, int q, const float* const* omegas, float* const* cores_out,
+                                  int64_t* ranks_out, void* workspace, size_t ws_bytes, void* stream,
+                                  const tt_options* opts) {
+  if (!omegas) return fail(TT_EINVAL, "omegas is NULL");
+  return decompose_impl(tensor, dims, d, ranks, oversample, q, omegas, 0, cores_out, ranks_out, workspace,
+                        ws_bytes, stream, opts);
+}
+
+tt_status tt_rbki_device_status(const void* workspace, void* stream, int* device_status) {
+  if (!workspace || !device_status) return fail(TT_EINVAL, "NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  int h = 0;
+  TTR_CUDA(cudaMemcpyAsync(&h, workspace, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TTR_CUDA(cudaStreamSynchronize(st));
+  *device_status = h;
+  return TT_OK;
+}
+
+const char* tt_rbki_last_error(void) { return g_last_error.c_str(); }
+
+tt_status tt_permute_convert(const void* src, int src_dtype, const int64_t* dims, const int64_t* src_strides,
+                             const int* perm, int d, void* dst, int dst_dtype, void* stream) {
+  if (!src || !dst || !dims || !src_strides) return fail(TT_EINVAL, "NULL argument");
+  if (d < 1 || d > 8) return fail(TT_EINVAL, "d must be in [1, 8]");
+  if ((src_dtype != TT_F32 && src_dtype != TT_BF16) || (dst_dtype != TT_F32 && dst_dtype != TT_BF16))
+    return fail(TT_EINVAL, "dtype must be TT_F32 or TT_BF16");
+  bool seen[8] = {false};
+  for (int j = 0; j < d; ++j) {
+    if (dims[j] < 0 || src_strides[j] < 0) return fail(TT_EINVAL, "negative size or stride");
+    const int s = perm ? perm[j] : j;
+    if (s < 0 || s >= d || seen[s]) return fail(TT_EINVAL, "perm is not a permutation");
+    seen[s] = true;
+  }
+  TTR_CUDA(ttr::launch_permute(src, src_dtype, dst, dst_dtype, dims, src_strides, perm, d, (cudaStream_t)stream));
+  return TT_OK;
+}
+
+tt_status tt_omega_generate(uint64_t seed, int mode, int64_t n, int b, void* out, int out_dtype, int64_t ld,
+                            void* stream) {
+  if (!out) return fail(TT_EINVAL, "out is NULL");
+  if (n < 0 || b < 0 || ld < b || mode < 0) return fail(TT_EINVAL, "bad shape");
+  if (out_dtype != TT_F32 && out_dtype != TT_BF16) return fail(TT_EINVAL, "bad dtype");
+  if (n == 0 || b == 0) return TT_OK;
+  TTR_CUDA(ttr::launch_omega(seed, mode, n, b, out, out_dtype, ld, 1, (cudaStream_t)stream));
+  return TT_OK;
+}
+
+tt_status tt_pass_workspace_size(int op, int64_t m, int64_t n, int b, int c_dtype, size_t* bytes) {
+  if (!bytes) return fail(TT_EINVAL, "bytes is NULL");
+  if (m < 1 || n < 1) return fail(TT_EINVAL, "bad shape");
+  if (c_dtype != TT_F32 && c_dtype != TT_BF16) return fail(TT_EINVAL, "bad dtype");
+  size_t part = 0, sbuf = 0;
+  switch (op) {
+    case TT_PASS_SKETCH:
+      if (b < 1 || b > 64) return fail(TT_EUNSUPPORTED, "b must be in [1, 64]");
+      part = ttr::simt_cs_partials(m, n, b);
+      sbuf = (size_t)b * n;
+      break;
+    case TT_PASS_GRAMAPPLY:
+      if (b < 1 || b > 64) return fail(TT_EUNSUPPORTED, "b must be in [1, 64]");
+      if (ttr::simt_ga_fused_ok(m, b)) {
+        part = ttr::simt_ga_partials(m, n, b);
+      } else {
+        part = ttr::simt_cs_partials(m, n, b);
+        sbuf = (size_t)b * n;
+      }
+      break;
+    case TT_PASS_PROJECT:
+      if (b < 1 || b > 64) return fail(TT_EUNSUPPORTED, "b must be in [1, 64]");
+      break;
+    case TT_PASS_GRAM:
+      if (m > 128) return fail(TT_EUNSUPPORTED, "Gram pass needs m <= 128");
+      part = ttr::simt_gram_partials(m, n);
+      break;
+    default:
+      return fail(TT_EINVAL, "unknown op");
+  }
+  *bytes = align_up(part * 4) + align_up(sbuf * 4) + 256;
+  return TT_OK;
+}
+
+tt_status tt_pass(int op, const void* C, int c_dtype, int64_t m, int64_t n, int b, const float* x, void* y,
+                  int y_dtype, void* workspace, size_t ws_bytes, void* stream) {
+  size_t need = 0;
+  tt_status s = tt_pass_workspace_size(op, m, n, b, c_dtype, &need);
+  if (s != TT_OK) return s;
+  if (!C || !y || (op != TT_PASS_GRAM && !x)) return fail(TT_EINVAL, "NULL argument");
+  if (!workspace || ws_bytes < need) return fail(TT_ENOMEM, "workspace too small");
+  if (((uintptr_t)workspace & 255) != 0) return fail(TT_EINVAL, "workspace must be 256-byte aligned");
+  cudaStream_t st = (cudaStream_t)stream;
+  float* part = (float*)workspace;
+  size_t part_bytes = 0;
+  if (op == TT_PASS_GRAM) part_bytes = align_up(ttr::simt_gram_partials(m, n) * 4);
+  else if (op == TT_PASS_GRAMAPPLY && ttr::simt_ga_fused_ok(m, b)) part_bytes = align_up(ttr::simt_ga_partials(m, n, b) * 4);
+  else part_bytes = align_up(ttr::simt_cs_partials(m, n, b) * 4);
+  float* sbuf = (float*)((char*)workspace + part_bytes);
+  const bool bf = c_dtype == TT_BF16;
+  switch (op) {
+    case TT_PASS_SKETCH:
+      TTR_CUDA(ttr::launch_omega_transpose_any(x, n, b, sbuf, TT_F32, st));
+      if (bf) TTR_CUDA(ttr::simt_cs<__nv_bfloat16>((const __nv_bfloat16*)C, m, n, sbuf, n, b, part, (float*)y, b, st));
+      else TTR_CUDA(ttr::simt_cs<float>((const float*)C, m, n, sbuf, n, b, part, (float*)y, b, st));
+      break;
+    case TT_PASS_GRAMAPPLY:
+      if (ttr::simt_ga_fused_ok(m, b)) {
+        if (bf) TTR_CUDA(ttr::simt_ga<__nv_bfloat16>((const __nv_bfloat16*)C, m, n, x, b, b, part, (float*)y, b, st));
+        else TTR_CUDA(ttr::simt_ga<float>((const float*)C, m, n, x, b, b, part, (float*)y, b, st));
+      } else {
+        if (bf) {
+          TTR_CUDA((ttr::simt_proj<__nv_bfloat16, float>((const __nv_bfloat16*)C, m, n, x, b, b, sbuf, n, st)));
+          TTR_CUDA(ttr::simt_cs<__nv_bfloat16>((const __nv_bfloat16*)C, m, n, sbuf, n, b, part, (float*)y, b, st));
+        } else {
+          TTR_CUDA((ttr::simt_proj<float, float>((const float*)C, m, n, x, b, b, sbuf, n, st)));
+          TTR_CUDA(ttr::simt_cs<float>((const float*)C, m, n, sbuf, n, b, part, (float*)y, b, st));
+        }
+      }
+      break;
+    case TT_PASS_PROJECT:
+      if (y_dtype == TT_BF16) {
+        if (bf) TTR_CUDA((ttr::simt_proj<__nv_bfloat16, __nv_bfloat16>((const __nv_bfloat16*)C, m, n, x, b, b, (__nv_bfloat16*)y, n, st)));
+        else TTR_CUDA((ttr::simt_proj<float, __nv_bfloat16>((const float*)C, m, n, x, b, b, (__nv_bfloat16*)y, n, st)));
+      } else {
+        if (bf) TTR_CUDA((ttr::simt_proj<__nv_bfloat16, float>((const __nv_bfloat16*)C, m, n, x, b, b, (float*)y, n, st)));
+        else TTR_CUDA((ttr::simt_proj<float, float>((const float*)C, m, n, x, b, b, (float*)y, n, st)));
+      }
+      break;
+    case TT_PASS_GRAM:
+      if (bf) TTR_CUDA(ttr::simt_gram<__nv_bfloat16>((const __nv_bfloat16*)C, m, n, part, (float*)y, st));
+      else TTR_CUDA(ttr::simt_gram<float>((const float*)C, m, n, part, (float*)y, st));
+      break;
+  }
+  return TT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,53 @@
+// Shared definitions for the TT-rBKI CUDA library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/tt_rbki.h"
+
+namespace ttr {
+
+// Device status word values (mirrors tt_status where they overlap).
+enum : int { DEV_OK = 0, DEV_BREAKDOWN = TT_EBREAKDOWN, DEV_NONFINITE = TT_ENONFINITE };
+
+// Record the first non-OK status (later ones do not overwrite it).
+__device__ __forceinline__ void set_status(int* status, int code) {
+  if (status) atomicCAS(status, DEV_OK, code);
+}
+
+// Element loads/stores for the two storage types.
+__device__ __forceinline__ float ld_elem(const float* p, int64_t i) { return p[i]; }
+__device__ __forceinline__ float ld_elem(const __nv_bfloat16* p, int64_t i) {
+  return __bfloat162float(p[i]);
+}
+__device__ __forceinline__ void st_elem(float* p, int64_t i, float v) { p[i] = v; }
+__device__ __forceinline__ void st_elem(__nv_bfloat16* p, int64_t i, float v) {
+  p[i] = __float2bfloat16_rn(v);
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the whole CTA; `red` holds >= 32 floats of shared scratch.
+// Every thread receives the total.  Contains two __syncthreads().
+__device__ __forceinline__ float block_sum(float v, float* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  float t = (lane < nw) ? red[lane] : 0.f;
+  return warp_sum(t);
+}
+
+__host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+__host__ __device__ inline int64_t imin(int64_t a, int64_t b) { return a < b ? a : b; }
+__host__ __device__ inline int64_t imax(int64_t a, int64_t b) { return a > b ? a : b; }
+
+}  // namespace ttr

@@ -1,0 +1,46 @@
+// Internal launcher declarations shared by the kernel files and the host
+// driver.  Every launcher enqueues on the given stream and returns the
+// launch status; none synchronises.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace ttr {
+
+// ---- SIMT streaming passes (stream_simt.cu)
+template <typename TIn, typename TOut>
+cudaError_t simt_proj(const TIn* C, int64_t m, int64_t n, const float* X, int ldx, int b, TOut* S,
+                      int64_t lds, cudaStream_t st);
+template <typename TIn>
+cudaError_t simt_cs(const TIn* C, int64_t m, int64_t n, const float* S, int64_t lds, int b,
+                    float* partials, float* out, int64_t ldo, cudaStream_t st);
+template <typename TIn>
+cudaError_t simt_ga(const TIn* C, int64_t m, int64_t n, const float* X, int ldx, int b,
+                    float* partials, float* out, int64_t ldo, cudaStream_t st);
+template <typename TIn>
+cudaError_t simt_gram(const TIn* C, int64_t m, int64_t n, float* partials, float* out, cudaStream_t st);
+bool simt_ga_fused_ok(int64_t m, int b);
+int64_t simt_ga_partials(int64_t m, int64_t n, int b);   // floats
+int64_t simt_cs_partials(int64_t m, int64_t n, int b);   // floats
+int64_t simt_gram_partials(int64_t m, int64_t n);        // floats
+
+// ---- small dense algebra (small.cu)
+size_t orth_scratch_floats(int64_t m, int zc, int kq);
+cudaError_t launch_orth_block(const float* Z, int64_t ldz, int64_t m, int zc, float* Q, int64_t ldq, int kq,
+                              int c, float* scratch, uint64_t seed, int* status, cudaStream_t st);
+size_t rr_scratch_floats(int k);
+cudaError_t launch_rayleigh_ritz(const float* Q, const float* W, int64_t ld, int64_t m, int k, int r,
+                                 int identity_q, float* scratch, float* U, float* core, cudaStream_t st);
+cudaError_t launch_last_core(const void* R, int dtype, int64_t count, float* core, int* status, cudaStream_t st);
+cudaError_t launch_check_finite(const float* p, int64_t count, int* status, cudaStream_t st);
+
+// ---- inputs (misc.cu)
+cudaError_t launch_omega(uint64_t seed, int mode, int64_t n, int b, void* out, int dtype, int64_t si,
+                         int64_t sc, cudaStream_t st);
+cudaError_t launch_omega_transpose_any(const float* src, int64_t n, int b, void* dst, int dtype, cudaStream_t st);
+cudaError_t launch_permute(const void* src, int sdt, void* dst, int ddt, const int64_t* dims,
+                           const int64_t* sstrides, const int* perm, int d, cudaStream_t st);
+
+}  // namespace ttr

@@ -1,0 +1,429 @@
+// CUDA-core (SIMT) streaming passes over an unfolding C (m x n, row-major).
+//
+// These are the plain FP32 form of the four passes of Alg. 3 (and the form
+// used for shapes the tensor-core kernels do not cover):
+//   proj  : S = X^T C              (Alg. 3 step 10, and the first half of a
+//                                   Krylov power for tall unfoldings)
+//   cs    : Y = C S^T              (Alg. 3 step 4: the sketch C W with
+//                                   S = W^T, or the second half of a power)
+//   ga    : Y = C (C^T X)          (Alg. 3 step 4: one Krylov power, fused so
+//                                   each column tile of C is read once)
+//   gram  : G = C C^T              (exhaustion route: all of R^m is Krylov)
+// Reductions over n are split across CTAs into per-CTA partials that a
+// second kernel sums in a fixed order, so results are bit-reproducible.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace ttr {
+
+// ---------------------------------------------------------------- proj
+// S[c][col] = sum_i X[i][c] C[i][col];  256 threads = 16 (cols) x 16 (c).
+template <typename TIn, typename TOut, int VB>
+__global__ void __launch_bounds__(256) k_proj(const TIn* __restrict__ C, int64_t m, int64_t n,
+                                              const float* __restrict__ X, int ldx, int b,
+                                              TOut* __restrict__ S, int64_t lds) {
+  constexpr int TN = 64, RC = 32;
+  __shared__ float Cs[RC][TN];
+  __shared__ float Xs[RC][16 * VB];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int64_t col0 = (int64_t)blockIdx.x * TN;
+  float acc[VB][4];
+#pragma unroll
+  for (int v = 0; v < VB; ++v)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[v][u] = 0.f;
+  for (int64_t i0 = 0; i0 < m; i0 += RC) {
+    for (int e = threadIdx.x; e < RC * TN; e += 256) {
+      int r = e / TN, c = e % TN;
+      int64_t gi = i0 + r, gc = col0 + c;
+      Cs[r][c] = (gi < m && gc < n) ? ld_elem(C, gi * n + gc) : 0.f;
+    }
+    for (int e = threadIdx.x; e < RC * 16 * VB; e += 256) {
+      int r = e / (16 * VB), c = e % (16 * VB);
+      int64_t gi = i0 + r;
+      Xs[r][c] = (gi < m && c < b) ? X[gi * ldx + c] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int r = 0; r < RC; ++r) {
+      float cv[4], xv[VB];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) cv[u] = Cs[r][tx + 16 * u];
+#pragma unroll
+      for (int v = 0; v < VB; ++v) xv[v] = Xs[r][ty + 16 * v];
+#pragma unroll
+      for (int v = 0; v < VB; ++v)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[v][u] = fmaf(xv[v], cv[u], acc[v][u]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int v = 0; v < VB; ++v) {
+    int c = ty + 16 * v;
+    if (c >= b) continue;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      int64_t gc = col0 + tx + 16 * u;
+      if (gc < n) st_elem(S, (int64_t)c * lds + gc, acc[v][u]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- cs
+// P[split][i][c] = sum_{col in split} C[i][col] S[c][col] for the CTA's
+// 32-row tile; grid = (row tiles, splits).
+template <typename TIn, int VB>
+__global__ void __launch_bounds__(256) k_cs(const TIn* __restrict__ C, int64_t m, int64_t n,
+                                            const float* __restrict__ S, int64_t lds, int b,
+                                            float* __restrict__ P, int64_t cols_per_split) {
+  constexpr int TN = 64, RM = 32;
+  __shared__ float Cs[RM][TN + 1];
+  __shared__ float Ss[16 * VB][TN + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int64_t row0 = (int64_t)blockIdx.x * RM;
+  const int64_t cbeg = (int64_t)blockIdx.y * cols_per_split;
+  const int64_t cend = min(n, cbeg + cols_per_split);
+  float acc[2][VB];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int v = 0; v < VB; ++v) acc[a][v] = 0.f;
+  for (int64_t c0 = cbeg; c0 < cend; c0 += TN) {
+    for (int e = threadIdx.x; e < RM * TN; e += 256) {
+      int r = e / TN, c = e % TN;
+      int64_t gi = row0 + r, gc = c0 + c;
+      Cs[r][c] = (gi < m && gc < cend) ? ld_elem(C, gi * n + gc) : 0.f;
+    }
+    for (int e = threadIdx.x; e < 16 * VB * TN; e += 256) {
+      int r = e / TN, c = e % TN;
+      int64_t gc = c0 + c;
+      Ss[r][c] = (r < b && gc < cend) ? S[(int64_t)r * lds + gc] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int t = 0; t < TN; ++t) {
+      float ci[2], sv[VB];
+#pragma unroll
+      for (int a = 0; a < 2; ++a) ci[a] = Cs[ty + 16 * a][t];
+#pragma unroll
+      for (int v = 0; v < VB; ++v) sv[v] = Ss[tx + 16 * v][t];
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int v = 0; v < VB; ++v) acc[a][v] = fmaf(ci[a], sv[v], acc[a][v]);
+    }
+    __syncthreads();
+  }
+  float* out = P + (int64_t)blockIdx.y * m * b;
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    int64_t i = row0 + ty + 16 * a;
+    if (i >= m) continue;
+#pragma unroll
+    for (int v = 0; v < VB; ++v) {
+      int c = tx + 16 * v;
+      if (c < b) out[i * b + c] = acc[a][v];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- ga (fused)
+// P[cta] = sum over the CTA's column tiles C_j (C_j^T X), m <= 256, b <= 48.
+// Each 32-column tile of C is loaded once into shared memory and used by both
+// products.  Accumulator rows i = ty + 16 a, columns c = tx + 16 v.
+template <typename TIn, int MA, int VB>
+__global__ void __launch_bounds__(256) k_ga_fused(const TIn* __restrict__ C, int64_t m, int64_t n,
+                                                  const float* __restrict__ X, int ldx, int b,
+                                                  float* __restrict__ P, int64_t tiles_per_cta) {
+  constexpr int TN = 32;
+  constexpr int MP = 16 * MA;            // padded row count
+  constexpr int BP = 16 * VB;            // padded column count
+  extern __shared__ float sm[];
+  float* Cs = sm;                        // [MP][TN + 1]
+  float* Xs = Cs + MP * (TN + 1);        // [MP][BP + 1]
+  float* Ts = Xs + MP * (BP + 1);        // [TN][BP + 1]
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  for (int e = threadIdx.x; e < MP * BP; e += 256) {
+    int r = e / BP, c = e % BP;
+    Xs[r * (BP + 1) + c] = (r < m && c < b) ? X[(int64_t)r * ldx + c] : 0.f;
+  }
+  float acc[MA][VB];
+#pragma unroll
+  for (int a = 0; a < MA; ++a)
+#pragma unroll
+    for (int v = 0; v < VB; ++v) acc[a][v] = 0.f;
+  const int64_t ntiles = (n + TN - 1) / TN;
+  const int64_t t_beg = (int64_t)blockIdx.x * tiles_per_cta;
+  const int64_t t_end = min(ntiles, t_beg + tiles_per_cta);
+  for (int64_t tile = t_beg; tile < t_end; ++tile) {
+    const int64_t c0 = tile * TN;
+    __syncthreads();
+    for (int e = threadIdx.x; e < MP * TN; e += 256) {
+      int r = e / TN, c = e % TN;
+      int64_t gc = c0 + c;
+      Cs[r * (TN + 1) + c] = (r < m && gc < n) ? ld_elem(C, (int64_t)r * n + gc) : 0.f;
+    }
+    __syncthreads();
+    // T[t][c] = sum_i C[i][t] X[i][c]; thread -> t = tx + 16 u (u < 2), c = ty + 16 v
+    {
+      float tacc[2][VB];
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < VB; ++v) tacc[u][v] = 0.f;
+      for (int i = 0; i < MP; ++i) {
+        float cv0 = Cs[i * (TN + 1) + tx], cv1 = Cs[i * (TN + 1) + tx + 16];
+#pragma unroll
+        for (int v = 0; v < VB; ++v) {
+          float xv = Xs[i * (BP + 1) + ty + 16 * v];
+          tacc[0][v] = fmaf(cv0, xv, tacc[0][v]);
+          tacc[1][v] = fmaf(cv1, xv, tacc[1][v]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < VB; ++v) Ts[(tx + 16 * u) * (BP + 1) + ty + 16 * v] = tacc[u][v];
+    }
+    __syncthreads();
+    // acc[i][c] += sum_t C[i][t] T[t][c]
+#pragma unroll 4
+    for (int t = 0; t < TN; ++t) {
+      float tv[VB];
+#pragma unroll
+      for (int v = 0; v < VB; ++v) tv[v] = Ts[t * (BP + 1) + tx + 16 * v];
+#pragma unroll
+      for (int a = 0; a < MA; ++a) {
+        float cv = Cs[(ty + 16 * a) * (TN + 1) + t];
+#pragma unroll
+        for (int v = 0; v < VB; ++v) acc[a][v] = fmaf(cv, tv[v], acc[a][v]);
+      }
+    }
+  }
+  float* out = P + (int64_t)blockIdx.x * m * b;
+#pragma unroll
+  for (int a = 0; a < MA; ++a) {
+    int i = ty + 16 * a;
+    if (i >= m) continue;
+#pragma unroll
+    for (int v = 0; v < VB; ++v) {
+      int c = tx + 16 * v;
+      if (c < b) out[(int64_t)i * b + c] = acc[a][v];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- gram
+// P[cta] = sum over the CTA's column tiles C_j C_j^T, m <= 128.
+template <typename TIn, int MA>
+__global__ void __launch_bounds__(256) k_gram(const TIn* __restrict__ C, int64_t m, int64_t n,
+                                              float* __restrict__ P, int64_t tiles_per_cta) {
+  constexpr int TN = 32, MP = 16 * MA;
+  __shared__ float Cs[MP][TN + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  float acc[MA][MA];
+#pragma unroll
+  for (int a = 0; a < MA; ++a)
+#pragma unroll
+    for (int l = 0; l < MA; ++l) acc[a][l] = 0.f;
+  const int64_t ntiles = (n + TN - 1) / TN;
+  const int64_t t_beg = (int64_t)blockIdx.x * tiles_per_cta;
+  const int64_t t_end = min(ntiles, t_beg + tiles_per_cta);
+  for (int64_t tile = t_beg; tile < t_end; ++tile) {
+    const int64_t c0 = tile * TN;
+    __syncthreads();
+    for (int e = threadIdx.x; e < MP * TN; e += 256) {
+      int r = e / TN, c = e % TN;
+      int64_t gc = c0 + c;
+      Cs[r][c] = (r < m && gc < n) ? ld_elem(C, (int64_t)r * n + gc) : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int t = 0; t < TN; ++t) {
+      float ci[MA], cj[MA];
+#pragma unroll
+      for (int a = 0; a < MA; ++a) ci[a] = Cs[ty + 16 * a][t];
+#pragma unroll
+      for (int l = 0; l < MA; ++l) cj[l] = Cs[tx + 16 * l][t];
+#pragma unroll
+      for (int a = 0; a < MA; ++a)
+#pragma unroll
+        for (int l = 0; l < MA; ++l) acc[a][l] = fmaf(ci[a], cj[l], acc[a][l]);
+    }
+  }
+  float* out = P + (int64_t)blockIdx.x * m * m;
+#pragma unroll
+  for (int a = 0; a < MA; ++a) {
+    int i = ty + 16 * a;
+    if (i >= m) continue;
+#pragma unroll
+    for (int l = 0; l < MA; ++l) {
+      int j = tx + 16 * l;
+      if (j < m) out[(int64_t)i * m + j] = acc[a][l];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- reduce
+// out[r * ldo + c] = sum_{s < S} P[s][r][c] (fixed order), r < rows, c < cols.
+__global__ void k_reduce_partials(const float* __restrict__ P, int S, int64_t rows, int cols,
+                                  float* __restrict__ out, int64_t ldo) {
+  const int64_t E = rows * cols;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int k = 0; k < S; ++k) s += P[(int64_t)k * E + e];
+    int64_t r = e / cols;
+    int c = (int)(e % cols);
+    out[r * ldo + c] = s;
+  }
+}
+
+// ======================================================================
+// Launchers
+// ======================================================================
+static int target_ctas() { return 4 * 152; }
+
+static void reduce_launch(const float* P, int S, int64_t rows, int cols, float* out, int64_t ldo,
+                          cudaStream_t st) {
+  int64_t E = rows * cols;
+  int blocks = (int)imin(ceil_div(E, 256), 1024);
+  k_reduce_partials<<<blocks, 256, 0, st>>>(P, S, rows, cols, out, ldo);
+}
+
+template <typename TIn, typename TOut>
+cudaError_t simt_proj(const TIn* C, int64_t m, int64_t n, const float* X, int ldx, int b, TOut* S,
+                      int64_t lds, cudaStream_t st) {
+  dim3 grid((unsigned)ceil_div(n, 64));
+  if (b <= 16)
+    k_proj<TIn, TOut, 1><<<grid, 256, 0, st>>>(C, m, n, X, ldx, b, S, lds);
+  else if (b <= 32)
+    k_proj<TIn, TOut, 2><<<grid, 256, 0, st>>>(C, m, n, X, ldx, b, S, lds);
+  else if (b <= 48)
+    k_proj<TIn, TOut, 3><<<grid, 256, 0, st>>>(C, m, n, X, ldx, b, S, lds);
+  else if (b <= 64)
+    k_proj<TIn, TOut, 4><<<grid, 256, 0, st>>>(C, m, n, X, ldx, b, S, lds);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+int64_t simt_cs_splits(int64_t m, int64_t n) {
+  int64_t rt = ceil_div(m, 32);
+  int64_t s = imax(1, target_ctas() / rt);
+  s = imin(s, imax(1, ceil_div(n, 256)));
+  return s;
+}
+
+template <typename TIn>
+cudaError_t simt_cs(const TIn* C, int64_t m, int64_t n, const float* S, int64_t lds, int b,
+                    float* partials, float* out, int64_t ldo, cudaStream_t st) {
+  int64_t splits = simt_cs_splits(m, n);
+  int64_t per = ceil_div(ceil_div(n, 64), splits) * 64;
+  dim3 grid((unsigned)ceil_div(m, 32), (unsigned)splits);
+  if (b <= 16)
+    k_cs<TIn, 1><<<grid, 256, 0, st>>>(C, m, n, S, lds, b, partials, per);
+  else if (b <= 32)
+    k_cs<TIn, 2><<<grid, 256, 0, st>>>(C, m, n, S, lds, b, partials, per);
+  else if (b <= 48)
+    k_cs<TIn, 3><<<grid, 256, 0, st>>>(C, m, n, S, lds, b, partials, per);
+  else if (b <= 64)
+    k_cs<TIn, 4><<<grid, 256, 0, st>>>(C, m, n, S, lds, b, partials, per);
+  else
+    return cudaErrorInvalidValue;
+  reduce_launch(partials, (int)splits, m, b, out, ldo, st);
+  return cudaGetLastError();
+}
+
+int64_t simt_tiles_split(int64_t n, int64_t tn) {
+  int64_t tiles = ceil_div(n, tn);
+  int64_t ctas = imin(tiles, target_ctas());
+  return ceil_div(tiles, ctas);   // tiles per CTA
+}
+
+template <typename TIn, int MA, int VB>
+static void ga_launch(const TIn* C, int64_t m, int64_t n, const float* X, int ldx, int b, float* P,
+                      int64_t tpc, int ctas, cudaStream_t st) {
+  size_t smem = sizeof(float) * ((16 * MA) * 33 + (16 * MA) * (16 * VB + 1) + 32 * (16 * VB + 1));
+  auto kern = k_ga_fused<TIn, MA, VB>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  kern<<<ctas, 256, smem, st>>>(C, m, n, X, ldx, b, P, tpc);
+}
+
+template <typename TIn, int VB>
+static cudaError_t ga_dispatch_m(const TIn* C, int64_t m, int64_t n, const float* X, int ldx, int b,
+                                 float* P, int64_t tpc, int ctas, cudaStream_t st) {
+  int ma = (int)ceil_div(m, 16);
+  switch (ma) {
+#define TTR_GA_CASE(K) \
+  case K: ga_launch<TIn, K, VB>(C, m, n, X, ldx, b, P, tpc, ctas, st); break;
+    TTR_GA_CASE(1) TTR_GA_CASE(2) TTR_GA_CASE(3) TTR_GA_CASE(4) TTR_GA_CASE(5) TTR_GA_CASE(6)
+    TTR_GA_CASE(7) TTR_GA_CASE(8) TTR_GA_CASE(9) TTR_GA_CASE(10) TTR_GA_CASE(11) TTR_GA_CASE(12)
+    TTR_GA_CASE(13) TTR_GA_CASE(14) TTR_GA_CASE(15) TTR_GA_CASE(16)
+#undef TTR_GA_CASE
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaSuccess;
+}
+
+bool simt_ga_fused_ok(int64_t m, int b) { return m <= 256 && b <= 48 && ceil_div(m, 16) * ceil_div(b, 16) <= 48; }
+
+template <typename TIn>
+cudaError_t simt_ga(const TIn* C, int64_t m, int64_t n, const float* X, int ldx, int b,
+                    float* partials, float* out, int64_t ldo, cudaStream_t st) {
+  if (!simt_ga_fused_ok(m, b)) return cudaErrorInvalidValue;
+  int64_t tpc = simt_tiles_split(n, 32);
+  int ctas = (int)ceil_div(ceil_div(n, 32), tpc);
+  cudaError_t e;
+  if (b <= 16)
+    e = ga_dispatch_m<TIn, 1>(C, m, n, X, ldx, b, partials, tpc, ctas, st);
+  else if (b <= 32)
+    e = ga_dispatch_m<TIn, 2>(C, m, n, X, ldx, b, partials, tpc, ctas, st);
+  else
+    e = ga_dispatch_m<TIn, 3>(C, m, n, X, ldx, b, partials, tpc, ctas, st);
+  if (e != cudaSuccess) return e;
+  reduce_launch(partials, ctas, m, b, out, ldo, st);
+  return cudaGetLastError();
+}
+
+int64_t simt_ga_partials(int64_t m, int64_t n, int b) {
+  int64_t tpc = simt_tiles_split(n, 32);
+  return ceil_div(ceil_div(n, 32), tpc) * m * b;
+}
+int64_t simt_cs_partials(int64_t m, int64_t n, int b) { return simt_cs_splits(m, n) * m * b; }
+int64_t simt_gram_partials(int64_t m, int64_t n) {
+  int64_t tpc = simt_tiles_split(n, 32);
+  return ceil_div(ceil_div(n, 32), tpc) * m * m;
+}
+
+template <typename TIn>
+cudaError_t simt_gram(const TIn* C, int64_t m, int64_t n, float* partials, float* out, cudaStream_t st) {
+  int64_t tpc = simt_tiles_split(n, 32);
+  int ctas = (int)ceil_div(ceil_div(n, 32), tpc);
+  int ma = (int)ceil_div(m, 16);
+  switch (ma) {
+#define TTR_GR_CASE(K) \
+  case K: k_gram<TIn, K><<<ctas, 256, 0, st>>>(C, m, n, partials, tpc); break;
+    TTR_GR_CASE(1) TTR_GR_CASE(2) TTR_GR_CASE(3) TTR_GR_CASE(4) TTR_GR_CASE(5) TTR_GR_CASE(6)
+    TTR_GR_CASE(7) TTR_GR_CASE(8)
+#undef TTR_GR_CASE
+    default: return cudaErrorInvalidValue;
+  }
+  reduce_launch(partials, ctas, m, (int)m, out, m, st);
+  return cudaGetLastError();
+}
+
+// Explicit instantiations.
+template cudaError_t simt_proj<float, float>(const float*, int64_t, int64_t, const float*, int, int, float*, int64_t, cudaStream_t);
+template cudaError_t simt_proj<float, __nv_bfloat16>(const float*, int64_t, int64_t, const float*, int, int, __nv_bfloat16*, int64_t, cudaStream_t);
+template cudaError_t simt_proj<__nv_bfloat16, float>(const __nv_bfloat16*, int64_t, int64_t, const float*, int, int, float*, int64_t, cudaStream_t);
+template cudaError_t simt_proj<__nv_bfloat16, __nv_bfloat16>(const __nv_bfloat16*, int64_t, int64_t, const float*, int, int, __nv_bfloat16*, int64_t, cudaStream_t);
+template cudaError_t simt_cs<float>(const float*, int64_t, int64_t, const float*, int64_t, int, float*, float*, int64_t, cudaStream_t);
+template cudaError_t simt_cs<__nv_bfloat16>(const __nv_bfloat16*, int64_t, int64_t, const float*, int64_t, int, float*, float*, int64_t, cudaStream_t);
+template cudaError_t simt_ga<float>(const float*, int64_t, int64_t, const float*, int, int, float*, float*, int64_t, cudaStream_t);
+template cudaError_t simt_ga<__nv_bfloat16>(const __nv_bfloat16*, int64_t, int64_t, const float*, int, int, float*, float*, int64_t, cudaStream_t);
+template cudaError_t simt_gram<float>(const float*, int64_t, int64_t, float*, float*, cudaStream_t);
+template cudaError_t simt_gram<__nv_bfloat16>(const __nv_bfloat16*, int64_t, int64_t, float*, float*, cudaStream_t);
+
+}  // namespace ttr

@@ -1,0 +1,130 @@
+"""Kernel-level parity: each step-level entry point against the oracle or an
+FP64 recomputation of the same inputs, on small odd shapes with ragged
+tails.  Runs through the C ABI on the GPU."""
+import numpy as np
+import pytest
+
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tt():
+    import paper_2308_01480_gb300 as tt
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    tt._native.lib()
+    return tt
+
+
+@pytest.mark.parametrize("seed,k,n,b", [(7, 0, 1000, 9), (2 ** 40 + 5, 3, 4097, 30), (1, 1, 1, 1),
+                                        (123, 2, 333, 40), (99, 0, 70001, 13)])
+def test_omega_matches_oracle_generator(tt, seed, k, n, b):
+    """Device Philox4x32-10 + Box-Muller equals the oracle's float64
+    evaluation of the same definition to binary32 rounding of the transform."""
+    g = tt.omega_generate(seed, k, n, b).cpu().double().numpy()
+    ref = oracle.omega_from_seed(seed, k, n, b)
+    assert g.shape == ref.shape
+    assert np.max(np.abs(g - ref)) < 4e-6
+    gb = tt.omega_generate(seed, k, n, b, dtype=torch.bfloat16).cpu().float()
+    rb = torch.from_numpy(ref).float().to(torch.bfloat16).float()
+    # identical except where the binary32 value sits on a bf16 rounding boundary
+    diff = (gb - rb).abs()
+    assert float(diff.max()) <= float(rb.abs().max()) * 2 ** -7
+    assert float((diff > 0).float().mean()) < 1e-3
+
+
+@pytest.mark.parametrize("shape,view_perm,perm", [
+    ((5, 7, 3, 9), (2, 0, 3, 1), None),
+    ((5, 7, 3, 9), (2, 0, 3, 1), (3, 1, 0, 2)),
+    ((4, 1, 6, 5, 3), (0, 1, 2, 3, 4), (4, 3, 2, 1, 0)),
+    ((33, 17), (1, 0), (1, 0)),
+    ((2, 3, 4, 5, 6, 7), (5, 4, 3, 2, 1, 0), (1, 3, 5, 0, 2, 4)),
+])
+def test_permute_convert_bit_exact(tt, shape, view_perm, perm):
+    g = torch.Generator(device="cpu").manual_seed(3)
+    x = torch.randn(*shape, generator=g).cuda()
+    xs = x.permute(*view_perm)            # a strided source
+    ref = xs.permute(*perm).contiguous() if perm else xs.contiguous()
+    out = tt.permute_convert(xs, perm)
+    assert out.is_contiguous() and torch.equal(out, ref)
+    outb = tt.permute_convert(xs, perm, dst_dtype=torch.bfloat16)
+    assert torch.equal(outb, ref.to(torch.bfloat16))       # round-to-nearest-even
+    xb = xs.to(torch.bfloat16)
+    assert torch.equal(tt.permute_convert(xb, perm), ref.to(torch.bfloat16))
+    assert torch.equal(tt.permute_convert(xb, perm, dst_dtype=torch.float32),
+                       ref.to(torch.bfloat16).float())
+
+
+def _rand(shape, seed, dtype=np.float32):
+    return np.random.default_rng(seed).standard_normal(shape).astype(dtype)
+
+
+def _as_dev(a, bf16):
+    t = torch.from_numpy(a).cuda()
+    return t.to(torch.bfloat16) if bf16 else t
+
+
+def _host64(t):
+    return t.float().cpu().double().numpy()
+
+
+SHAPES = [(1, 1, 1), (7, 31, 9), (40, 4097, 30), (129, 31, 1), (256, 2050, 40), (33, 1000, 15),
+          (300, 777, 20), (7, 4097, 40)]
+
+
+@pytest.mark.parametrize("m,n,b", SHAPES)
+@pytest.mark.parametrize("bf16", [False, True])
+def test_pass_sketch(tt, m, n, b, bf16):
+    C = _as_dev(_rand((m, n), 1), bf16)
+    W = _rand((n, b), 2)
+    y = tt.tt_pass(tt.TT_PASS_SKETCH, C, x=torch.from_numpy(W).cuda())
+    Ch = _host64(C)
+    ref = Ch @ W.astype(np.float64)
+    bound = np.abs(Ch) @ np.abs(W.astype(np.float64))
+    assert np.max(np.abs(_host64(y) - ref)) <= 1e-5 * np.max(bound)
+
+
+@pytest.mark.parametrize("m,n,b", SHAPES)
+@pytest.mark.parametrize("bf16", [False, True])
+def test_pass_gram_apply(tt, m, n, b, bf16):
+    C = _as_dev(_rand((m, n), 3), bf16)
+    X = _rand((m, b), 4)
+    y = tt.tt_pass(tt.TT_PASS_GRAMAPPLY, C, x=torch.from_numpy(X).cuda())
+    Ch = _host64(C)
+    ref = Ch @ (Ch.T @ X.astype(np.float64))
+    bound = np.abs(Ch) @ (np.abs(Ch).T @ np.abs(X.astype(np.float64)))
+    assert np.max(np.abs(_host64(y) - ref)) <= 1e-5 * np.max(bound)
+
+
+@pytest.mark.parametrize("m,n,b", SHAPES)
+@pytest.mark.parametrize("bf16", [False, True])
+def test_pass_project(tt, m, n, b, bf16):
+    C = _as_dev(_rand((m, n), 5), bf16)
+    X = _rand((m, b), 6)
+    Ch = _host64(C)
+    ref = X.astype(np.float64).T @ Ch
+    bound = np.abs(X.astype(np.float64)).T @ np.abs(Ch)
+    y = tt.tt_pass(tt.TT_PASS_PROJECT, C, x=torch.from_numpy(X).cuda())
+    assert np.max(np.abs(_host64(y) - ref)) <= 1e-5 * np.max(bound)
+    yb = tt.tt_pass(tt.TT_PASS_PROJECT, C, x=torch.from_numpy(X).cuda(), y_dtype=torch.bfloat16)
+    assert yb.dtype == torch.bfloat16
+    assert np.max(np.abs(_host64(yb) - ref)) <= 2 ** -8 * np.max(np.abs(ref)) + 1e-5 * np.max(bound)
+
+
+@pytest.mark.parametrize("m,n", [(1, 1), (7, 31), (40, 4097), (64, 1000), (128, 333), (100, 65)])
+@pytest.mark.parametrize("bf16", [False, True])
+def test_pass_gram(tt, m, n, bf16):
+    C = _as_dev(_rand((m, n), 7), bf16)
+    y = tt.tt_pass(tt.TT_PASS_GRAM, C)
+    Ch = _host64(C)
+    ref = Ch @ Ch.T
+    bound = np.abs(Ch) @ np.abs(Ch).T
+    assert np.max(np.abs(_host64(y) - ref)) <= 1e-5 * np.max(bound)
+
+
+def test_pass_rejects_unsupported(tt):
+    C = torch.zeros((200, 10), device="cuda")
+    with pytest.raises(tt.TTError):
+        tt.tt_pass(tt.TT_PASS_GRAM, C)
