@@ -1,0 +1,353 @@
+#!/usr/bin/env python3
+"""Benchmark of the TT-rBKI hot path on GB300.
+
+One step = one whole TT-rBKI decomposition (every mode: Omega draw, sketch,
+Krylov powers, orthonormalisation, Rayleigh-Ritz, projection) of the
+40^5 precision-form workload: a tensor of TT ranks 20 with 0.8^j slice
+scales plus 5% Gaussian noise, stored once in BF16 (204.8 MB, larger than
+the 129 MB L2), target ranks 20, p = 10, q = 4.  The same tensor is also
+decomposed in the plain FP32 form for the BF16-vs-FP32 comparison at
+matched TT error.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank decomposes its own copy (independent
+replicas, weak scaling); rank 0 prints one JSON line.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2308_01480_gb300 import workloads as W  # noqa: E402
+
+METRIC = "rBKI-TT time and HBM-roofline fraction, BF16 vs FP32 at matched TT error"
+CONFIG_ID = 3
+# ncu DRAM traffic (read + write bytes per launch) of the dominant kernel, by
+# kernel family, with the profile summary it comes from; None when the
+# kernel changed after the capture.
+NCU_TRAFFIC = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = max(smax, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def rel_error_dev(A64, cores):
+    """||A - A_hat||_F / ||A||_F on the device in float64 (A64 is the float64
+    tensor on the GPU); A_hat is contracted core by core."""
+    import torch
+    dims = A64.shape
+    M = cores[-1].double().reshape(cores[-1].shape[0], -1)
+    for G in reversed(cores[1:-1]):
+        ra, I, rb = G.shape
+        M = (G.double().reshape(ra * I, rb) @ M).reshape(ra, -1)
+    F = cores[0].double().reshape(dims[0], -1)
+    Am = A64.reshape(dims[0], -1)
+    num = 0.0
+    for s in range(0, dims[0], 8):
+        num += float(torch.sum((Am[s:s + 8] - F[s:s + 8] @ M) ** 2))
+    return float(np.sqrt(num) / float(torch.linalg.norm(Am)))
+
+
+def time_steps(fn, steps, warmup, sync_all):
+    """Runs fn() warmup times, then times `steps` calls with CUDA events on
+    the current stream; returns milliseconds for the timed steps."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    sync_all()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(steps):
+        fn()
+    e1.record(st)
+    e1.synchronize()
+    sync_all()
+    return e0.elapsed_time(e1)
+
+
+def run_ours(args):
+    import torch
+    import paper_2308_01480_gb300 as tt
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        dist = dist_mod
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier_sync():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    w = W.CONFIGS[CONFIG_ID]
+    t0 = time.time()
+    A = W.make_tensor(w)                     # float64 host tensor, seeded
+    gen_s = time.time() - t0
+    A32 = torch.from_numpy(A.astype(np.float32)).to(dev)
+    # canonical BF16 copy made by the library's own convert kernel
+    Abf = tt.permute_convert(A32, dst_dtype=torch.bfloat16)
+    torch.cuda.synchronize()
+
+    ranks, p, q, seed = w.ranks, w.oversample, w.q, w.omega_seed
+    opts_bf = tt.options(storage=tt.TT_BF16, remainder=tt.TT_BF16)
+    opts_32 = tt.options(storage=tt.TT_F32, remainder=tt.TT_F32)
+    rr, _ = tt.core_sizes(w.dims, ranks)
+    cores_bf = [torch.empty((rr[k], w.dims[k], rr[k + 1]), dtype=torch.float32, device=dev)
+                for k in range(len(w.dims))]
+    cores_32 = [torch.empty_like(c) for c in cores_bf]
+    ws_bf = torch.empty(tt.workspace_size(w.dims, ranks, p, q, opts_bf), dtype=torch.uint8, device=dev)
+    ws_32 = torch.empty(tt.workspace_size(w.dims, ranks, p, q, opts_32), dtype=torch.uint8, device=dev)
+
+    def step_bf():
+        tt.decompose(Abf, ranks, p, q, omega_seed=seed, opts=opts_bf, workspace=ws_bf, cores=cores_bf)
+
+    def step_32():
+        tt.decompose(A32, ranks, p, q, omega_seed=seed, opts=opts_32, workspace=ws_32, cores=cores_32)
+
+    # ---- timed region: BF16 precision form (the headline)
+    for _ in range(args.warmup):
+        step_bf()
+    barrier_sync()
+    clocks = ClockSampler(local)
+    clocks.start()
+    tt.profile_begin(event_timing=True)
+    ms = time_steps(step_bf, args.steps, 0, barrier_sync)
+    stats = tt.profile_end()
+    clk = clocks.stop()
+    if tt.device_status(ws_bf) != 0:
+        raise RuntimeError("device status not OK after the BF16 runs")
+    ms_max = ms
+    if dist is not None:
+        tmax = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        ms_max = float(tmax.item())
+
+    # ---- FP32 form on the same tensor (comparison point)
+    fp32_steps = max(1, min(args.steps, 5))
+    ms32 = time_steps(step_32, fp32_steps, 1, barrier_sync)
+
+    # ---- accuracy of both forms against the float64 tensor
+    A64 = torch.from_numpy(A).to(dev)
+    eps_bf = rel_error_dev(A64, cores_bf)
+    eps_32 = rel_error_dev(A64, cores_32)
+    del A64
+
+    # ---- end to end through the public API with host buffers
+    host_bf = torch.empty(Abf.shape, dtype=torch.bfloat16, pin_memory=True)
+    host_bf.copy_(Abf.cpu())
+    dev_in = torch.empty_like(Abf)
+    core_host = [torch.empty(c.shape, dtype=torch.float32, pin_memory=True) for c in cores_bf]
+
+    def step_e2e():
+        dev_in.copy_(host_bf, non_blocking=True)
+        tt.decompose(dev_in, ranks, p, q, omega_seed=seed, opts=opts_bf, workspace=ws_bf, cores=cores_bf)
+        for h, c in zip(core_host, cores_bf):
+            h.copy_(c, non_blocking=True)
+
+    e2e_steps = max(1, min(args.steps, 5))
+    ms_e2e = time_steps(step_e2e, e2e_steps, 1, barrier_sync)
+    h2d = host_bf.numel() * host_bf.element_size()
+    d2h = sum(c.numel() * 4 for c in cores_bf)
+
+    # ---- roofline of the dominant kernel
+    peaks, peak_src = measured_peaks()
+    pass_stats = {k: v for k, v in stats.items() if v["bytes"] > 0 and v["ms"] > 0}
+    dom_name, dom = max(pass_stats.items(), key=lambda kv: kv[1]["ms"])
+    launches_dom = max(1, dom["launches"])
+    per_launch_ms = dom["ms"] / launches_dom
+    per_launch_bytes = dom["bytes"] / launches_dom
+    achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
+    traffic = NCU_TRAFFIC.get(dom_name)
+    total_launches = sum(v["launches"] for v in stats.values())
+
+    result = {
+        "metric": METRIC,
+        "value": world * args.steps / (ms_max * 1e-3),
+        "unit": "decompositions/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "bf16",
+        "data": "synthetic (seeded; paper's datasets unavailable)",
+        "config": {
+            "workload": f"{w.name}: 40^5 tensor, TT ranks 20 (0.8^j slices) + 5% Gaussian noise; "
+                        "BF16 storage and remainders, ranks 20, p=10, q=4",
+            "dims": list(w.dims), "ranks": list(ranks), "oversample": p, "q": q,
+            "omega": "Philox4x32-10 + Box-Muller on device, seed %d" % seed,
+            "l2": "input (204.8 MB BF16) larger than L2 (129 MB); no flush",
+            "parallelism": f"replicas{world}" if world > 1 else "single GPU",
+        },
+        "tt_error": {"bf16": eps_bf, "fp32": eps_32},
+        "fp32_form": {"ms_per_step": ms32 / fp32_steps, "decompositions_per_s": fp32_steps / (ms32 * 1e-3),
+                      "tt_error": eps_32, "speedup_bf16_over_fp32": (ms32 / fp32_steps) / (ms_max / args.steps)},
+        "e2e": {"value": e2e_steps / (ms_e2e * 1e-3), "unit": "decompositions/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": total_launches,
+        "roofline": {"bound": "hbm", "kernel": dom_name, "achieved": achieved,
+                     "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                     "peak_source": peak_src, "traffic": traffic,
+                     "bytes_per_launch": per_launch_bytes, "ms_per_launch": per_launch_ms,
+                     "launches": dom["launches"]},
+        "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
+                        "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 and v["bytes"] > 0 else None}
+                    for k, v in stats.items()},
+        "clocks": clk,
+        "input_gen_s": gen_s,
+    }
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(A, w)
+    if dist is not None:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(result))
+
+
+def oracle_step(A, w):
+    """One TT-rBKI decomposition by the FP64 oracle on the host cores."""
+    import oracle
+    oracle.tt_rbki(A, w.ranks, w.oversample, w.q, seed=w.omega_seed)
+
+
+def cpu_baseline(A, w):
+    t0 = time.time()
+    oracle_step(A, w)
+    dt = time.time() - t0
+    return {"value": 1.0 / dt, "unit": "decompositions/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "one full decomposition of the same workload by the float64 numpy oracle "
+                      "(BLAS/LAPACK threads = all host cores)", "seconds": dt}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    w = W.CONFIGS[CONFIG_ID]
+    A = W.make_tensor(w)
+    for _ in range(args.warmup):
+        oracle_step(A, w)
+    t0 = time.time()
+    for _ in range(args.steps):
+        oracle_step(A, w)
+    dt = time.time() - t0
+    v = args.steps / dt
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "decompositions/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded)", "config": {"workload": w.name},
+        "cpu_baseline": {"value": v, "unit": "decompositions/s", "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": "one full decomposition per step by the float64 numpy oracle"},
+        "e2e": {"value": v, "unit": "decompositions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

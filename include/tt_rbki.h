@@ -209,6 +209,25 @@ TT_API tt_status tt_pass(int op, const void* C, int c_dtype, int64_t m, int64_t 
                   const float* x, void* y, int y_dtype, void* workspace, size_t ws_bytes,
                   void* stream);
 
+/* ------------------------------------------------------------------------
+ * Kernel accounting for benchmarks (no counterpart in the paper).
+ * Between tt_rbki_profile_begin and tt_rbki_profile_end every kernel launch
+ * of the library is counted per kernel family; with event_timing = 1 each
+ * launch of a family is also bracketed by CUDA events on its stream, and
+ * the family's algorithmic bytes and flops are summed.  Process-global;
+ * tt_rbki_profile_end synchronises the recorded events.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+  char name[32];        /* kernel family                                       */
+  int64_t launches;     /* kernel launches                                     */
+  double ms;            /* summed event durations (0 without event timing)     */
+  double bytes;         /* summed algorithmic HBM bytes                        */
+  double flops;         /* summed algorithmic flops                            */
+} tt_kernel_stat;
+
+TT_API tt_status tt_rbki_profile_begin(int event_timing);
+TT_API tt_status tt_rbki_profile_end(tt_kernel_stat* stats, int max_stats, int* n_stats);
+
 #ifdef __cplusplus
 }
 #endif

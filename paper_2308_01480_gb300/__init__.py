@@ -12,7 +12,8 @@ from ._native import (TT_BF16, TT_F32, TT_PASS_GRAM, TT_PASS_GRAMAPPLY,  # noqa:
                       TT_PASS_PROJECT, TT_PASS_SKETCH, TTError)
 
 __all__ = ["decompose", "workspace_size", "core_sizes", "omega_generate", "permute_convert",
-           "tt_pass", "device_status", "options", "TTError", "TT_F32", "TT_BF16"]
+           "tt_pass", "device_status", "options", "profile_begin", "profile_end", "TTError", "TT_F32",
+           "TT_BF16"]
 
 
 def _torch():
@@ -110,6 +111,20 @@ def decompose(tensor, ranks, oversample, q, omega_seed=0, omegas=None, opts=None
     N.check(status)
     decompose.last_workspace = workspace
     return cores, list(ranks_out)
+
+
+def profile_begin(event_timing=True):
+    """Start counting kernel launches (and timing them with CUDA events)."""
+    N.check(N.lib().tt_rbki_profile_begin(1 if event_timing else 0))
+
+
+def profile_end():
+    """Stop accounting; returns {family: dict(launches, ms, bytes, flops)}."""
+    arr = (N.TTKernelStat * 64)()
+    n = ctypes.c_int()
+    N.check(N.lib().tt_rbki_profile_end(arr, 64, ctypes.byref(n)))
+    return {arr[i].name.decode(): dict(launches=arr[i].launches, ms=arr[i].ms, bytes=arr[i].bytes,
+                                       flops=arr[i].flops) for i in range(n.value)}
 
 
 def device_status(workspace, stream=None):

@@ -23,6 +23,11 @@ class TTOptions(ctypes.Structure):
                 ("exhaust_gram", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
+class TTKernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("ms", ctypes.c_double),
+                ("bytes", ctypes.c_double), ("flops", ctypes.c_double)]
+
+
 class TTError(RuntimeError):
     def __init__(self, status, message):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
@@ -53,6 +58,9 @@ _SIGNATURES = {
                            ctypes.c_int64, _vp], ctypes.c_int),
     "tt_pass_workspace_size": ([ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                 ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "tt_rbki_profile_begin": ([ctypes.c_int], ctypes.c_int),
+    "tt_rbki_profile_end": ([ctypes.POINTER(TTKernelStat), ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
+                            ctypes.c_int),
     "tt_pass": ([ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, _vp, _vp,
                  ctypes.c_int, _vp, ctypes.c_size_t, _vp], ctypes.c_int),
 }

@@ -9,6 +9,24 @@
 
 namespace ttr {
 
+// ---- accounting (profile.cu)
+void note_launch(const char* family, int count = 1);
+// Brackets the launches made during its lifetime with CUDA events on `st`
+// and adds bytes/flops to the family, when profiling is on.
+class ProfScope {
+ public:
+  ProfScope(const char* family, cudaStream_t st, double bytes, double flops);
+  ~ProfScope();
+  ProfScope(const ProfScope&) = delete;
+  ProfScope& operator=(const ProfScope&) = delete;
+
+ private:
+  const char* fam_;
+  cudaStream_t st_;
+  cudaEvent_t a_{}, b_{};
+  bool timed_ = false;
+};
+
 // ---- SIMT streaming passes (stream_simt.cu)
 template <typename TIn, typename TOut>
 cudaError_t simt_proj(const TIn* C, int64_t m, int64_t n, const float* X, int ldx, int b, TOut* S,

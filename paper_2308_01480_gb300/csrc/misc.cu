@@ -61,6 +61,8 @@ cudaError_t launch_omega(uint64_t seed, int mode, int64_t n, int b, void* out, i
                          int64_t sc, cudaStream_t st) {
   const int64_t total = n * ((b + 3) / 4);
   const int blocks = (int)imin(ceil_div(total, 256), 152 * 16);
+  ProfScope prof("omega_philox", st, (double)n * b * (dtype == TT_BF16 ? 2 : 4), 0);
+  note_launch("omega_philox");
   if (dtype == TT_BF16)
     k_omega<__nv_bfloat16><<<blocks, 256, 0, st>>>(seed, (uint32_t)mode, n, b, (__nv_bfloat16*)out, si, sc);
   else
@@ -92,6 +94,7 @@ cudaError_t launch_omega_transpose(const float* src, int64_t n, int b, void* dst
     return cudaErrorInvalidValue;
   }
   dim3 grid((unsigned)ceil_div(n, 64));
+  note_launch("omega_transpose");
   if (dtype == TT_BF16)
     k_transpose_in<__nv_bfloat16><<<grid, 256, 0, st>>>(src, n, b, (__nv_bfloat16*)dst);
   else
@@ -112,6 +115,7 @@ __global__ void k_transpose_in_wide(const float* __restrict__ src, int64_t n, in
 cudaError_t launch_omega_transpose_any(const float* src, int64_t n, int b, void* dst, int dtype, cudaStream_t st) {
   if (b <= 32) return launch_omega_transpose(src, n, b, dst, dtype, st);
   const int blocks = (int)imin(ceil_div(n * b, 256), 152 * 16);
+  note_launch("omega_transpose");
   if (dtype == TT_BF16)
     k_transpose_in_wide<__nv_bfloat16><<<blocks, 256, 0, st>>>(src, n, b, (__nv_bfloat16*)dst);
   else
@@ -153,6 +157,7 @@ cudaError_t launch_permute(const void* src, int sdt, void* dst, int ddt, const i
   }
   if (total == 0) return cudaSuccess;
   const int blocks = (int)imin(ceil_div(total, 256), 152 * 32);
+  note_launch("permute_convert");
   if (sdt == TT_F32 && ddt == TT_F32)
     k_permute<float, float><<<blocks, 256, 0, st>>>((const float*)src, (float*)dst, total, a);
   else if (sdt == TT_F32 && ddt == TT_BF16)

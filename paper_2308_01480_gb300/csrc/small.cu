@@ -351,6 +351,8 @@ cudaError_t launch_orth_block(const float* Z, int64_t ldz, int64_t m, int zc, fl
   size_t smem = sizeof(float) * ((size_t)kq + c + 32 + 64 + 4 * 32 + 64 + m + zc + 8);
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
   cudaFuncSetAttribute(k_orth_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  ProfScope prof("orth_block", st, 0, 0);
+  note_launch("orth_block");
   k_orth_block<<<1, SMALL_THREADS, smem, st>>>(Z, ldz, m, zc, Q, ldq, kq, c, scratch, seed, status);
   return cudaGetLastError();
 }
@@ -365,6 +367,8 @@ cudaError_t launch_rayleigh_ritz(const float* Q, const float* W, int64_t ld, int
   if (k > 256) return cudaErrorInvalidValue;   // cs scratch holds 128 pairs
   size_t smem = base + (use_global ? 0 : mats);
   cudaFuncSetAttribute(k_rayleigh_ritz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  ProfScope prof("rayleigh_ritz", st, 0, 0);
+  note_launch("rayleigh_ritz");
   k_rayleigh_ritz<<<1, SMALL_THREADS, smem, st>>>(Q, W, ld, m, k, r, identity_q, scratch,
                                                   scratch + (size_t)k * (k + 1), use_global, U, core);
   return cudaGetLastError();
@@ -372,6 +376,7 @@ cudaError_t launch_rayleigh_ritz(const float* Q, const float* W, int64_t ld, int
 
 cudaError_t launch_last_core(const void* R, int dtype, int64_t count, float* core, int* status, cudaStream_t st) {
   int blocks = (int)imin(ceil_div(count, 256), 1024);
+  note_launch("last_core");
   if (dtype == TT_BF16)
     k_last_core<__nv_bfloat16><<<blocks, 256, 0, st>>>((const __nv_bfloat16*)R, count, core);
   else
@@ -381,6 +386,7 @@ cudaError_t launch_last_core(const void* R, int dtype, int64_t count, float* cor
 
 cudaError_t launch_check_finite(const float* p, int64_t count, int* status, cudaStream_t st) {
   int blocks = (int)imin(ceil_div(count, 256), 1024);
+  note_launch("check_finite");
   k_check_finite<<<blocks, 256, 0, st>>>(p, count, status);
   return cudaGetLastError();
 }

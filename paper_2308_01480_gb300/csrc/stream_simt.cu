@@ -290,12 +290,16 @@ static void reduce_launch(const float* P, int S, int64_t rows, int cols, float* 
   int64_t E = rows * cols;
   int blocks = (int)imin(ceil_div(E, 256), 1024);
   k_reduce_partials<<<blocks, 256, 0, st>>>(P, S, rows, cols, out, ldo);
+  note_launch("reduce_partials");
 }
 
 template <typename TIn, typename TOut>
 cudaError_t simt_proj(const TIn* C, int64_t m, int64_t n, const float* X, int ldx, int b, TOut* S,
                       int64_t lds, cudaStream_t st) {
   dim3 grid((unsigned)ceil_div(n, 64));
+  ProfScope prof("proj_simt", st, (double)m * n * sizeof(TIn) + (double)m * b * 4 + (double)b * n * sizeof(TOut),
+                 2.0 * m * n * b);
+  note_launch("proj_simt");
   if (b <= 16)
     k_proj<TIn, TOut, 1><<<grid, 256, 0, st>>>(C, m, n, X, ldx, b, S, lds);
   else if (b <= 32)
@@ -322,6 +326,9 @@ cudaError_t simt_cs(const TIn* C, int64_t m, int64_t n, const float* S, int64_t 
   int64_t splits = simt_cs_splits(m, n);
   int64_t per = ceil_div(ceil_div(n, 64), splits) * 64;
   dim3 grid((unsigned)ceil_div(m, 32), (unsigned)splits);
+  {
+  ProfScope prof("cs_simt", st, (double)m * n * sizeof(TIn) + (double)b * n * 4, 2.0 * m * n * b);
+  note_launch("cs_simt");
   if (b <= 16)
     k_cs<TIn, 1><<<grid, 256, 0, st>>>(C, m, n, S, lds, b, partials, per);
   else if (b <= 32)
@@ -332,6 +339,7 @@ cudaError_t simt_cs(const TIn* C, int64_t m, int64_t n, const float* S, int64_t 
     k_cs<TIn, 4><<<grid, 256, 0, st>>>(C, m, n, S, lds, b, partials, per);
   else
     return cudaErrorInvalidValue;
+  }
   reduce_launch(partials, (int)splits, m, b, out, ldo, st);
   return cudaGetLastError();
 }
@@ -376,12 +384,16 @@ cudaError_t simt_ga(const TIn* C, int64_t m, int64_t n, const float* X, int ldx,
   int64_t tpc = simt_tiles_split(n, 32);
   int ctas = (int)ceil_div(ceil_div(n, 32), tpc);
   cudaError_t e;
+  {
+  ProfScope prof("gram_apply_simt", st, (double)m * n * sizeof(TIn) + (double)m * b * 4, 4.0 * m * n * b);
+  note_launch("gram_apply_simt");
   if (b <= 16)
     e = ga_dispatch_m<TIn, 1>(C, m, n, X, ldx, b, partials, tpc, ctas, st);
   else if (b <= 32)
     e = ga_dispatch_m<TIn, 2>(C, m, n, X, ldx, b, partials, tpc, ctas, st);
   else
     e = ga_dispatch_m<TIn, 3>(C, m, n, X, ldx, b, partials, tpc, ctas, st);
+  }
   if (e != cudaSuccess) return e;
   reduce_launch(partials, ctas, m, b, out, ldo, st);
   return cudaGetLastError();
@@ -402,6 +414,9 @@ cudaError_t simt_gram(const TIn* C, int64_t m, int64_t n, float* partials, float
   int64_t tpc = simt_tiles_split(n, 32);
   int ctas = (int)ceil_div(ceil_div(n, 32), tpc);
   int ma = (int)ceil_div(m, 16);
+  {
+  ProfScope prof("gram_simt", st, (double)m * n * sizeof(TIn), 2.0 * m * m * n);
+  note_launch("gram_simt");
   switch (ma) {
 #define TTR_GR_CASE(K) \
   case K: k_gram<TIn, K><<<ctas, 256, 0, st>>>(C, m, n, partials, tpc); break;
@@ -409,6 +424,7 @@ cudaError_t simt_gram(const TIn* C, int64_t m, int64_t n, float* partials, float
     TTR_GR_CASE(7) TTR_GR_CASE(8)
 #undef TTR_GR_CASE
     default: return cudaErrorInvalidValue;
+  }
   }
   reduce_launch(partials, ctas, m, (int)m, out, m, st);
   return cudaGetLastError();

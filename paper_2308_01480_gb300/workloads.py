@@ -70,7 +70,7 @@ def dense_from_cores(cores):
     T = cores[0].reshape(dims[0], -1)
     for G in cores[1:]:
         ra, I, rb = G.shape
-        T = np.einsum("xa,aib->xib", T, G, optimize=True).reshape(-1, rb)
+        T = (T @ G.reshape(ra, I * rb)).reshape(-1, rb)
     return T.reshape(dims)
 
 
