@@ -210,6 +210,35 @@ TT_API tt_status tt_pass(int op, const void* C, int c_dtype, int64_t m, int64_t 
                   void* stream);
 
 /* ------------------------------------------------------------------------
+ * Allocation-free Gram-apply.  The paper has no counterpart: this entry
+ * point exists for deployment, not for the method.
+ *
+ * Computes Y = C (C^T X) exactly like tt_pass(TT_PASS_GRAMAPPLY, ...) but
+ * takes no workspace.  It is meant for callers that cannot allocate device
+ * memory at the point of the call: code running inside another framework's
+ * stream capture or memory pool, latency-critical loops in which cudaMalloc
+ * would synchronise the device, or plugins whose host application owns all
+ * device memory.  The per-CTA partial sums go to one fixed array of 16 MiB
+ * (4,194,304 floats) in the library's device image, so every GPU on which
+ * the library is loaded holds those 16 MiB until the process exits.
+ *   C      device, m x n row-major, c_dtype TT_F32 or TT_BF16.
+ *   x      device, m x b float32 row-major.
+ *   y      device, m x b float32 row-major, written.
+ * Limits: 1 <= m <= 256 and 1 <= b <= 48, else TT_EUNSUPPORTED.  The pass
+ * runs at most 4,194,304 / (m b) CTAs so their partials fit the array.
+ * The first call on a device looks up the array's device address on the
+ * current device; make that first call before any stream capture.  All
+ * calls share the array; each call overwrites the part it reads, so nothing
+ * needs clearing, but calls whose kernels overlap on the GPU (several
+ * streams, or several host threads at once) race on it and give wrong
+ * results.  Allocates nothing: no cudaMalloc, cudaFree or allocating
+ * library routine.  Errors: TT_EINVAL (NULL pointer, dtype, size < 1),
+ * TT_EUNSUPPORTED, TT_ECUDA; the message is in tt_rbki_last_error().
+ */
+TT_API tt_status tt_gram_apply_noalloc(const void* C, int c_dtype, int64_t m, int64_t n, int b,
+                                       const float* x, float* y, void* stream);
+
+/* ------------------------------------------------------------------------
  * Kernel accounting for benchmarks (no counterpart in the paper).
  * Between tt_rbki_profile_begin and tt_rbki_profile_end every kernel launch
  * of the library is counted per kernel family; with event_timing = 1 each

@@ -58,6 +58,8 @@ _SIGNATURES = {
                            ctypes.c_int64, _vp], ctypes.c_int),
     "tt_pass_workspace_size": ([ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                 ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "tt_gram_apply_noalloc": ([_vp, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, _vp, _vp,
+                               _vp], ctypes.c_int),
     "tt_rbki_profile_begin": ([ctypes.c_int], ctypes.c_int),
     "tt_rbki_profile_end": ([ctypes.POINTER(TTKernelStat), ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
                             ctypes.c_int),

@@ -268,6 +268,10 @@ tt_status decompose_impl(const void* tensor, const int64_t* dims, int d, const i
 
 }  // namespace
 
+namespace ttr {
+void set_last_error(const char* msg) { g_last_error = msg; }
+}  // namespace ttr
+
 extern "C" {
 
 tt_status tt_rbki_default_options(tt_options* o) {

@@ -9,6 +9,9 @@
 
 namespace ttr {
 
+// ---- error message returned by tt_rbki_last_error (api.cu)
+void set_last_error(const char* msg);
+
 // ---- accounting (profile.cu)
 void note_launch(const char* family, int count = 1);
 // Brackets the launches made during its lifetime with CUDA events on `st`
@@ -39,6 +42,9 @@ cudaError_t simt_ga(const TIn* C, int64_t m, int64_t n, const float* X, int ldx,
                     float* partials, float* out, int64_t ldo, cudaStream_t st);
 template <typename TIn>
 cudaError_t simt_gram(const TIn* C, int64_t m, int64_t n, float* partials, float* out, cudaStream_t st);
+template <typename TIn>
+cudaError_t simt_ga_with_ctas(const TIn* C, int64_t m, int64_t n, const float* X, int ldx, int b,
+                              float* partials, int64_t max_ctas, float* out, int64_t ldo, cudaStream_t st);
 bool simt_ga_fused_ok(int64_t m, int b);
 int64_t simt_ga_partials(int64_t m, int64_t n, int b);   // floats
 int64_t simt_cs_partials(int64_t m, int64_t n, int b);   // floats

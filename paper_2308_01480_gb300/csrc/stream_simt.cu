@@ -399,6 +399,34 @@ cudaError_t simt_ga(const TIn* C, int64_t m, int64_t n, const float* X, int ldx,
   return cudaGetLastError();
 }
 
+// Fused Gram-apply with at most max_ctas CTAs, so that the partials fit a
+// caller-given buffer of max_ctas * m * b floats.
+template <typename TIn>
+cudaError_t simt_ga_with_ctas(const TIn* C, int64_t m, int64_t n, const float* X, int ldx, int b,
+                              float* partials, int64_t max_ctas, float* out, int64_t ldo, cudaStream_t st) {
+  if (!simt_ga_fused_ok(m, b) || max_ctas < 1) return cudaErrorInvalidValue;
+  const int64_t tiles = ceil_div(n, 32);
+  const int64_t ctas0 = imin(imin(tiles, target_ctas()), max_ctas);
+  const int64_t tpc = ceil_div(tiles, ctas0);
+  const int ctas = (int)ceil_div(tiles, tpc);
+  cudaError_t e;
+  {
+    ProfScope prof("gram_apply_simt", st, (double)m * n * sizeof(TIn) + (double)m * b * 4, 4.0 * m * n * b);
+    note_launch("gram_apply_simt");
+    if (b <= 16)
+      e = ga_dispatch_m<TIn, 1>(C, m, n, X, ldx, b, partials, tpc, ctas, st);
+    else if (b <= 32)
+      e = ga_dispatch_m<TIn, 2>(C, m, n, X, ldx, b, partials, tpc, ctas, st);
+    else
+      e = ga_dispatch_m<TIn, 3>(C, m, n, X, ldx, b, partials, tpc, ctas, st);
+  }
+  if (e != cudaSuccess) return e;
+  reduce_launch(partials, ctas, m, b, out, ldo, st);
+  return cudaGetLastError();
+}
+template cudaError_t simt_ga_with_ctas<float>(const float*, int64_t, int64_t, const float*, int, int, float*, int64_t, float*, int64_t, cudaStream_t);
+template cudaError_t simt_ga_with_ctas<__nv_bfloat16>(const __nv_bfloat16*, int64_t, int64_t, const float*, int, int, float*, int64_t, float*, int64_t, cudaStream_t);
+
 int64_t simt_ga_partials(int64_t m, int64_t n, int b) {
   int64_t tpc = simt_tiles_split(n, 32);
   return ceil_div(ceil_div(n, 32), tpc) * m * b;
