@@ -128,6 +128,7 @@ tt_status build_plan(const int64_t* dims, int d, const int64_t* ranks, int p, in
       maxPart = std::max(maxPart, (size_t)ttr::simt_gram_partials(M.m, M.n));
       maxG = std::max(maxG, (size_t)(M.m * M.m));
       maxSmall = std::max(maxSmall, ttr::rr_scratch_floats((int)M.m));
+      maxSmall = std::max(maxSmall, ttr::rr_fast_scratch_floats(M.m, (int)M.m, M.r_out));
     } else {
       maxS = std::max(maxS, (size_t)(M.b * M.n));
       maxPart = std::max(maxPart, (size_t)ttr::simt_cs_partials(M.m, M.n, M.b));
@@ -139,6 +140,8 @@ tt_status build_plan(const int64_t* dims, int d, const int64_t* ranks, int p, in
       maxQ = std::max(maxQ, (size_t)(M.m * M.kq));
       maxSmall = std::max(maxSmall, ttr::orth_scratch_floats(M.m, M.b, M.kq));
       maxSmall = std::max(maxSmall, ttr::rr_scratch_floats(M.kq));
+      maxSmall = std::max(maxSmall, ttr::orth_fast_scratch_floats(M.m, M.kq, M.b));
+      maxSmall = std::max(maxSmall, ttr::rr_fast_scratch_floats(M.m, M.kq, M.r_out));
     }
     maxU = std::max(maxU, (size_t)(M.m * M.r_out));
   }
@@ -172,7 +175,10 @@ tt_status run_mode(const Plan& P, int k, const TIn* C, char* ws, const float* om
   if (M.gram_route) {
     float* G = (float*)(ws + P.off_G);
     TTR_CUDA(ttr::simt_gram<TIn>(C, M.m, M.n, part, G, st));
-    TTR_CUDA(ttr::launch_rayleigh_ritz(nullptr, G, M.m, M.m, (int)M.m, r, 1, small, U, core, st));
+    if (ttr::eig_top_ok((int)M.m))
+      TTR_CUDA(ttr::launch_rr_fast(nullptr, G, M.m, M.m, (int)M.m, r, 1, small, U, core, st));
+    else
+      TTR_CUDA(ttr::launch_rayleigh_ritz(nullptr, G, M.m, M.m, (int)M.m, r, 1, small, U, core, st));
   } else {
     float* S = (float*)(ws + P.off_S);
     float* T = (float*)(ws + P.off_T);
@@ -188,7 +194,22 @@ tt_status run_mode(const Plan& P, int k, const TIn* C, char* ws, const float* om
     // sketch Y = C Omega, first basis block
     TTR_CUDA(ttr::simt_cs<TIn>(C, M.m, M.n, S, M.n, M.b, part, Y, M.b, st));
     const uint64_t rseed = 0x5EEDull * (uint64_t)(k + 1);
-    TTR_CUDA(ttr::launch_orth_block(Y, M.b, M.m, M.b, Q, kq, 0, M.blocks[0], small, rseed, status, st));
+    int* flag = status + 1;
+    unsigned* ticket = reinterpret_cast<unsigned*>(status + 2);
+    // orthonormalise a block: multi-CTA CholeskyQR path with the one-CTA
+    // robust path as fallback (run only if the fast path flagged a
+    // breakdown); the one-CTA path alone when the dimension cap truncates
+    auto orth = [&](const float* Z, int64_t ldz, int zc, int kq0, int c, uint64_t sd) -> tt_status {
+      if (c == zc && ttr::orth_fast_ok(M.m, kq0, zc)) {
+        TTR_CUDA(ttr::launch_orth_fast(Z, ldz, M.m, zc, Q, kq, kq0, small, ticket, flag, st));
+        TTR_CUDA(ttr::launch_orth_block(Z, ldz, M.m, zc, Q, kq, kq0, c, small, sd, status, flag, st));
+      } else {
+        TTR_CUDA(ttr::launch_orth_block(Z, ldz, M.m, zc, Q, kq, kq0, c, small, sd, status, nullptr, st));
+      }
+      return TT_OK;
+    };
+    tt_status os = orth(Y, M.b, M.b, 0, M.blocks[0], rseed);
+    if (os != TT_OK) return os;
     int col = 0;
     for (size_t j = 0; j < M.blocks.size(); ++j) {
       const int cj = M.blocks[j];
@@ -201,12 +222,16 @@ tt_status run_mode(const Plan& P, int k, const TIn* C, char* ws, const float* om
         TTR_CUDA((ttr::simt_proj<TIn, float>(C, M.m, M.n, Xj, kq, cj, T, M.n, st)));
         TTR_CUDA(ttr::simt_cs<TIn>(C, M.m, M.n, T, M.n, cj, part, Wj, kq, st));
       }
-      if (j + 1 < M.blocks.size())
-        TTR_CUDA(ttr::launch_orth_block(Wj, kq, M.m, cj, Q, kq, col + cj, M.blocks[j + 1], small,
-                                        rseed + 7919ull * (j + 1), status, st));
+      if (j + 1 < M.blocks.size()) {
+        os = orth(Wj, kq, cj, col + cj, M.blocks[j + 1], rseed + 7919ull * (j + 1));
+        if (os != TT_OK) return os;
+      }
       col += cj;
     }
-    TTR_CUDA(ttr::launch_rayleigh_ritz(Q, W, kq, M.m, kq, r, 0, small, U, core, st));
+    if (ttr::eig_top_ok(kq))
+      TTR_CUDA(ttr::launch_rr_fast(Q, W, kq, M.m, kq, r, 0, small, U, core, st));
+    else
+      TTR_CUDA(ttr::launch_rayleigh_ritz(Q, W, kq, M.m, kq, r, 0, small, U, core, st));
   }
   // Alg. 3 step 10: next remainder R = U^T C (r x n)
   char* Rout = ws + ((k % 2 == 0) ? P.off_R0 : P.off_R1);
@@ -237,7 +262,7 @@ tt_status decompose_impl(const void* tensor, const int64_t* dims, int d, const i
   cudaStream_t st = (cudaStream_t)stream;
   char* ws = (char*)workspace;
   int* status = (int*)(ws + P.off_status);
-  TTR_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
+  TTR_CUDA(cudaMemsetAsync(status, 0, 256, st));   // status, breakdown flag, orth ticket
   for (int k = 0; k < d - 1; ++k) {
     const void* C;
     int dt;

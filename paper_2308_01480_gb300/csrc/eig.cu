@@ -1,0 +1,494 @@
+// Rayleigh-Ritz of one mode (Alg. 3 steps 6-8): the top-r eigenpairs of the
+// small symmetric matrix H = Q^T C C^T Q (or of the Gram C C^T on the
+// exhaustion route), then U = Q V_r.
+//
+// The eigensolver runs in one CTA in FP32: Householder reduction of H to a
+// tridiagonal T, bisection by Sturm counts for the r largest eigenvalues
+// (one warp per eigenvalue, 32-point multisection), inverse iteration on T
+// with a pivoted tridiagonal LU for their eigenvectors, modified
+// Gram-Schmidt across them, and the back-transformation by the stored
+// reflectors.  Only the r wanted eigenvectors are ever formed.
+#include <float.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace ttr {
+
+constexpr int EIG_THREADS = 1024;
+constexpr int EIG_KMAX = 224;   // H (k x (k+1) floats) must fit shared memory
+
+// ------------------------------------------------------------ partial A^T B
+// P[cta][s][t] = sum_{i in rows of cta} A[i][s] B[i][t], s < ka, t < kb.
+__global__ void __launch_bounds__(256) k_tn_partials(const float* __restrict__ A, int64_t lda, int ka,
+                                                     const float* __restrict__ B, int64_t ldb, int kb,
+                                                     int64_t m, int64_t rows_per_cta, float* __restrict__ P) {
+  constexpr int RC = 16;
+  extern __shared__ float sm[];
+  float* As = sm;                  // [RC][ka]
+  float* Bs = As + RC * ka;        // [RC][kb]
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_cta;
+  const int64_t r1 = imin(m, r0 + rows_per_cta);
+  const int E = ka * kb;
+  float* out = P + (int64_t)blockIdx.x * E;
+  // each thread owns outputs e = e0 + tid + 256 u, u < 16
+  for (int e0 = 0; e0 < E; e0 += 256 * 16) {
+    float a[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) a[u] = 0.f;
+    for (int64_t i0 = r0; i0 < r1; i0 += RC) {
+      const int rc = (int)imin(RC, r1 - i0);
+      __syncthreads();
+      for (int x = threadIdx.x; x < RC * ka; x += 256) {
+        int r = x / ka, s = x % ka;
+        As[x] = r < rc ? A[(i0 + r) * lda + s] : 0.f;
+      }
+      for (int x = threadIdx.x; x < RC * kb; x += 256) {
+        int r = x / kb, t = x % kb;
+        Bs[x] = r < rc ? B[(i0 + r) * ldb + t] : 0.f;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int e = e0 + threadIdx.x + 256 * u;
+        if (e < E) {
+          const int s = e / kb, t = e % kb;
+          float v = a[u];
+          for (int r = 0; r < RC; ++r) v = fmaf(As[r * ka + s], Bs[r * kb + t], v);
+          a[u] = v;
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int e = e0 + threadIdx.x + 256 * u;
+      if (e < E) out[e] = a[u];
+    }
+  }
+}
+
+// out[e] = sum_{c < nparts} P[c][e] (fixed order)
+__global__ void k_sum_parts(const float* __restrict__ P, int nparts, int64_t E, float* __restrict__ out) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int c = 0; c < nparts; ++c) s += P[(int64_t)c * E + e];
+    out[e] = s;
+  }
+}
+
+// ------------------------------------------------------------ eigensolver
+struct EigSmem {
+  float* H;      // [k][k+1]
+  float* d;      // [k]
+  float* e;      // [k]
+  float* tau;    // [k]
+  float* v;      // [k]
+  float* p;      // [k]
+  float* red;    // [64]
+  float* lam;    // [r]
+};
+
+// Householder tridiagonalisation of the symmetric H (full storage, row
+// stride ld).  Afterwards d/e hold T, and column j of H below the
+// subdiagonal holds the reflector v_j (with implicit leading 1), tau[j] its
+// scale: P_j = I - tau_j v_j v_j^T acting on indices j+1..k-1.
+__device__ void householder_tridiag(EigSmem& S, int k, int ld) {
+  float* H = S.H;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  for (int j = 0; j + 2 < k; ++j) {
+    const int L = k - j - 1;            // reflector length
+    float part = 0.f;
+    for (int i = 1 + tid; i < L; i += blockDim.x) {
+      const float x = H[(j + 1 + i) * ld + j];
+      part = fmaf(x, x, part);
+    }
+    const float sigma = block_sum(part, S.red);
+    if (tid == 0) {
+      const float x0 = H[(j + 1) * ld + j];
+      float t = 0.f, v0 = 1.f, beta = x0;
+      if (sigma > 0.f) {
+        const float mu = sqrtf(x0 * x0 + sigma);
+        v0 = (x0 <= 0.f) ? x0 - mu : -sigma / (x0 + mu);
+        t = 2.f * v0 * v0 / (sigma + v0 * v0);
+        beta = mu;
+      }
+      S.tau[j] = t;
+      S.e[j] = beta;
+      S.d[j] = H[j * ld + j];
+      S.red[40] = (sigma > 0.f) ? 1.f / v0 : 0.f;
+    }
+    __syncthreads();
+    const float inv_v0 = S.red[40];
+    const float t = S.tau[j];
+    for (int i = tid; i < L; i += blockDim.x) {
+      float vi = (i == 0) ? 1.f : H[(j + 1 + i) * ld + j] * inv_v0;
+      if (t == 0.f) vi = (i == 0) ? 1.f : 0.f;
+      S.v[i] = vi;
+      if (i > 0) H[(j + 1 + i) * ld + j] = vi;     // keep v_j for back-transformation
+    }
+    __syncthreads();
+    if (t == 0.f) continue;
+    // p = t * A v, A = H[j+1.., j+1..]; one warp per row
+    for (int row = wid; row < L; row += nw) {
+      const float* hr = H + (j + 1 + row) * ld + (j + 1);
+      float s = 0.f;
+      for (int c = lane; c < L; c += 32) s = fmaf(hr[c], S.v[c], s);
+      s = warp_sum(s);
+      if (lane == 0) S.p[row] = t * s;
+    }
+    __syncthreads();
+    float kp = 0.f;
+    for (int i = tid; i < L; i += blockDim.x) kp = fmaf(S.v[i], S.p[i], kp);
+    const float K = 0.5f * t * block_sum(kp, S.red);
+    for (int i = tid; i < L; i += blockDim.x) S.p[i] = S.p[i] - K * S.v[i];   // w
+    __syncthreads();
+    // A -= v w^T + w v^T
+    for (int x = tid; x < L * L; x += blockDim.x) {
+      const int r = x / L, c = x % L;
+      float* h = H + (j + 1 + r) * ld + (j + 1 + c);
+      *h -= S.v[r] * S.p[c] + S.p[r] * S.v[c];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    if (k >= 2) {
+      S.d[k - 2] = H[(k - 2) * ld + (k - 2)];
+      S.e[k - 2] = H[(k - 1) * ld + (k - 2)];
+      S.tau[k - 2] = 0.f;
+    }
+    S.d[k - 1] = H[(k - 1) * ld + (k - 1)];
+    S.e[k - 1] = 0.f;
+    S.tau[k - 1] = 0.f;
+  }
+  __syncthreads();
+}
+
+// Number of eigenvalues of T (d, e) smaller than x (Sturm sequence).
+__device__ __forceinline__ int sturm_count(const float* d, const float* e2, int k, float x, float pivmin) {
+  int c = 0;
+  float q = d[0] - x;
+  if (fabsf(q) < pivmin) q = -pivmin;
+  c += q < 0.f;
+  for (int i = 1; i < k; ++i) {
+    q = (d[i] - x) - e2[i - 1] / q;
+    if (fabsf(q) < pivmin) q = -pivmin;
+    c += q < 0.f;
+  }
+  return c;
+}
+
+// Solves (T - lam I) x = y in place (x holds y on entry), using a pivoted
+// tridiagonal LU written to per-vector scratch w[0..5k).
+__device__ void tri_solve_inverse_iteration(const float* d, const float* e, int k, float lam, float tiny,
+                                            float* x, float* w) {
+  float* u0 = w;
+  float* u1 = w + k;
+  float* u2 = w + 2 * k;
+  float* l = w + 3 * k;
+  float* sw = w + 4 * k;
+  float alpha = d[0] - lam, beta = (k > 1) ? e[0] : 0.f;
+  for (int i = 0; i + 1 < k; ++i) {
+    const float sub = e[i];
+    const float a1 = d[i + 1] - lam, c1 = (i + 2 < k) ? e[i + 1] : 0.f;
+    if (fabsf(alpha) >= fabsf(sub)) {
+      const float piv = (fabsf(alpha) < tiny) ? copysignf(tiny, alpha) : alpha;
+      const float li = sub / piv;
+      u0[i] = piv; u1[i] = beta; u2[i] = 0.f; l[i] = li; sw[i] = 0.f;
+      alpha = a1 - li * beta;
+      beta = c1;
+    } else {
+      const float li = alpha / sub;
+      u0[i] = (fabsf(sub) < tiny) ? copysignf(tiny, sub) : sub;
+      u1[i] = a1; u2[i] = c1; l[i] = li; sw[i] = 1.f;
+      alpha = beta - li * a1;
+      beta = -li * c1;
+    }
+  }
+  u0[k - 1] = (fabsf(alpha) < tiny) ? copysignf(tiny, alpha) : alpha;
+  // forward: apply the row exchanges and multipliers
+  for (int i = 0; i + 1 < k; ++i) {
+    if (sw[i] != 0.f) { const float t = x[i]; x[i] = x[i + 1]; x[i + 1] = t; }
+    x[i + 1] -= l[i] * x[i];
+  }
+  // back substitution with the upper factor (bandwidth 2)
+  for (int i = k - 1; i >= 0; --i) {
+    float s = x[i];
+    if (i + 1 < k) s -= u1[i] * x[i + 1];
+    if (i + 2 < k) s -= u2[i] * x[i + 2];
+    x[i] = s / u0[i];
+  }
+}
+
+// Top-r eigenpairs of the symmetric k x k matrix held in S.H (ld = k+1).
+// Writes eigenvectors as columns of Vout (k x r, row stride ldv) in global
+// memory and eigenvalues (descending) to S.lam.  scratch: 6 * k * r floats.
+__device__ void sym_eig_top(EigSmem& S, int k, int r, float* Vout, int ldv, float* scratch) {
+  const int ld = k + 1;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  householder_tridiag(S, k, ld);
+  float* e2 = S.p;                        // reuse: squared off-diagonals
+  for (int i = tid; i < k; i += blockDim.x) e2[i] = S.e[i] * S.e[i];
+  __syncthreads();
+  // Gershgorin interval and scale
+  float glo = FLT_MAX, ghi = -FLT_MAX, amax = 0.f;
+  for (int i = tid; i < k; i += blockDim.x) {
+    const float off = (i > 0 ? fabsf(S.e[i - 1]) : 0.f) + (i + 1 < k ? fabsf(S.e[i]) : 0.f);
+    glo = fminf(glo, S.d[i] - off);
+    ghi = fmaxf(ghi, S.d[i] + off);
+    amax = fmaxf(amax, fmaxf(fabsf(S.d[i]), fabsf(S.e[i])));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    glo = fminf(glo, __shfl_xor_sync(0xffffffffu, glo, o));
+    ghi = fmaxf(ghi, __shfl_xor_sync(0xffffffffu, ghi, o));
+    amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  }
+  __syncthreads();
+  if (lane == 0) { S.red[wid] = glo; S.red[32 + wid] = ghi; }
+  __syncthreads();
+  if (tid == 0) {
+    float a = FLT_MAX, bb = -FLT_MAX;
+    for (int w = 0; w < nw; ++w) { a = fminf(a, S.red[w]); bb = fmaxf(bb, S.red[32 + w]); }
+    S.red[0] = a; S.red[1] = bb;
+  }
+  __syncthreads();
+  glo = S.red[0];
+  ghi = S.red[1];
+  __syncthreads();
+  if (lane == 0) S.red[wid] = amax;
+  __syncthreads();
+  if (tid == 0) { float a = 0.f; for (int w = 0; w < nw; ++w) a = fmaxf(a, S.red[w]); S.red[2] = a; }
+  __syncthreads();
+  const float tnorm = fmaxf(S.red[2], FLT_MIN);
+  const float pivmin = FLT_MIN * fmaxf(1.f, tnorm * tnorm);
+  const float pad = 2.f * FLT_EPSILON * tnorm + pivmin;
+  // bisection: warp w finds the (j)-th largest eigenvalue for j = w, w + nw, ...
+  for (int j = wid; j < r; j += nw) {
+    const int t = k - 1 - j;             // ascending index
+    float lo = glo - pad, hi = ghi + pad;
+    for (int it = 0; it < 12; ++it) {
+      const float x = lo + (hi - lo) * (float)(lane + 1) / 33.f;
+      const int cnt = sturm_count(S.d, e2, k, x, pivmin);
+      const unsigned ge = __ballot_sync(0xffffffffu, cnt >= t + 1);
+      const float xs = __shfl_sync(0xffffffffu, x, ge ? (__ffs(ge) - 1) : 31);
+      const int s = ge ? (__ffs(ge) - 1) : 32;
+      const float xprev = __shfl_sync(0xffffffffu, x, s > 0 ? s - 1 : 0);
+      if (s == 32) lo = xs;                          // all points below: lambda in (x_31, hi)
+      else { hi = xs; if (s > 0) lo = xprev; }
+      if (hi - lo <= 2.f * FLT_EPSILON * fmaxf(fabsf(lo), fabsf(hi)) + pivmin) break;
+    }
+    if (lane == 0) S.lam[j] = 0.5f * (lo + hi);
+  }
+  __syncthreads();
+  // inverse iteration: one thread per wanted eigenvector, vectors in scratch
+  float* X = scratch;                  // [r][k]
+  float* Wk = scratch + (size_t)r * k; // [r][5k]
+  const float tiny = FLT_EPSILON * tnorm + pivmin;
+  for (int j = tid; j < r; j += blockDim.x) {
+    float* x = X + (size_t)j * k;
+    float* w = Wk + (size_t)j * 5 * k;
+    for (int i = 0; i < k; ++i) x[i] = 1.f + 0.01f * (float)((i * 7 + j * 13) % 11);
+    for (int it = 0; it < 3; ++it) {
+      tri_solve_inverse_iteration(S.d, S.e, k, S.lam[j], tiny, x, w);
+      float mx = 0.f;
+      for (int i = 0; i < k; ++i) mx = fmaxf(mx, fabsf(x[i]));
+      const float sc = mx > 0.f ? 1.f / mx : 0.f;
+      for (int i = 0; i < k; ++i) x[i] *= sc;
+    }
+  }
+  __syncthreads();
+  // Gram-Schmidt (classical, twice) across the r vectors in descending
+  // eigenvalue order; restores orthogonality inside clusters
+  float* dots = S.v;                   // [r] (r <= k)
+  for (int j = 0; j < r; ++j) {
+    float* xj = X + (size_t)j * k;
+    for (int pass = 0; pass < 2 && j > 0; ++pass) {
+      for (int i2 = wid; i2 < j; i2 += nw) {
+        const float* xi = X + (size_t)i2 * k;
+        float pp = 0.f;
+        for (int i = lane; i < k; i += 32) pp = fmaf(xi[i], xj[i], pp);
+        pp = warp_sum(pp);
+        if (lane == 0) dots[i2] = pp;
+      }
+      __syncthreads();
+      for (int i = tid; i < k; i += blockDim.x) {
+        float s = xj[i];
+        for (int i2 = 0; i2 < j; ++i2) s -= dots[i2] * X[(size_t)i2 * k + i];
+        xj[i] = s;
+      }
+      __syncthreads();
+    }
+    float pp = 0.f;
+    for (int i = tid; i < k; i += blockDim.x) pp = fmaf(xj[i], xj[i], pp);
+    const float nrm = sqrtf(block_sum(pp, S.red));
+    const float inv = nrm > 0.f ? 1.f / nrm : 0.f;
+    for (int i = tid; i < k; i += blockDim.x) xj[i] *= inv;
+    __syncthreads();
+  }
+  // back-transformation x <- P_0 P_1 ... P_{k-3} x ; one warp per vector
+  for (int j = wid; j < r; j += nw) {
+    float* x = X + (size_t)j * k;
+    for (int h = k - 3; h >= 0; --h) {
+      const float t = S.tau[h];
+      if (t == 0.f) continue;
+      const int L = k - h - 1;
+      float s = 0.f;
+      for (int i = lane; i < L; i += 32) {
+        const float vi = (i == 0) ? 1.f : S.H[(h + 1 + i) * ld + h];
+        s = fmaf(vi, x[h + 1 + i], s);
+      }
+      s = warp_sum(s) * t;
+      for (int i = lane; i < L; i += 32) {
+        const float vi = (i == 0) ? 1.f : S.H[(h + 1 + i) * ld + h];
+        x[h + 1 + i] -= s * vi;
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  for (int x = tid; x < k * r; x += blockDim.x) {
+    const int i = x / r, j = x % r;
+    Vout[(size_t)i * ldv + j] = X[(size_t)j * k + i];
+  }
+  __syncthreads();
+}
+
+// H (k x k, global, row stride ldh) -> top-r eigenvectors V (k x r, ld r).
+__global__ void __launch_bounds__(EIG_THREADS) k_eig_top(const float* __restrict__ Hin, int64_t ldh, int k, int r,
+                                                        float* __restrict__ V, float* __restrict__ scratch,
+                                                        float* __restrict__ evals) {
+  extern __shared__ float sm[];
+  EigSmem S;
+  S.H = sm;
+  S.d = S.H + (size_t)k * (k + 1);
+  S.e = S.d + k;
+  S.tau = S.e + k;
+  S.v = S.tau + k;
+  S.p = S.v + k;
+  S.red = S.p + k;
+  S.lam = S.red + 64;
+  for (int x = threadIdx.x; x < k * k; x += blockDim.x) {
+    const int i = x / k, j = x % k;
+    S.H[i * (k + 1) + j] = 0.5f * (Hin[(int64_t)i * ldh + j] + Hin[(int64_t)j * ldh + i]);
+  }
+  __syncthreads();
+  sym_eig_top(S, k, r, V, r, scratch);
+  if (evals)
+    for (int j = threadIdx.x; j < r; j += blockDim.x) evals[j] = S.lam[j];
+}
+
+// U (m x r) = Q (m x k, ld ldq) V (k x r); also written to core (same layout).
+__global__ void __launch_bounds__(256) k_apply_basis(const float* __restrict__ Q, int64_t ldq, int64_t m, int k,
+                                                     const float* __restrict__ V, int r, float* __restrict__ U,
+                                                     float* __restrict__ core, int64_t rows_per_cta) {
+  extern __shared__ float sm[];
+  float* Vs = sm;   // [k][r]
+  for (int x = threadIdx.x; x < k * r; x += blockDim.x) Vs[x] = V[x];
+  __syncthreads();
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_cta;
+  const int64_t r1 = imin(m, r0 + rows_per_cta);
+  for (int64_t x = threadIdx.x; x < (r1 - r0) * r; x += blockDim.x) {
+    const int64_t i = r0 + x / r;
+    const int j = (int)(x % r);
+    const float* qi = Q + i * ldq;
+    float s = 0.f;
+    for (int t = 0; t < k; ++t) s = fmaf(qi[t], Vs[t * r + j], s);
+    U[i * r + j] = s;
+    if (core) core[i * r + j] = s;
+  }
+}
+
+// ------------------------------------------------------------ launchers
+size_t eig_scratch_floats(int k, int r) { return (size_t)k * k + (size_t)6 * k * r + (size_t)k * r + 64; }
+
+bool eig_top_ok(int k) { return k >= 1 && k <= EIG_KMAX; }
+
+static size_t eig_smem(int k, int r) { return sizeof(float) * ((size_t)k * (k + 1) + 5 * (size_t)k + 64 + r + 8); }
+
+cudaError_t launch_eig_top(const float* H, int64_t ldh, int k, int r, float* V, float* scratch, float* evals,
+                           cudaStream_t st) {
+  if (!eig_top_ok(k) || r > k || r < 1) return cudaErrorInvalidValue;
+  const size_t smem = eig_smem(k, r);
+  cudaFuncSetAttribute(k_eig_top, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  ProfScope prof("eig_top", st, 0, 0);
+  note_launch("eig_top");
+  k_eig_top<<<1, EIG_THREADS, smem, st>>>(H, ldh, k, r, V, scratch, evals);
+  return cudaGetLastError();
+}
+
+static int rows_split(int64_t m, int64_t* rows_per_cta) {
+  int64_t ctas = imin(ceil_div(m, 16), 128);
+  *rows_per_cta = ceil_div(m, ctas);
+  return (int)ceil_div(m, *rows_per_cta);
+}
+
+size_t tn_parts_floats(int64_t m, int ka, int kb) {
+  int64_t rpc;
+  return (size_t)rows_split(m, &rpc) * ka * kb;
+}
+
+cudaError_t launch_tn(const float* A, int64_t lda, int ka, const float* B, int64_t ldb, int kb, int64_t m,
+                      float* parts, float* out, cudaStream_t st) {
+  int64_t rpc;
+  const int ctas = rows_split(m, &rpc);
+  const size_t smem = sizeof(float) * 16 * (size_t)(ka + kb);
+  cudaFuncSetAttribute(k_tn_partials, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  {
+    ProfScope prof("tn_small", st, 0, 2.0 * m * ka * kb);
+    note_launch("tn_small");
+    k_tn_partials<<<ctas, 256, smem, st>>>(A, lda, ka, B, ldb, kb, m, rpc, parts);
+  }
+  const int64_t E = (int64_t)ka * kb;
+  note_launch("sum_parts");
+  k_sum_parts<<<(int)imin(ceil_div(E, 256), 256), 256, 0, st>>>(parts, ctas, E, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply_basis(const float* Q, int64_t ldq, int64_t m, int k, const float* V, int r, float* U,
+                               float* core, cudaStream_t st) {
+  int64_t rpc = 8;
+  const int ctas = (int)ceil_div(m, rpc);
+  const size_t smem = sizeof(float) * (size_t)k * r;
+  cudaFuncSetAttribute(k_apply_basis, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  ProfScope prof("apply_basis", st, 0, 2.0 * m * k * r);
+  note_launch("apply_basis");
+  k_apply_basis<<<ctas, 256, smem, st>>>(Q, ldq, m, k, V, r, U, core, rpc);
+  return cudaGetLastError();
+}
+
+// Rayleigh-Ritz: H = Q^T W (or H = G when Q is the identity), top-r
+// eigenvectors, U = Q V.  scratch holds rr_fast_scratch_floats(m, k, r).
+size_t rr_fast_scratch_floats(int64_t m, int k, int r) {
+  return tn_parts_floats(m, k, k) + (size_t)k * k + (size_t)k * r + eig_scratch_floats(k, r);
+}
+
+cudaError_t launch_rr_fast(const float* Q, const float* W, int64_t ld, int64_t m, int k, int r, int identity_q,
+                           float* scratch, float* U, float* core, cudaStream_t st) {
+  float* parts = scratch;
+  float* H = parts + tn_parts_floats(m, k, k);
+  float* V = H + (size_t)k * k;
+  float* es = V + (size_t)k * r;
+  cudaError_t e;
+  const float* Hsrc;
+  int64_t ldh;
+  if (identity_q) {
+    Hsrc = W;
+    ldh = ld;
+  } else {
+    e = launch_tn(Q, ld, k, W, ld, k, m, parts, H, st);
+    if (e != cudaSuccess) return e;
+    Hsrc = H;
+    ldh = k;
+  }
+  e = launch_eig_top(Hsrc, ldh, k, r, V, es, nullptr, st);
+  if (e != cudaSuccess) return e;
+  if (identity_q) {
+    // Q = I (m == k): U = V
+    e = cudaMemcpyAsync(U, V, sizeof(float) * (size_t)m * r, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && core)
+      e = cudaMemcpyAsync(core, V, sizeof(float) * (size_t)m * r, cudaMemcpyDeviceToDevice, st);
+    return e;
+  }
+  return launch_apply_basis(Q, ld, m, k, V, r, U, core, st);
+}
+
+}  // namespace ttr

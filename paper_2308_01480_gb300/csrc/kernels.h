@@ -53,7 +53,20 @@ int64_t simt_gram_partials(int64_t m, int64_t n);        // floats
 // ---- small dense algebra (small.cu)
 size_t orth_scratch_floats(int64_t m, int zc, int kq);
 cudaError_t launch_orth_block(const float* Z, int64_t ldz, int64_t m, int zc, float* Q, int64_t ldq, int kq,
-                              int c, float* scratch, uint64_t seed, int* status, cudaStream_t st);
+                              int c, float* scratch, uint64_t seed, int* status, const int* only_if,
+                              cudaStream_t st);
+
+// ---- multi-CTA block orthonormalisation (orth.cu)
+bool orth_fast_ok(int64_t m, int kq, int b);
+size_t orth_fast_scratch_floats(int64_t m, int kq, int b);
+cudaError_t launch_orth_fast(const float* W, int64_t ldw, int64_t m, int b, float* Q, int64_t ldq, int kq,
+                             float* scratch, unsigned* ticket, int* flag, cudaStream_t st);
+
+// ---- Rayleigh-Ritz through a tridiagonal eigensolver (eig.cu)
+bool eig_top_ok(int k);
+size_t rr_fast_scratch_floats(int64_t m, int k, int r);
+cudaError_t launch_rr_fast(const float* Q, const float* W, int64_t ld, int64_t m, int k, int r, int identity_q,
+                           float* scratch, float* U, float* core, cudaStream_t st);
 size_t rr_scratch_floats(int k);
 cudaError_t launch_rayleigh_ritz(const float* Q, const float* W, int64_t ld, int64_t m, int k, int r,
                                  int identity_q, float* scratch, float* U, float* core, cudaStream_t st);

@@ -146,7 +146,8 @@ __device__ void sort_desc(const float* H, int ldh, int k, int* order) {
 // Scratch (global): Zw m x zc, Zt m x zc, P kq x zc, G/Vg zc x zc.
 __global__ void __launch_bounds__(SMALL_THREADS)
 k_orth_block(const float* __restrict__ Z, int64_t ldz, int64_t m, int zc, float* Q, int64_t ldq, int kq,
-             int c, float* scratch, uint64_t seed, int* status) {
+             int c, float* scratch, uint64_t seed, int* status, const int* only_if) {
+  if (only_if && *only_if == 0) return;   // the fast path succeeded
   extern __shared__ float sm[];
   float* coef = sm;                 // [kq + c]
   float* red = coef + kq + c + 32;  // [64]
@@ -346,14 +347,15 @@ size_t orth_scratch_floats(int64_t m, int zc, int kq) {
 }
 
 cudaError_t launch_orth_block(const float* Z, int64_t ldz, int64_t m, int zc, float* Q, int64_t ldq, int kq,
-                              int c, float* scratch, uint64_t seed, int* status, cudaStream_t st) {
+                              int c, float* scratch, uint64_t seed, int* status, const int* only_if,
+                              cudaStream_t st) {
   if (zc > 64 || c > zc) return cudaErrorInvalidValue;
   size_t smem = sizeof(float) * ((size_t)kq + c + 32 + 64 + 4 * 32 + 64 + m + zc + 8);
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
   cudaFuncSetAttribute(k_orth_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   ProfScope prof("orth_block", st, 0, 0);
   note_launch("orth_block");
-  k_orth_block<<<1, SMALL_THREADS, smem, st>>>(Z, ldz, m, zc, Q, ldq, kq, c, scratch, seed, status);
+  k_orth_block<<<1, SMALL_THREADS, smem, st>>>(Z, ldz, m, zc, Q, ldq, kq, c, scratch, seed, status, only_if);
   return cudaGetLastError();
 }
 
