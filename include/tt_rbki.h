@@ -60,7 +60,9 @@ typedef enum {
   TT_EBREAKDOWN = 4,    /* (device status) a basis block could not be made
                            orthonormal even after random replacement         */
   TT_ENONFINITE = 5,    /* (device status) NaN or Inf found in the input      */
-  TT_EUNSUPPORTED = 6   /* shape outside the supported envelope               */
+  TT_EUNSUPPORTED = 6,  /* shape outside the supported envelope               */
+  TT_ETIMEOUT = 7       /* (device status) a bounded wait inside a kernel
+                           gave up; the results of that call are invalid     */
 } tt_status;
 
 typedef enum {
@@ -150,7 +152,7 @@ TT_API tt_status tt_rbki_decompose_omega(const void* tensor, const int64_t* dims
 /*
  * Reads the device status word of the last decomposition that used
  * `workspace` (synchronises `stream`).  *device_status receives TT_OK,
- * TT_ENONFINITE or TT_EBREAKDOWN.
+ * TT_ENONFINITE, TT_EBREAKDOWN or TT_ETIMEOUT.
  */
 TT_API tt_status tt_rbki_device_status(const void* workspace, void* stream, int* device_status);
 

@@ -10,12 +10,12 @@ import os
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libtt_rbki.so")
 
-TT_OK, TT_EINVAL, TT_ENOMEM, TT_ECUDA, TT_EBREAKDOWN, TT_ENONFINITE, TT_EUNSUPPORTED = range(7)
+TT_OK, TT_EINVAL, TT_ENOMEM, TT_ECUDA, TT_EBREAKDOWN, TT_ENONFINITE, TT_EUNSUPPORTED, TT_ETIMEOUT = range(8)
 TT_F32, TT_BF16 = 0, 1
 TT_PASS_SKETCH, TT_PASS_GRAMAPPLY, TT_PASS_PROJECT, TT_PASS_GRAM = range(4)
 
 STATUS_NAMES = {0: "TT_OK", 1: "TT_EINVAL", 2: "TT_ENOMEM", 3: "TT_ECUDA", 4: "TT_EBREAKDOWN",
-                5: "TT_ENONFINITE", 6: "TT_EUNSUPPORTED"}
+                5: "TT_ENONFINITE", 6: "TT_EUNSUPPORTED", 7: "TT_ETIMEOUT"}
 
 
 class TTOptions(ctypes.Structure):

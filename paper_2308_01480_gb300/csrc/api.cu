@@ -3,6 +3,7 @@
 // caller's stream without a host round trip.
 #include <cstdio>
 #include <cstring>
+#include <type_traits>
 #include <string>
 #include <vector>
 
@@ -44,7 +45,7 @@ struct Plan {
   std::vector<ModePlan> modes;
   // workspace offsets in bytes
   size_t off_status = 0, off_R0 = 0, off_R1 = 0, off_S = 0, off_T = 0, off_part = 0, off_Y = 0,
-         off_Q = 0, off_W = 0, off_U = 0, off_G = 0, off_small = 0, total = 0;
+         off_Q = 0, off_W = 0, off_U = 0, off_G = 0, off_small = 0, off_X = 0, total = 0;
 };
 
 tt_status resolve_options(const tt_options* in, tt_options* out) {
@@ -98,7 +99,8 @@ tt_status build_plan(const int64_t* dims, int d, const int64_t* ranks, int p, in
   int64_t total = 1;
   for (int k = 0; k < d; ++k) total *= dims[k];
   int64_t n = total;
-  size_t maxR = 0, maxS = 0, maxT = 0, maxPart = 0, maxY = 0, maxQ = 0, maxU = 0, maxG = 0, maxSmall = 0;
+  size_t maxR = 0, maxS = 0, maxT = 0, maxPart = 0, maxY = 0, maxQ = 0, maxU = 0, maxG = 0, maxSmall = 0,
+         maxX = 0;
   for (int k = 0; k < d - 1; ++k) {
     ModePlan& M = P.modes[k];
     n /= dims[k];
@@ -144,6 +146,17 @@ tt_status build_plan(const int64_t* dims, int d, const int64_t* ranks, int p, in
       maxSmall = std::max(maxSmall, ttr::rr_fast_scratch_floats(M.m, M.kq, M.r_out));
     }
     maxU = std::max(maxU, (size_t)(M.m * M.r_out));
+    // tensor-core passes (BF16 unfoldings)
+    const int cdt = (k == 0) ? P.storage : P.remainder;
+    if (cdt == TT_BF16 && ttr::tc_shape_ok(M.m, M.n)) {
+      maxPart = std::max(maxPart, (size_t)ttr::tc_cs_partials(M.m, M.n, M.b));
+      maxPart = std::max(maxPart, (size_t)ttr::tc_ga_partials(M.m, M.n, M.b));
+      if (M.m <= 128) maxPart = std::max(maxPart, (size_t)ttr::tc_gram_partials(M.m, M.n));
+      maxX = std::max(maxX, ttr::tc_proj_scratch_bytes(M.m, M.b, 0));
+      maxX = std::max(maxX, ttr::tc_proj_scratch_bytes(M.m, M.r_out, 1));
+      maxX = std::max(maxX, ttr::tc_ga_scratch_bytes(M.m, M.b));
+      if (!M.gram_route) maxT = std::max(maxT, (size_t)(M.b * M.n));
+    }
   }
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + std::max<size_t>(bytes, 1)); return o; };
@@ -159,6 +172,7 @@ tt_status build_plan(const int64_t* dims, int d, const int64_t* ranks, int p, in
   P.off_U = take(maxU * 4);
   P.off_G = take(maxG * 4);
   P.off_small = take(maxSmall * 4);
+  P.off_X = take(maxX);
   P.total = off;
   return TT_OK;
 }
@@ -167,6 +181,10 @@ template <typename TIn>
 tt_status run_mode(const Plan& P, int k, const TIn* C, char* ws, const float* omega_explicit, uint64_t seed,
                    float* core, cudaStream_t st) {
   const ModePlan& M = P.modes[k];
+  constexpr bool kBf16 = std::is_same<TIn, __nv_bfloat16>::value;
+  const bool use_tc = kBf16 && ttr::tc_shape_ok(M.m, M.n);
+  const __nv_bfloat16* Cb = reinterpret_cast<const __nv_bfloat16*>(C);
+  void* xs = ws + P.off_X;
   float* part = (float*)(ws + P.off_part);
   float* U = (float*)(ws + P.off_U);
   float* small = (float*)(ws + P.off_small);
@@ -174,7 +192,10 @@ tt_status run_mode(const Plan& P, int k, const TIn* C, char* ws, const float* om
   const int r = M.r_out;
   if (M.gram_route) {
     float* G = (float*)(ws + P.off_G);
-    TTR_CUDA(ttr::simt_gram<TIn>(C, M.m, M.n, part, G, st));
+    if (use_tc && M.m <= 128)
+      TTR_CUDA(ttr::tc_gram(Cb, M.m, M.n, part, G, status, st));
+    else
+      TTR_CUDA(ttr::simt_gram<TIn>(C, M.m, M.n, part, G, st));
     if (ttr::eig_top_ok((int)M.m))
       TTR_CUDA(ttr::launch_rr_fast(nullptr, G, M.m, M.m, (int)M.m, r, 1, small, U, core, st));
     else
@@ -186,13 +207,18 @@ tt_status run_mode(const Plan& P, int k, const TIn* C, char* ws, const float* om
     float* Q = (float*)(ws + P.off_Q);
     float* W = (float*)(ws + P.off_W);
     const int kq = M.kq;
-    // Alg. 3 step 3: Omega_k, stored transposed (b x n)
+    // Alg. 3 step 3: Omega_k, stored transposed (b x n); BF16 for the tensor cores
+    const int om_dt = use_tc ? TT_BF16 : TT_F32;
     if (omega_explicit)
-      TTR_CUDA(ttr::launch_omega_transpose_any(omega_explicit, M.n, M.b, S, TT_F32, st));
+      TTR_CUDA(ttr::launch_omega_transpose_any(omega_explicit, M.n, M.b, S, om_dt, st));
     else
-      TTR_CUDA(ttr::launch_omega(seed, k, M.n, M.b, S, TT_F32, 1, M.n, st));
+      TTR_CUDA(ttr::launch_omega(seed, k, M.n, M.b, S, om_dt, 1, M.n, st));
     // sketch Y = C Omega, first basis block
-    TTR_CUDA(ttr::simt_cs<TIn>(C, M.m, M.n, S, M.n, M.b, part, Y, M.b, st));
+    if (use_tc)
+      TTR_CUDA(ttr::tc_cs(Cb, M.m, M.n, reinterpret_cast<const __nv_bfloat16*>(S), M.n, M.b, part, Y, M.b, status,
+                          st));
+    else
+      TTR_CUDA(ttr::simt_cs<TIn>(C, M.m, M.n, S, M.n, M.b, part, Y, M.b, st));
     const uint64_t rseed = 0x5EEDull * (uint64_t)(k + 1);
     int* flag = status + 1;
     unsigned* ticket = reinterpret_cast<unsigned*>(status + 2);
@@ -216,7 +242,15 @@ tt_status run_mode(const Plan& P, int k, const TIn* C, char* ws, const float* om
       const float* Xj = Q + col;
       float* Wj = W + col;
       // one Krylov power: W_j = C C^T X_j (also the Rayleigh-Ritz data)
-      if (M.fused_ga) {
+      if (use_tc) {
+        if (ttr::tc_ga_ok(M.m, M.n, cj)) {
+          TTR_CUDA(ttr::tc_ga(Cb, M.m, M.n, Xj, kq, cj, part, Wj, kq, xs, status, st));
+        } else {
+          __nv_bfloat16* Tb = reinterpret_cast<__nv_bfloat16*>(T);
+          TTR_CUDA(ttr::tc_proj(Cb, M.m, M.n, Xj, kq, cj, 0, Tb, 1, M.n, xs, status, st));
+          TTR_CUDA(ttr::tc_cs(Cb, M.m, M.n, Tb, M.n, cj, part, Wj, kq, status, st));
+        }
+      } else if (M.fused_ga) {
         TTR_CUDA(ttr::simt_ga<TIn>(C, M.m, M.n, Xj, kq, cj, part, Wj, kq, st));
       } else {
         TTR_CUDA((ttr::simt_proj<TIn, float>(C, M.m, M.n, Xj, kq, cj, T, M.n, st)));
@@ -235,7 +269,9 @@ tt_status run_mode(const Plan& P, int k, const TIn* C, char* ws, const float* om
   }
   // Alg. 3 step 10: next remainder R = U^T C (r x n)
   char* Rout = ws + ((k % 2 == 0) ? P.off_R0 : P.off_R1);
-  if (P.remainder == TT_BF16)
+  if (use_tc && r <= 32)
+    TTR_CUDA(ttr::tc_proj(Cb, M.m, M.n, U, r, r, 1, Rout, P.remainder == TT_BF16 ? 1 : 0, M.n, xs, status, st));
+  else if (P.remainder == TT_BF16)
     TTR_CUDA((ttr::simt_proj<TIn, __nv_bfloat16>(C, M.m, M.n, U, r, r, (__nv_bfloat16*)Rout, M.n, st)));
   else
     TTR_CUDA((ttr::simt_proj<TIn, float>(C, M.m, M.n, U, r, r, (float*)Rout, M.n, st)));
@@ -385,70 +421,106 @@ tt_status tt_omega_generate(uint64_t seed, int mode, int64_t n, int b, void* out
   return TT_OK;
 }
 
-tt_status tt_pass_workspace_size(int op, int64_t m, int64_t n, int b, int c_dtype, size_t* bytes) {
-  if (!bytes) return fail(TT_EINVAL, "bytes is NULL");
+struct PassLayout {
+  size_t part = 0, sbuf = 0, xt = 0, status = 0, total = 0;
+  bool tc = false, fused = false;
+};
+
+static tt_status pass_layout(int op, int64_t m, int64_t n, int b, int c_dtype, PassLayout* L) {
   if (m < 1 || n < 1) return fail(TT_EINVAL, "bad shape");
   if (c_dtype != TT_F32 && c_dtype != TT_BF16) return fail(TT_EINVAL, "bad dtype");
-  size_t part = 0, sbuf = 0;
+  if (op != TT_PASS_GRAM && (b < 1 || b > 64)) return fail(TT_EUNSUPPORTED, "b must be in [1, 64]");
+  size_t part = 0, sbuf = 0, xt = 0;
+  const bool tc = c_dtype == TT_BF16 && ttr::tc_shape_ok(m, n);
+  L->tc = tc;
   switch (op) {
     case TT_PASS_SKETCH:
-      if (b < 1 || b > 64) return fail(TT_EUNSUPPORTED, "b must be in [1, 64]");
-      part = ttr::simt_cs_partials(m, n, b);
+      part = tc ? ttr::tc_cs_partials(m, n, b) : ttr::simt_cs_partials(m, n, b);
       sbuf = (size_t)b * n;
       break;
     case TT_PASS_GRAMAPPLY:
-      if (b < 1 || b > 64) return fail(TT_EUNSUPPORTED, "b must be in [1, 64]");
-      if (ttr::simt_ga_fused_ok(m, b)) {
-        part = ttr::simt_ga_partials(m, n, b);
+      if (tc) {
+        L->fused = ttr::tc_ga_ok(m, n, b);
+        part = L->fused ? ttr::tc_ga_partials(m, n, b) : ttr::tc_cs_partials(m, n, b);
+        if (!L->fused) sbuf = (size_t)b * n;
+        xt = std::max(ttr::tc_ga_scratch_bytes(m, b), ttr::tc_proj_scratch_bytes(m, b, 0));
       } else {
-        part = ttr::simt_cs_partials(m, n, b);
-        sbuf = (size_t)b * n;
+        L->fused = ttr::simt_ga_fused_ok(m, b);
+        part = L->fused ? ttr::simt_ga_partials(m, n, b) : ttr::simt_cs_partials(m, n, b);
+        if (!L->fused) sbuf = (size_t)b * n;
       }
       break;
     case TT_PASS_PROJECT:
-      if (b < 1 || b > 64) return fail(TT_EUNSUPPORTED, "b must be in [1, 64]");
+      if (tc) xt = ttr::tc_proj_scratch_bytes(m, b, b <= 32 ? 1 : 0);
       break;
     case TT_PASS_GRAM:
       if (m > 128) return fail(TT_EUNSUPPORTED, "Gram pass needs m <= 128");
-      part = ttr::simt_gram_partials(m, n);
+      part = tc ? ttr::tc_gram_partials(m, n) : ttr::simt_gram_partials(m, n);
       break;
     default:
       return fail(TT_EINVAL, "unknown op");
   }
-  *bytes = align_up(part * 4) + align_up(sbuf * 4) + 256;
+  L->part = 0;
+  L->sbuf = align_up(part * 4);
+  L->xt = L->sbuf + align_up(sbuf * 4);
+  L->status = L->xt + align_up(xt);
+  L->total = L->status + 256;
+  return TT_OK;
+}
+
+tt_status tt_pass_workspace_size(int op, int64_t m, int64_t n, int b, int c_dtype, size_t* bytes) {
+  if (!bytes) return fail(TT_EINVAL, "bytes is NULL");
+  PassLayout L;
+  tt_status s = pass_layout(op, m, n, b, c_dtype, &L);
+  if (s != TT_OK) return s;
+  *bytes = L.total;
   return TT_OK;
 }
 
 tt_status tt_pass(int op, const void* C, int c_dtype, int64_t m, int64_t n, int b, const float* x, void* y,
                   int y_dtype, void* workspace, size_t ws_bytes, void* stream) {
-  size_t need = 0;
-  tt_status s = tt_pass_workspace_size(op, m, n, b, c_dtype, &need);
+  PassLayout L;
+  tt_status s = pass_layout(op, m, n, b, c_dtype, &L);
   if (s != TT_OK) return s;
   if (!C || !y || (op != TT_PASS_GRAM && !x)) return fail(TT_EINVAL, "NULL argument");
-  if (!workspace || ws_bytes < need) return fail(TT_ENOMEM, "workspace too small");
+  if (!workspace || ws_bytes < L.total) return fail(TT_ENOMEM, "workspace too small");
   if (((uintptr_t)workspace & 255) != 0) return fail(TT_EINVAL, "workspace must be 256-byte aligned");
   cudaStream_t st = (cudaStream_t)stream;
-  float* part = (float*)workspace;
-  size_t part_bytes = 0;
-  if (op == TT_PASS_GRAM) part_bytes = align_up(ttr::simt_gram_partials(m, n) * 4);
-  else if (op == TT_PASS_GRAMAPPLY && ttr::simt_ga_fused_ok(m, b)) part_bytes = align_up(ttr::simt_ga_partials(m, n, b) * 4);
-  else part_bytes = align_up(ttr::simt_cs_partials(m, n, b) * 4);
-  float* sbuf = (float*)((char*)workspace + part_bytes);
+  char* ws = (char*)workspace;
+  float* part = (float*)(ws + L.part);
+  float* sbuf = (float*)(ws + L.sbuf);
+  void* xt = ws + L.xt;
+  int* status = (int*)(ws + L.status);
+  TTR_CUDA(cudaMemsetAsync(status, 0, 256, st));
   const bool bf = c_dtype == TT_BF16;
+  const __nv_bfloat16* Cb = (const __nv_bfloat16*)C;
+  __nv_bfloat16* Sb = (__nv_bfloat16*)sbuf;
   switch (op) {
     case TT_PASS_SKETCH:
-      TTR_CUDA(ttr::launch_omega_transpose_any(x, n, b, sbuf, TT_F32, st));
-      if (bf) TTR_CUDA(ttr::simt_cs<__nv_bfloat16>((const __nv_bfloat16*)C, m, n, sbuf, n, b, part, (float*)y, b, st));
-      else TTR_CUDA(ttr::simt_cs<float>((const float*)C, m, n, sbuf, n, b, part, (float*)y, b, st));
+      if (L.tc) {
+        TTR_CUDA(ttr::launch_omega_transpose_any(x, n, b, Sb, TT_BF16, st));
+        TTR_CUDA(ttr::tc_cs(Cb, m, n, Sb, n, b, part, (float*)y, b, status, st));
+      } else {
+        TTR_CUDA(ttr::launch_omega_transpose_any(x, n, b, sbuf, TT_F32, st));
+        if (bf) TTR_CUDA(ttr::simt_cs<__nv_bfloat16>(Cb, m, n, sbuf, n, b, part, (float*)y, b, st));
+        else TTR_CUDA(ttr::simt_cs<float>((const float*)C, m, n, sbuf, n, b, part, (float*)y, b, st));
+      }
       break;
     case TT_PASS_GRAMAPPLY:
-      if (ttr::simt_ga_fused_ok(m, b)) {
-        if (bf) TTR_CUDA(ttr::simt_ga<__nv_bfloat16>((const __nv_bfloat16*)C, m, n, x, b, b, part, (float*)y, b, st));
+      if (L.tc) {
+        if (L.fused) {
+          TTR_CUDA(ttr::tc_ga(Cb, m, n, x, b, b, part, (float*)y, b, xt, status, st));
+        } else {
+          TTR_CUDA(ttr::tc_proj(Cb, m, n, x, b, b, 0, Sb, 1, n, xt, status, st));
+          TTR_CUDA(ttr::tc_cs(Cb, m, n, Sb, n, b, part, (float*)y, b, status, st));
+        }
+      } else if (L.fused) {
+        if (bf) TTR_CUDA(ttr::simt_ga<__nv_bfloat16>(Cb, m, n, x, b, b, part, (float*)y, b, st));
         else TTR_CUDA(ttr::simt_ga<float>((const float*)C, m, n, x, b, b, part, (float*)y, b, st));
       } else {
         if (bf) {
-          TTR_CUDA((ttr::simt_proj<__nv_bfloat16, float>((const __nv_bfloat16*)C, m, n, x, b, b, sbuf, n, st)));
-          TTR_CUDA(ttr::simt_cs<__nv_bfloat16>((const __nv_bfloat16*)C, m, n, sbuf, n, b, part, (float*)y, b, st));
+          TTR_CUDA((ttr::simt_proj<__nv_bfloat16, float>(Cb, m, n, x, b, b, sbuf, n, st)));
+          TTR_CUDA(ttr::simt_cs<__nv_bfloat16>(Cb, m, n, sbuf, n, b, part, (float*)y, b, st));
         } else {
           TTR_CUDA((ttr::simt_proj<float, float>((const float*)C, m, n, x, b, b, sbuf, n, st)));
           TTR_CUDA(ttr::simt_cs<float>((const float*)C, m, n, sbuf, n, b, part, (float*)y, b, st));
@@ -456,16 +528,19 @@ tt_status tt_pass(int op, const void* C, int c_dtype, int64_t m, int64_t n, int 
       }
       break;
     case TT_PASS_PROJECT:
-      if (y_dtype == TT_BF16) {
-        if (bf) TTR_CUDA((ttr::simt_proj<__nv_bfloat16, __nv_bfloat16>((const __nv_bfloat16*)C, m, n, x, b, b, (__nv_bfloat16*)y, n, st)));
+      if (L.tc) {
+        TTR_CUDA(ttr::tc_proj(Cb, m, n, x, b, b, b <= 32 ? 1 : 0, y, y_dtype == TT_BF16 ? 1 : 0, n, xt, status, st));
+      } else if (y_dtype == TT_BF16) {
+        if (bf) TTR_CUDA((ttr::simt_proj<__nv_bfloat16, __nv_bfloat16>(Cb, m, n, x, b, b, (__nv_bfloat16*)y, n, st)));
         else TTR_CUDA((ttr::simt_proj<float, __nv_bfloat16>((const float*)C, m, n, x, b, b, (__nv_bfloat16*)y, n, st)));
       } else {
-        if (bf) TTR_CUDA((ttr::simt_proj<__nv_bfloat16, float>((const __nv_bfloat16*)C, m, n, x, b, b, (float*)y, n, st)));
+        if (bf) TTR_CUDA((ttr::simt_proj<__nv_bfloat16, float>(Cb, m, n, x, b, b, (float*)y, n, st)));
         else TTR_CUDA((ttr::simt_proj<float, float>((const float*)C, m, n, x, b, b, (float*)y, n, st)));
       }
       break;
     case TT_PASS_GRAM:
-      if (bf) TTR_CUDA(ttr::simt_gram<__nv_bfloat16>((const __nv_bfloat16*)C, m, n, part, (float*)y, st));
+      if (L.tc) TTR_CUDA(ttr::tc_gram(Cb, m, n, part, (float*)y, status, st));
+      else if (bf) TTR_CUDA(ttr::simt_gram<__nv_bfloat16>(Cb, m, n, part, (float*)y, st));
       else TTR_CUDA(ttr::simt_gram<float>((const float*)C, m, n, part, (float*)y, st));
       break;
   }

@@ -46,6 +46,27 @@ template <typename TIn>
 cudaError_t simt_ga_with_ctas(const TIn* C, int64_t m, int64_t n, const float* X, int ldx, int b,
                               float* partials, int64_t max_ctas, float* out, int64_t ldo, cudaStream_t st);
 bool simt_ga_fused_ok(int64_t m, int b);
+cudaError_t launch_reduce_partials(const float* P, int S, int64_t rows, int cols, float* out, int64_t ldo,
+                                   cudaStream_t st);
+cudaError_t launch_reduce_partials_grouped(const float* P, int per, int groups, int64_t rows, int cols,
+                                           int64_t group_rows, float* out, int64_t ldo, cudaStream_t st);
+
+// ---- tensor-core streaming passes on BF16 unfoldings (stream_tc.cu)
+bool tc_shape_ok(int64_t m, int64_t n);
+int64_t tc_gram_partials(int64_t m, int64_t n);
+cudaError_t tc_gram(const __nv_bfloat16* C, int64_t m, int64_t n, float* partials, float* out, int* status,
+                    cudaStream_t st);
+int64_t tc_cs_partials(int64_t m, int64_t n, int b);
+cudaError_t tc_cs(const __nv_bfloat16* C, int64_t m, int64_t n, const __nv_bfloat16* S, int64_t lds, int b,
+                  float* partials, float* out, int64_t ldo, int* status, cudaStream_t st);
+size_t tc_proj_scratch_bytes(int64_t m, int b, int split);
+cudaError_t tc_proj(const __nv_bfloat16* C, int64_t m, int64_t n, const float* X, int64_t ldx, int b, int split,
+                    void* S, int s_bf16, int64_t lds, void* scratch, int* status, cudaStream_t st);
+bool tc_ga_ok(int64_t m, int64_t n, int b);
+size_t tc_ga_scratch_bytes(int64_t m, int b);
+int64_t tc_ga_partials(int64_t m, int64_t n, int b);
+cudaError_t tc_ga(const __nv_bfloat16* C, int64_t m, int64_t n, const float* X, int64_t ldx, int b, float* partials,
+                  float* out, int64_t ldo, void* scratch, int* status, cudaStream_t st);
 int64_t simt_ga_partials(int64_t m, int64_t n, int b);   // floats
 int64_t simt_cs_partials(int64_t m, int64_t n, int b);   // floats
 int64_t simt_gram_partials(int64_t m, int64_t n);        // floats

@@ -280,6 +280,22 @@ __global__ void k_reduce_partials(const float* __restrict__ P, int S, int64_t ro
   }
 }
 
+// out[r][c] = sum over the CTAs of r's row group (slot j * groups + g) of
+// their partials; the CTAs of a group write only that group's rows.
+__global__ void k_reduce_grouped(const float* __restrict__ P, int per, int groups, int64_t rows, int cols,
+                                 int64_t group_rows, float* __restrict__ out, int64_t ldo) {
+  const int64_t E = rows * cols;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / cols;
+    const int c = (int)(e % cols);
+    const int g = (int)(r / group_rows);
+    float s = 0.f;
+    for (int j = 0; j < per; ++j) s += P[(int64_t)(j * groups + g) * E + e];
+    out[r * ldo + c] = s;
+  }
+}
+
 // ======================================================================
 // Launchers
 // ======================================================================
@@ -291,6 +307,21 @@ static void reduce_launch(const float* P, int S, int64_t rows, int cols, float* 
   int blocks = (int)imin(ceil_div(E, 256), 1024);
   k_reduce_partials<<<blocks, 256, 0, st>>>(P, S, rows, cols, out, ldo);
   note_launch("reduce_partials");
+}
+
+cudaError_t launch_reduce_partials(const float* P, int S, int64_t rows, int cols, float* out, int64_t ldo,
+                                   cudaStream_t st) {
+  reduce_launch(P, S, rows, cols, out, ldo, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_partials_grouped(const float* P, int per, int groups, int64_t rows, int cols,
+                                           int64_t group_rows, float* out, int64_t ldo, cudaStream_t st) {
+  const int64_t E = rows * cols;
+  note_launch("reduce_partials");
+  k_reduce_grouped<<<(int)imin(ceil_div(E, 256), 1024), 256, 0, st>>>(P, per, groups, rows, cols, group_rows, out,
+                                                                       ldo);
+  return cudaGetLastError();
 }
 
 template <typename TIn, typename TOut>

@@ -1,0 +1,637 @@
+// Tensor-core (tcgen05 + TMA) streaming passes over a BF16 unfolding C
+// (m x n, row-major), FP32 accumulation in Tensor Memory:
+//   gram : G = C C^T                 (m <= 128; exhaustion route)
+//   cs   : Y = C S^T, S is b x n      (sketch C W with S = W^T; second half
+//                                       of a Krylov power for tall C)
+//   proj : S = X^T C (b x n)          (projection U^T C of Alg. 3 step 10,
+//                                       with U split in BF16 hi + lo parts;
+//                                       first half of a power for tall C)
+//   ga   : Y = C (C^T X)              (one Krylov power for m <= 256, each
+//                                       column tile read from HBM once)
+// Column tiles of C arrive by TMA (128-byte swizzle) into a ring of shared
+// memory stages.  Warp 0 issues TMA, warp 1 issues tcgen05.mma from one
+// thread and owns the TMEM allocation, warps 2-5 read TMEM (each warp the
+// 32 lanes of its quarter) for the epilogue.  Every wait is bounded: on a
+// timeout the kernel records TT_ETIMEOUT in the status word, lets its own
+// copies and MMAs drain, frees TMEM and returns.
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "tc.cuh"
+
+namespace ttr {
+
+using namespace tc;
+
+constexpr int TC_THREADS = 192;
+constexpr int SMEM_LIMIT = 227 * 1024;
+
+enum : int { OPK_GRAM = 0, OPK_CS = 1, OPK_PROJ = 2, OPK_GA = 3 };
+
+struct TcParams {
+  int64_t m, n;
+  int b;            // logical output columns (proj: rows of S written)
+  int npad;         // MMA N (multiple of 16)
+  int mb;           // M blocks of 128 rows handled by a CTA (cs, ga)
+  int kb;           // 64-column boxes per tile (1 or 2)
+  int stages;
+  int64_t tiles;    // column tiles of width 64*kb
+  int64_t row_groups;
+  int nchunks;      // proj: 128-row chunks of C per tile
+  int split_hi_lo;  // proj: out = D[:, c] + D[:, c + lo_off]
+  int lo_off;
+  int out_bf16;     // proj: output dtype
+  int64_t ld_out;   // proj: row stride of S
+  void* out;        // proj: S (b x n); others: partials
+  int* status;
+  int stage_bytes;
+  int c_box_bytes;  // bytes of one C box (64 cols x box rows)
+  int c_box_rows;
+  int x_box_bytes;  // proj/ga: one X^T box (64 of m x npad)
+  int s_box_bytes;  // cs: one S box (64 cols x npad)
+  int x_res_bytes;  // ga: resident X^T bytes
+  int t_bytes;      // ga: one T buffer
+  int mpad;         // ga: padded m (multiple of 64)
+};
+
+struct TcShared {
+  uint64_t full[8];
+  uint64_t empty[8];
+  uint64_t dfull[2];
+  uint64_t dempty[2];
+  uint64_t tfull[2];
+  uint64_t tempty[2];
+  uint64_t zfull;
+  uint64_t drain;
+  uint64_t xfull;
+  uint32_t tmem_base;
+  int abort_flag;
+};
+
+__device__ __forceinline__ void tc_abort(TcShared* sh, int* status) {
+  sh->abort_flag = 1;
+  set_status(status, TT_ETIMEOUT);
+}
+
+// ---------------------------------------------------------------- kernel
+template <int OP>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+k_tc_stream(const __grid_constant__ CUtensorMap mapC, const __grid_constant__ CUtensorMap mapB, TcParams p) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* ring = smem;
+  uint8_t* xres = ring + (size_t)p.stages * p.stage_bytes;     // ga: resident X^T
+  uint8_t* tbuf = xres + p.x_res_bytes;                         // ga: T buffers
+  TcShared* sh = reinterpret_cast<TcShared*>(tbuf + 2 * p.t_bytes);
+  volatile int* abortp = &sh->abort_flag;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int S = p.stages;
+  const int row_group = (OP == OPK_CS) ? (int)(blockIdx.x % p.row_groups) : 0;
+  const int cta_in_group = (OP == OPK_CS) ? (int)(blockIdx.x / p.row_groups) : (int)blockIdx.x;
+  const int ctas_in_group = (OP == OPK_CS) ? (int)(gridDim.x / p.row_groups) : (int)gridDim.x;
+  const int64_t row0 = (int64_t)row_group * p.mb * 128;
+  // tiles handled by this CTA: cta_in_group, + ctas_in_group, ...
+  const int64_t my_tiles =
+      (p.tiles > cta_in_group) ? (p.tiles - cta_in_group + ctas_in_group - 1) / ctas_in_group : 0;
+  const uint32_t tmem_cols = (OP == OPK_PROJ) ? 128u : (OP == OPK_GA ? 256u : (p.mb * p.npad <= 32 ? 32u :
+                              p.mb * p.npad <= 64 ? 64u : p.mb * p.npad <= 128 ? 128u : 256u));
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) { mbar_init(&sh->full[s], 1); mbar_init(&sh->empty[s], 1); }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&sh->dfull[i], 1); mbar_init(&sh->dempty[i], 4);
+      mbar_init(&sh->tfull[i], 4); mbar_init(&sh->tempty[i], 1);
+    }
+    mbar_init(&sh->zfull, 1);
+    mbar_init(&sh->drain, 1);
+    mbar_init(&sh->xfull, 1);
+    sh->abort_flag = 0;
+    fence_barrier_init();
+    prefetch_tmap(&mapC);
+    prefetch_tmap(&mapB);
+  }
+  if (warp == 1) {
+    tmem_alloc(&sh->tmem_base, tmem_cols);
+    tmem_relinquish();
+  }
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = sh->tmem_base;
+
+  // =========================================================== producer
+  if (warp == 0) {
+    if (lane == 0) {
+      int64_t last_fill[8];
+      for (int s = 0; s < 8; ++s) last_fill[s] = -1;
+      bool ok = true;
+      if (OP == OPK_GA) {
+        // resident X^T: mpad/64 boxes of (64 x npad)
+        const int nbox = p.mpad / 64;
+        mbar_arrive_expect_tx(&sh->xfull, (uint32_t)(nbox * p.x_box_bytes));
+        for (int i = 0; i < nbox; ++i) tma_load_2d(xres + (size_t)i * p.x_box_bytes, &mapB, &sh->xfull, i * 64, 0);
+      }
+      int64_t fill = 0;
+      const int per_tile = (OP == OPK_PROJ) ? p.nchunks : 1;
+      for (int64_t it = 0; it < my_tiles && ok; ++it) {
+        const int64_t tile = cta_in_group + it * ctas_in_group;
+        for (int ch = 0; ch < per_tile && ok; ++ch, ++fill) {
+          const int s = (int)(fill % S);
+          const uint32_t round = (uint32_t)(fill / S);
+          if (!mbar_wait(&sh->empty[s], (round & 1) ^ 1, abortp)) { tc_abort(sh, p.status); ok = false; break; }
+          uint8_t* st = ring + (size_t)s * p.stage_bytes;
+          const int x0 = (int)(tile * 64 * p.kb);
+          if (OP == OPK_GRAM || OP == OPK_GA) {
+            mbar_arrive_expect_tx(&sh->full[s], (uint32_t)(p.kb * p.c_box_bytes));
+            for (int kb = 0; kb < p.kb; ++kb) tma_load_2d(st + (size_t)kb * p.c_box_bytes, &mapC, &sh->full[s], x0 + 64 * kb, 0);
+          } else if (OP == OPK_CS) {
+            mbar_arrive_expect_tx(&sh->full[s], (uint32_t)(p.mb * p.c_box_bytes + p.s_box_bytes));
+            for (int b = 0; b < p.mb; ++b)
+              tma_load_2d(st + (size_t)b * p.c_box_bytes, &mapC, &sh->full[s], x0, (int)(row0 + 128 * b));
+            tma_load_2d(st + (size_t)p.mb * p.c_box_bytes, &mapB, &sh->full[s], x0, 0);
+          } else {  // PROJ: C chunk (2 boxes of 64 cols x 128 rows) + X^T chunk (2 boxes 64 x npad)
+            mbar_arrive_expect_tx(&sh->full[s], (uint32_t)(2 * p.c_box_bytes + 2 * p.x_box_bytes));
+            for (int kb = 0; kb < 2; ++kb)
+              tma_load_2d(st + (size_t)kb * p.c_box_bytes, &mapC, &sh->full[s], x0 + 64 * kb, ch * 128);
+            for (int kb = 0; kb < 2; ++kb)
+              tma_load_2d(st + 2 * (size_t)p.c_box_bytes + (size_t)kb * p.x_box_bytes, &mapB, &sh->full[s],
+                          ch * 128 + 64 * kb, 0);
+          }
+          last_fill[s] = fill;
+        }
+      }
+      // drain: every issued copy must land before the CTA can exit
+      for (int s = 0; s < S; ++s)
+        if (last_fill[s] >= 0) {
+          int zero = 0;
+          mbar_wait(&sh->full[s], (uint32_t)((last_fill[s] / S) & 1), &zero);
+        }
+      if (OP == OPK_GA) { int zero = 0; mbar_wait(&sh->xfull, 0, &zero); }
+    }
+  }
+  // =========================================================== MMA issuer
+  else if (warp == 1) {
+    if (lane == 0) {
+      bool ok = true;
+      int64_t fill = 0;
+      if (OP == OPK_GRAM) {
+        const uint32_t idesc = idesc_bf16(128, p.npad, 0, 0);
+        for (int64_t it = 0; it < my_tiles && ok; ++it, ++fill) {
+          const int s = (int)(fill % S);
+          if (!mbar_wait(&sh->full[s], (uint32_t)((fill / S) & 1), abortp)) { tc_abort(sh, p.status); ok = false; break; }
+          tc_fence_after();
+          const uint32_t base = smem_u32(ring + (size_t)s * p.stage_bytes);
+          for (int ks = 0; ks < 4 * p.kb; ++ks) {
+            const uint32_t a = base + (ks >> 2) * p.c_box_bytes + (ks & 3) * 32;
+            const uint64_t da = smem_desc(a, 16, 1024, SW_128B);
+            mma_bf16(tmem, da, da, idesc, (it > 0 || ks > 0) ? 1u : 0u);
+          }
+          mma_commit(&sh->empty[s]);
+        }
+        mma_commit(&sh->zfull);
+      } else if (OP == OPK_CS) {
+        const uint32_t idesc = idesc_bf16(128, p.npad, 0, 0);
+        for (int64_t it = 0; it < my_tiles && ok; ++it, ++fill) {
+          const int s = (int)(fill % S);
+          if (!mbar_wait(&sh->full[s], (uint32_t)((fill / S) & 1), abortp)) { tc_abort(sh, p.status); ok = false; break; }
+          tc_fence_after();
+          const uint32_t base = smem_u32(ring + (size_t)s * p.stage_bytes);
+          const uint32_t sb = base + p.mb * p.c_box_bytes;
+          for (int b = 0; b < p.mb; ++b)
+            for (int ks = 0; ks < 4; ++ks) {
+              const uint64_t da = smem_desc(base + b * p.c_box_bytes + ks * 32, 16, 1024, SW_128B);
+              const uint64_t db = smem_desc(sb + ks * 32, 16, 1024, SW_128B);
+              mma_bf16(tmem + (uint32_t)(b * p.npad), da, db, idesc, (it > 0 || ks > 0) ? 1u : 0u);
+            }
+          mma_commit(&sh->empty[s]);
+        }
+        mma_commit(&sh->zfull);
+      } else if (OP == OPK_PROJ) {
+        // D1 (128 x npad) = C_tile^T X: A is MN-major (tile columns contiguous)
+        const uint32_t idesc = idesc_bf16(128, p.npad, 1, 0);
+        for (int64_t it = 0; it < my_tiles && ok; ++it) {
+          const int buf = (int)(it & 1);
+          const uint32_t use = (uint32_t)(it >> 1);
+          if (!mbar_wait(&sh->dempty[buf], (use & 1) ^ 1, abortp)) { tc_abort(sh, p.status); ok = false; break; }
+          tc_fence_after();
+          const uint32_t d = tmem + (uint32_t)(buf * 64);
+          for (int ch = 0; ch < p.nchunks && ok; ++ch, ++fill) {
+            const int s = (int)(fill % S);
+            if (!mbar_wait(&sh->full[s], (uint32_t)((fill / S) & 1), abortp)) { tc_abort(sh, p.status); ok = false; break; }
+            tc_fence_after();
+            const uint32_t base = smem_u32(ring + (size_t)s * p.stage_bytes);
+            const uint32_t xb = base + 2 * p.c_box_bytes;
+            for (int ks = 0; ks < 8; ++ks) {
+              // A: rows 16 ks .. 16 ks + 15 of the chunk; two 64-column atoms p.c_box_bytes apart
+              const uint64_t da = smem_desc(base + ks * 2048, p.c_box_bytes, 1024, SW_128B);
+              // B: X^T box (npad rows x 64 of m), K offset within the 64-wide atom
+              const uint64_t db = smem_desc(xb + (ks >> 2) * p.x_box_bytes + (ks & 3) * 32, 16, 1024, SW_128B);
+              mma_bf16(d, da, db, idesc, (ch > 0 || ks > 0) ? 1u : 0u);
+            }
+            mma_commit(&sh->empty[s]);
+          }
+          if (ok) mma_commit(&sh->dfull[buf]);
+        }
+      } else {  // OPK_GA
+        const uint32_t idesc1 = idesc_bf16(128, p.npad, 1, 0);   // T = C_tile^T X
+        const uint32_t idesc2 = idesc_bf16(128, p.npad, 0, 1);   // Z += C_tile T (T MN-major)
+        const uint32_t dz = tmem + 128;                           // Z accumulators (mb x npad)
+        if (!mbar_wait(&sh->xfull, 0, abortp)) { tc_abort(sh, p.status); ok = false; }
+        tc_fence_after();
+        const uint32_t xbase = smem_u32(xres);
+        auto gemm1 = [&](int64_t it, int s) {
+          const int buf = (int)(it & 1);
+          const uint32_t d = tmem + (uint32_t)(buf * 64);
+          const uint32_t base = smem_u32(ring + (size_t)s * p.stage_bytes);
+          for (int ks = 0; ks < p.mpad / 16; ++ks) {
+            const uint64_t da = smem_desc(base + ks * 2048, p.c_box_bytes, 1024, SW_128B);
+            const uint64_t db = smem_desc(xbase + (ks >> 2) * p.x_box_bytes + (ks & 3) * 32, 16, 1024, SW_128B);
+            mma_bf16(d, da, db, idesc1, ks > 0 ? 1u : 0u);
+          }
+          mma_commit(&sh->dfull[buf]);
+        };
+        auto gemm2 = [&](int64_t it, int s) {
+          const int buf = (int)(it & 1);
+          const uint32_t base = smem_u32(ring + (size_t)s * p.stage_bytes);
+          const uint32_t tb = smem_u32(tbuf + (size_t)buf * p.t_bytes);
+          for (int b = 0; b < p.mb; ++b)
+            for (int ks = 0; ks < 8; ++ks) {
+              const uint64_t da = smem_desc(base + (ks >> 2) * p.c_box_bytes + b * 16384 + (ks & 3) * 32, 16, 1024,
+                                            SW_128B);
+              // T_j: MN-major, no swizzle: 8x8 core matrices; K groups 128 B apart,
+              // MN groups (8 columns of T) 2048 B apart
+              const uint64_t db = smem_desc(tb + ks * 256, 128, 2048, SW_NONE);
+              mma_bf16(dz + (uint32_t)(b * p.npad), da, db, idesc2, (it > 0 || ks > 0) ? 1u : 0u);
+            }
+          mma_commit(&sh->tempty[buf]);
+          mma_commit(&sh->empty[s]);
+        };
+        int64_t prev_it = -1;
+        int prev_s = 0;
+        for (int64_t it = 0; it < my_tiles && ok; ++it, ++fill) {
+          const int s = (int)(fill % S);
+          const int buf = (int)(it & 1);
+          const uint32_t use = (uint32_t)(it >> 1);
+          if (!mbar_wait(&sh->full[s], (uint32_t)((fill / S) & 1), abortp)) { tc_abort(sh, p.status); ok = false; break; }
+          if (!mbar_wait(&sh->dempty[buf], (use & 1) ^ 1, abortp)) { tc_abort(sh, p.status); ok = false; break; }
+          tc_fence_after();
+          gemm1(it, s);
+          if (prev_it >= 0) {
+            const uint32_t pu = (uint32_t)(prev_it >> 1);
+            if (!mbar_wait(&sh->tfull[prev_it & 1], pu & 1, abortp)) { tc_abort(sh, p.status); ok = false; break; }
+            tc_fence_after();
+            gemm2(prev_it, prev_s);
+          }
+          prev_it = it;
+          prev_s = s;
+        }
+        if (ok && prev_it >= 0) {
+          const uint32_t pu = (uint32_t)(prev_it >> 1);
+          if (!mbar_wait(&sh->tfull[prev_it & 1], pu & 1, abortp)) { tc_abort(sh, p.status); ok = false; }
+          else { tc_fence_after(); gemm2(prev_it, prev_s); }
+        }
+        mma_commit(&sh->zfull);
+      }
+      // drain: all issued MMAs complete before TMEM can be freed
+      mma_commit(&sh->drain);
+      int zero = 0;
+      mbar_wait(&sh->drain, 0, &zero);
+    }
+  }
+  // =========================================================== epilogue
+  else {
+    const int q = warp & 3;                         // TMEM lane quarter of this warp
+    const int lrow = q * 32 + lane;                 // TMEM lane of this thread
+    const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
+    if (OP == OPK_PROJ || OP == OPK_GA) {
+      for (int64_t it = 0; it < my_tiles; ++it) {
+        const int buf = (int)(it & 1);
+        const uint32_t use = (uint32_t)(it >> 1);
+        if (!mbar_wait(&sh->dfull[buf], use & 1, abortp)) { tc_abort(sh, p.status); break; }
+        tc_fence_after();
+        float v[64];
+        for (int c0 = 0; c0 < p.npad; c0 += 16) tmem_ld16(tmem + lane_addr + (uint32_t)(buf * 64 + c0), v + c0);
+        tmem_wait_ld();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sh->dempty[buf]);
+        const int64_t tile = cta_in_group + it * ctas_in_group;
+        const int64_t col = tile * 128 + lrow;
+        if (OP == OPK_PROJ) {
+          if (col < p.n) {
+            for (int c = 0; c < p.b; ++c) {
+              float x = v[c];
+              if (p.split_hi_lo) x += v[c + p.lo_off];
+              if (p.out_bf16)
+                reinterpret_cast<__nv_bfloat16*>(p.out)[(int64_t)c * p.ld_out + col] = __float2bfloat16_rn(x);
+              else
+                reinterpret_cast<float*>(p.out)[(int64_t)c * p.ld_out + col] = x;
+            }
+          }
+        } else {
+          // T_j row lrow (tile column) -> BF16, MN-major core-matrix layout
+          if (!mbar_wait(&sh->tempty[buf], (use & 1) ^ 1, abortp)) { tc_abort(sh, p.status); break; }
+          uint8_t* tb = tbuf + (size_t)buf * p.t_bytes;
+          const int kgrp = lrow >> 3, krow = lrow & 7;
+          for (int g = 0; g < p.npad / 8; ++g) {
+            uint32_t w[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+              const __nv_bfloat162 pr = __floats2bfloat162_rn(v[8 * g + 2 * h], v[8 * g + 2 * h + 1]);
+              w[h] = *reinterpret_cast<const uint32_t*>(&pr);
+            }
+            *reinterpret_cast<uint4*>(tb + (size_t)g * 2048 + kgrp * 128 + krow * 16) = make_uint4(w[0], w[1], w[2], w[3]);
+          }
+          fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&sh->tfull[buf]);
+        }
+      }
+    }
+    if (OP != OPK_PROJ) {
+      // final accumulators -> per-CTA partials (rows of this CTA, FP32)
+      if (mbar_wait(&sh->zfull, 0, abortp)) {
+        tc_fence_after();
+        float* P = reinterpret_cast<float*>(p.out) + (int64_t)blockIdx.x * p.m * p.b;
+        const int mbn = (OP == OPK_GRAM) ? 1 : p.mb;
+        const uint32_t zoff = (OP == OPK_GA) ? 128u : 0u;
+        for (int b = 0; b < mbn; ++b) {
+          float v[64];
+          for (int c0 = 0; c0 < p.npad; c0 += 16)
+            tmem_ld16(tmem + lane_addr + zoff + (uint32_t)(b * p.npad + c0), v + c0);
+          tmem_wait_ld();
+          const int64_t row = row0 + (int64_t)b * 128 + lrow;
+          if (row < p.m && !*abortp) {
+            const int ncol = (OP == OPK_GRAM) ? (int)p.m : p.b;
+            for (int c = 0; c < ncol; ++c) P[row * ncol + c] = v[c];
+          }
+        }
+        tc_fence_before();
+      } else {
+        tc_abort(sh, p.status);
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, tmem_cols);
+  }
+}
+
+// ================================================================ host side
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::mutex g_enc_mu;
+
+cudaError_t get_encoder(PFN_cuTensorMapEncodeTiled_v12000* out) {
+  std::lock_guard<std::mutex> lk(g_enc_mu);
+  if (!g_encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  *out = g_encode;
+  return cudaSuccess;
+}
+
+// 2-D BF16 map over a row-major (rows x cols) array with row stride ld
+// elements; box = (64 columns, box_rows rows); 128-byte swizzle.
+cudaError_t make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc;
+  cudaError_t e = get_encoder(&enc);
+  if (e != cudaSuccess) return e;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+  cuuint32_t box[2] = {64u, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1u, 1u};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+int num_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 148;
+  }
+  return sms;
+}
+
+size_t tc_smem_bytes(const TcParams& p) {
+  return 1024 + (size_t)p.stages * p.stage_bytes + p.x_res_bytes + 2 * (size_t)p.t_bytes + sizeof(TcShared) + 64;
+}
+
+template <int OP>
+cudaError_t launch_tc(const CUtensorMap& mc, const CUtensorMap& mb, const TcParams& p, int ctas, cudaStream_t st) {
+  const size_t smem = tc_smem_bytes(p);
+  if (smem > (size_t)SMEM_LIMIT) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_tc_stream<OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_tc_stream<OP><<<ctas, TC_THREADS, smem, st>>>(mc, mb, p);
+  return cudaGetLastError();
+}
+
+int pad16(int x) { return (x + 15) & ~15; }
+
+// X (m x b FP32, ld ldx) -> X^T (rows x ldt BF16), zero padded; with split,
+// rows [lo_off, lo_off + b) hold bf16(X - bf16(X)).
+__global__ void k_prep_xt(const float* __restrict__ X, int64_t ldx, int64_t m, int b, int split, int lo_off,
+                          int rows, int64_t ldt, __nv_bfloat16* __restrict__ Xt) {
+  const int64_t total = (int64_t)rows * ldt;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / ldt);
+    const int64_t i = e % ldt;
+    float v = 0.f;
+    if (i < m) {
+      if (r < b) {
+        v = __bfloat162float(__float2bfloat16_rn(X[i * ldx + r]));
+      } else if (split && r >= lo_off && r < lo_off + b) {
+        const float x = X[i * ldx + (r - lo_off)];
+        v = x - __bfloat162float(__float2bfloat16_rn(x));
+      }
+    }
+    Xt[e] = __float2bfloat16_rn(v);
+  }
+}
+
+cudaError_t prep_xt(const float* X, int64_t ldx, int64_t m, int b, int split, int lo_off, int rows, int64_t ldt,
+                    __nv_bfloat16* Xt, cudaStream_t st) {
+  const int64_t total = (int64_t)rows * ldt;
+  note_launch("prep_xt");
+  k_prep_xt<<<(int)imin(ceil_div(total, 256), 1024), 256, 0, st>>>(X, ldx, m, b, split, lo_off, rows, ldt, Xt);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- public launchers
+bool tc_shape_ok(int64_t m, int64_t n) { return n % 8 == 0 && n >= 64 && m >= 1 && n < (int64_t(1) << 31); }
+
+int64_t tc_gram_partials(int64_t m, int64_t n) {
+  const int64_t tiles = ceil_div(n, 128);
+  return imin(tiles, num_sms()) * m * m;
+}
+
+cudaError_t tc_gram(const __nv_bfloat16* C, int64_t m, int64_t n, float* partials, float* out, int* status,
+                    cudaStream_t st) {
+  if (m > 128 || !tc_shape_ok(m, n)) return cudaErrorInvalidValue;
+  TcParams p{};
+  p.m = m; p.n = n; p.b = (int)m; p.npad = pad16((int)m); p.mb = 1; p.kb = 2;
+  p.c_box_rows = 128; p.c_box_bytes = 128 * 128;
+  p.stage_bytes = 2 * p.c_box_bytes;
+  p.tiles = ceil_div(n, 128);
+  p.stages = 6;
+  p.out = partials; p.status = status; p.row_groups = 1;
+  CUtensorMap mc;
+  cudaError_t e = make_map(&mc, C, m, n, n, 128);
+  if (e != cudaSuccess) return e;
+  const int ctas = (int)imin(p.tiles, num_sms());
+  {
+    ProfScope prof("gram_tc", st, (double)m * n * 2, 2.0 * m * m * n);
+    note_launch("gram_tc");
+    e = launch_tc<OPK_GRAM>(mc, mc, p, ctas, st);
+  }
+  if (e != cudaSuccess) return e;
+  return launch_reduce_partials(partials, ctas, m, (int)m, out, m, st);
+}
+
+// Y (m x b, ld ldo) = C S^T with S (b x n BF16, row stride lds).
+int64_t tc_cs_partials(int64_t m, int64_t n, int b) {
+  const int64_t groups = ceil_div(m, 512);
+  const int64_t tiles = ceil_div(n, 64);
+  const int64_t per = imax(1, imin(tiles, num_sms() / groups));
+  return groups * per * m * b;
+}
+
+cudaError_t tc_cs(const __nv_bfloat16* C, int64_t m, int64_t n, const __nv_bfloat16* S, int64_t lds, int b,
+                  float* partials, float* out, int64_t ldo, int* status, cudaStream_t st) {
+  if (b > 64 || !tc_shape_ok(m, n) || lds % 8 != 0) return cudaErrorInvalidValue;
+  TcParams p{};
+  p.m = m; p.n = n; p.b = b; p.npad = pad16(b); p.kb = 1;
+  p.row_groups = ceil_div(m, 512);
+  p.mb = (int)imin(4, ceil_div(ceil_div(m, p.row_groups), 128));
+  p.c_box_rows = 128; p.c_box_bytes = 128 * 128;
+  p.s_box_bytes = p.npad * 128;
+  p.stage_bytes = (p.mb * p.c_box_bytes + p.s_box_bytes + 1023) / 1024 * 1024;
+  p.tiles = ceil_div(n, 64);
+  p.stages = (int)imin(8, (SMEM_LIMIT - 4096) / p.stage_bytes);
+  if (p.stages < 2) return cudaErrorInvalidValue;
+  p.out = partials; p.status = status;
+  CUtensorMap mc, ms;
+  cudaError_t e = make_map(&mc, C, m, n, n, 128);
+  if (e == cudaSuccess) e = make_map(&ms, S, b, n, lds, p.npad);
+  if (e != cudaSuccess) return e;
+  const int64_t per = imax(1, imin(p.tiles, num_sms() / p.row_groups));
+  const int ctas = (int)(per * p.row_groups);
+  {
+    ProfScope prof("cs_tc", st, (double)m * n * 2 + (double)b * n * 2, 2.0 * m * n * b);
+    note_launch("cs_tc");
+    e = launch_tc<OPK_CS>(mc, ms, p, ctas, st);
+  }
+  if (e != cudaSuccess) return e;
+  // partial slot = CTA index; rows outside a CTA's row group are not written,
+  // so each group's partials are reduced over its own CTAs
+  return launch_reduce_partials_grouped(partials, (int)per, (int)p.row_groups, m, b, (int64_t)p.mb * 128, out, ldo,
+                                        st);
+}
+
+// S (b x n, row stride lds, BF16 or FP32) = X^T C; X m x b FP32 (ld ldx).
+// With split, X is applied as BF16 hi + lo parts (FP32-accurate products).
+size_t tc_proj_scratch_bytes(int64_t m, int b, int split) {
+  const int rows = split ? 64 : pad16(b);
+  const int64_t ldt = (m + 7) / 8 * 8;
+  return (size_t)rows * ldt * 2 + 256;
+}
+
+cudaError_t tc_proj(const __nv_bfloat16* C, int64_t m, int64_t n, const float* X, int64_t ldx, int b, int split,
+                    void* S, int s_bf16, int64_t lds, void* scratch, int* status, cudaStream_t st) {
+  if (!tc_shape_ok(m, n) || (split ? b > 32 : b > 64)) return cudaErrorInvalidValue;
+  TcParams p{};
+  p.m = m; p.n = n; p.b = b;
+  p.split_hi_lo = split;
+  p.lo_off = split ? 32 : 0;
+  p.npad = split ? 64 : pad16(b);
+  p.kb = 2; p.mb = 1; p.row_groups = 1;
+  p.nchunks = (int)ceil_div(m, 128);
+  p.c_box_rows = 128; p.c_box_bytes = 128 * 128;
+  p.x_box_bytes = p.npad * 128;
+  p.stage_bytes = (2 * p.c_box_bytes + 2 * p.x_box_bytes + 1023) / 1024 * 1024;
+  p.tiles = ceil_div(n, 128);
+  p.stages = (int)imin(8, (SMEM_LIMIT - 4096) / p.stage_bytes);
+  p.out_bf16 = s_bf16; p.ld_out = lds; p.out = S; p.status = status;
+  const int rows = p.npad;
+  const int64_t ldt = (m + 7) / 8 * 8;
+  __nv_bfloat16* Xt = reinterpret_cast<__nv_bfloat16*>(scratch);
+  cudaError_t e = prep_xt(X, ldx, m, b, split, p.lo_off, rows, ldt, Xt, st);
+  if (e != cudaSuccess) return e;
+  CUtensorMap mc, mx;
+  e = make_map(&mc, C, m, n, n, 128);
+  if (e == cudaSuccess) e = make_map(&mx, Xt, rows, m, ldt, p.npad);
+  if (e != cudaSuccess) return e;
+  const int ctas = (int)imin(p.tiles, num_sms());
+  ProfScope prof("proj_tc", st, (double)m * n * 2 + (double)b * n * (s_bf16 ? 2 : 4), 2.0 * m * n * p.npad);
+  note_launch("proj_tc");
+  return launch_tc<OPK_PROJ>(mc, mx, p, ctas, st);
+}
+
+// Y (m x b, ld ldo) = C (C^T X), m <= 256, b <= 64; X m x b FP32 (ld ldx).
+bool tc_ga_ok(int64_t m, int64_t n, int b) { return m <= 256 && b <= 64 && tc_shape_ok(m, n); }
+
+size_t tc_ga_scratch_bytes(int64_t m, int b) {
+  const int64_t ldt = (m + 7) / 8 * 8;
+  return (size_t)pad16(b) * ldt * 2 + 256;
+}
+
+int64_t tc_ga_partials(int64_t m, int64_t n, int b) {
+  return imin(ceil_div(n, 128), num_sms()) * m * b;
+}
+
+cudaError_t tc_ga(const __nv_bfloat16* C, int64_t m, int64_t n, const float* X, int64_t ldx, int b, float* partials,
+                  float* out, int64_t ldo, void* scratch, int* status, cudaStream_t st) {
+  if (!tc_ga_ok(m, n, b)) return cudaErrorInvalidValue;
+  TcParams p{};
+  p.m = m; p.n = n; p.b = b; p.npad = pad16(b);
+  p.kb = 2; p.row_groups = 1;
+  p.mpad = (int)ceil_div(m, 128) * 128;
+  p.mb = p.mpad / 128;
+  p.c_box_rows = p.mpad; p.c_box_bytes = p.mpad * 128;
+  p.x_box_bytes = p.npad * 128;
+  p.x_res_bytes = (p.mpad / 64) * p.x_box_bytes;
+  p.t_bytes = p.npad / 8 * 2048;
+  p.stage_bytes = 2 * p.c_box_bytes;
+  p.tiles = ceil_div(n, 128);
+  const int fixed = 1024 + p.x_res_bytes + 2 * p.t_bytes + (int)sizeof(TcShared) + 64;
+  p.stages = (int)imin(8, (SMEM_LIMIT - fixed) / p.stage_bytes);
+  if (p.stages < 2) return cudaErrorInvalidValue;
+  p.out = partials; p.status = status;
+  const int64_t ldt = (m + 7) / 8 * 8;
+  __nv_bfloat16* Xt = reinterpret_cast<__nv_bfloat16*>(scratch);
+  cudaError_t e = prep_xt(X, ldx, m, b, 0, 0, p.npad, ldt, Xt, st);
+  if (e != cudaSuccess) return e;
+  CUtensorMap mc, mx;
+  e = make_map(&mc, C, m, n, n, p.mpad);
+  if (e == cudaSuccess) e = make_map(&mx, Xt, p.npad, m, ldt, p.npad);
+  if (e != cudaSuccess) return e;
+  const int ctas = (int)imin(p.tiles, num_sms());
+  {
+    ProfScope prof("gram_apply_tc", st, (double)m * n * 2, 4.0 * m * n * b);
+    note_launch("gram_apply_tc");
+    e = launch_tc<OPK_GA>(mc, mx, p, ctas, st);
+  }
+  if (e != cudaSuccess) return e;
+  return launch_reduce_partials(partials, ctas, m, b, out, ldo, st);
+}
+
+}  // namespace ttr

@@ -94,7 +94,16 @@ def test_exact_recovery_fp32(tt, dims, ranks):
     assert oracle.tt_error(A, got) < 2e-5
 
 
-@pytest.mark.parametrize("case", CASES)
+# shapes whose unfoldings take the tensor-core passes in BF16 (n % 8 == 0)
+CASES_TC = [
+    ((24, 32, 40, 16), (6, 8, 4), (6, 8, 4), 4, 3, 0.03),
+    ((48, 64, 64), (10, 12), (10, 12), 6, 2, 0.05),
+    ((20, 40, 40, 32), (15, 15, 5), (15, 15, 5), 5, 2, 0.02),       # m = 600 at mode 2 (two-pass power)
+    ((40, 40, 40, 40), (20, 20, 20), (20, 20, 20), 10, 4, 0.05),
+]
+
+
+@pytest.mark.parametrize("case", CASES + CASES_TC)
 def test_bf16_error_criterion(tt, case):
     dims, gr, ranks, p, q, noise = case
     A = noisy_tt(dims, gr, 31, noise)

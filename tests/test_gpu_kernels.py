@@ -70,8 +70,25 @@ def _host64(t):
     return t.float().cpu().double().numpy()
 
 
+def _bf16(a):
+    """Round-to-nearest-even to bfloat16, returned as float64."""
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(torch.bfloat16).double().numpy()
+
+
+def _tc_path(n, bf16):
+    """BF16 unfoldings whose rows are 16-byte multiples take the tensor-core
+    passes, which round the small operand (W, X, and C^T X inside a Krylov
+    power) to BF16 by design; the projection keeps FP32 accuracy through a
+    hi + lo split of X when b <= 32."""
+    return bf16 and n % 8 == 0 and n >= 64
+
+
+# Shapes with n a multiple of 8 (and n >= 64) take the tensor-core path for
+# BF16 unfoldings; tails are ragged against the 64/128-column tiles.
 SHAPES = [(1, 1, 1), (7, 31, 9), (40, 4097, 30), (129, 31, 1), (256, 2050, 40), (33, 1000, 15),
-          (300, 777, 20), (7, 4097, 40)]
+          (300, 777, 20), (7, 4097, 40),
+          (40, 4104, 30), (256, 2048, 40), (300, 1024, 20), (7, 4104, 40), (129, 1000, 1),
+          (800, 2056, 30), (64, 1032, 64), (128, 4096, 16), (1, 64, 8), (200, 72, 33)]
 
 
 @pytest.mark.parametrize("m,n,b", SHAPES)
@@ -81,7 +98,8 @@ def test_pass_sketch(tt, m, n, b, bf16):
     W = _rand((n, b), 2)
     y = tt.tt_pass(tt.TT_PASS_SKETCH, C, x=torch.from_numpy(W).cuda())
     Ch = _host64(C)
-    ref = Ch @ W.astype(np.float64)
+    Wr = _bf16(W) if _tc_path(n, bf16) else W.astype(np.float64)
+    ref = Ch @ Wr
     bound = np.abs(Ch) @ np.abs(W.astype(np.float64))
     assert np.max(np.abs(_host64(y) - ref)) <= 1e-5 * np.max(bound)
 
@@ -93,9 +111,15 @@ def test_pass_gram_apply(tt, m, n, b, bf16):
     X = _rand((m, b), 4)
     y = tt.tt_pass(tt.TT_PASS_GRAMAPPLY, C, x=torch.from_numpy(X).cuda())
     Ch = _host64(C)
-    ref = Ch @ (Ch.T @ X.astype(np.float64))
     bound = np.abs(Ch) @ (np.abs(Ch).T @ np.abs(X.astype(np.float64)))
-    assert np.max(np.abs(_host64(y) - ref)) <= 1e-5 * np.max(bound)
+    if _tc_path(n, bf16):
+        # X and T = C^T X rounded to BF16; an FP32 T lying within rounding of
+        # a BF16 tie may round the other way, hence the looser factor
+        ref = Ch @ _bf16(Ch.T @ _bf16(X))
+        assert np.max(np.abs(_host64(y) - ref)) <= 2e-4 * np.max(bound)
+    else:
+        ref = Ch @ (Ch.T @ X.astype(np.float64))
+        assert np.max(np.abs(_host64(y) - ref)) <= 1e-5 * np.max(bound)
 
 
 @pytest.mark.parametrize("m,n,b", SHAPES)
@@ -104,7 +128,8 @@ def test_pass_project(tt, m, n, b, bf16):
     C = _as_dev(_rand((m, n), 5), bf16)
     X = _rand((m, b), 6)
     Ch = _host64(C)
-    ref = X.astype(np.float64).T @ Ch
+    Xr = _bf16(X) if (_tc_path(n, bf16) and b > 32) else X.astype(np.float64)
+    ref = Xr.T @ Ch
     bound = np.abs(X.astype(np.float64)).T @ np.abs(Ch)
     y = tt.tt_pass(tt.TT_PASS_PROJECT, C, x=torch.from_numpy(X).cuda())
     assert np.max(np.abs(_host64(y) - ref)) <= 1e-5 * np.max(bound)
@@ -113,7 +138,8 @@ def test_pass_project(tt, m, n, b, bf16):
     assert np.max(np.abs(_host64(yb) - ref)) <= 2 ** -8 * np.max(np.abs(ref)) + 1e-5 * np.max(bound)
 
 
-@pytest.mark.parametrize("m,n", [(1, 1), (7, 31), (40, 4097), (64, 1000), (128, 333), (100, 65)])
+@pytest.mark.parametrize("m,n", [(1, 1), (7, 31), (40, 4097), (64, 1000), (128, 333), (100, 65),
+                                 (40, 4104), (128, 2048), (100, 1000), (1, 64), (17, 8200)])
 @pytest.mark.parametrize("bf16", [False, True])
 def test_pass_gram(tt, m, n, bf16):
     C = _as_dev(_rand((m, n), 7), bf16)
