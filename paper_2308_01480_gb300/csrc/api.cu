@@ -146,6 +146,7 @@ tt_status build_plan(const int64_t* dims, int d, const int64_t* ranks, int p, in
       maxSmall = std::max(maxSmall, ttr::rr_fast_scratch_floats(M.m, M.kq, M.r_out));
     }
     maxU = std::max(maxU, (size_t)(M.m * M.r_out));
+    maxPart = std::max(maxPart, (size_t)(ttr::simt_proj_splits(M.m, M.n) * M.b * M.n));
     // tensor-core passes (BF16 unfoldings)
     const int cdt = (k == 0) ? P.storage : P.remainder;
     if (cdt == TT_BF16 && ttr::tc_shape_ok(M.m, M.n)) {
@@ -253,7 +254,7 @@ tt_status run_mode(const Plan& P, int k, const TIn* C, char* ws, const float* om
       } else if (M.fused_ga) {
         TTR_CUDA(ttr::simt_ga<TIn>(C, M.m, M.n, Xj, kq, cj, part, Wj, kq, st));
       } else {
-        TTR_CUDA((ttr::simt_proj<TIn, float>(C, M.m, M.n, Xj, kq, cj, T, M.n, st)));
+        TTR_CUDA((ttr::simt_proj<TIn, float>(C, M.m, M.n, Xj, kq, cj, T, M.n, st, part)));
         TTR_CUDA(ttr::simt_cs<TIn>(C, M.m, M.n, T, M.n, cj, part, Wj, kq, st));
       }
       if (j + 1 < M.blocks.size()) {
@@ -272,9 +273,9 @@ tt_status run_mode(const Plan& P, int k, const TIn* C, char* ws, const float* om
   if (use_tc && r <= 32)
     TTR_CUDA(ttr::tc_proj(Cb, M.m, M.n, U, r, r, 1, Rout, P.remainder == TT_BF16 ? 1 : 0, M.n, xs, status, st));
   else if (P.remainder == TT_BF16)
-    TTR_CUDA((ttr::simt_proj<TIn, __nv_bfloat16>(C, M.m, M.n, U, r, r, (__nv_bfloat16*)Rout, M.n, st)));
+    TTR_CUDA((ttr::simt_proj<TIn, __nv_bfloat16>(C, M.m, M.n, U, r, r, (__nv_bfloat16*)Rout, M.n, st, part)));
   else
-    TTR_CUDA((ttr::simt_proj<TIn, float>(C, M.m, M.n, U, r, r, (float*)Rout, M.n, st)));
+    TTR_CUDA((ttr::simt_proj<TIn, float>(C, M.m, M.n, U, r, r, (float*)Rout, M.n, st, part)));
   return TT_OK;
 }
 

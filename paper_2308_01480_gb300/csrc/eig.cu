@@ -15,7 +15,7 @@
 
 namespace ttr {
 
-constexpr int EIG_THREADS = 1024;
+constexpr int EIG_THREADS = 256;
 constexpr int EIG_KMAX = 224;   // H (k x (k+1) floats) must fit shared memory
 
 // ------------------------------------------------------------ partial A^T B
@@ -92,62 +92,73 @@ struct EigSmem {
 // stride ld).  Afterwards d/e hold T, and column j of H below the
 // subdiagonal holds the reflector v_j (with implicit leading 1), tau[j] its
 // scale: P_j = I - tau_j v_j v_j^T acting on indices j+1..k-1.
+// Four barriers per column: reflector, v, p = tau A v, rank-2 update.
 __device__ void householder_tridiag(EigSmem& S, int k, int ld) {
   float* H = S.H;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nt = blockDim.x, nw = nt >> 5;
   for (int j = 0; j + 2 < k; ++j) {
-    const int L = k - j - 1;            // reflector length
-    float part = 0.f;
-    for (int i = 1 + tid; i < L; i += blockDim.x) {
-      const float x = H[(j + 1 + i) * ld + j];
-      part = fmaf(x, x, part);
-    }
-    const float sigma = block_sum(part, S.red);
-    if (tid == 0) {
-      const float x0 = H[(j + 1) * ld + j];
-      float t = 0.f, v0 = 1.f, beta = x0;
-      if (sigma > 0.f) {
-        const float mu = sqrtf(x0 * x0 + sigma);
-        v0 = (x0 <= 0.f) ? x0 - mu : -sigma / (x0 + mu);
-        t = 2.f * v0 * v0 / (sigma + v0 * v0);
-        beta = mu;
+    const int L = k - j - 1;                   // reflector length
+    float* col = H + (j + 1) * ld + j;         // x_i = col[i * ld]
+    if (wid == 0) {
+      float part = 0.f;
+      for (int i = 1 + lane; i < L; i += 32) {
+        const float x = col[i * ld];
+        part = fmaf(x, x, part);
       }
-      S.tau[j] = t;
-      S.e[j] = beta;
-      S.d[j] = H[j * ld + j];
-      S.red[40] = (sigma > 0.f) ? 1.f / v0 : 0.f;
+      const float sigma = warp_sum(part);
+      if (lane == 0) {
+        const float x0 = col[0];
+        float t = 0.f, v0 = 1.f, beta = x0;
+        if (sigma > 0.f) {
+          const float mu = sqrtf(x0 * x0 + sigma);
+          v0 = (x0 <= 0.f) ? x0 - mu : -sigma / (x0 + mu);
+          t = 2.f * v0 * v0 / (sigma + v0 * v0);
+          beta = mu;
+        }
+        S.tau[j] = t;
+        S.e[j] = beta;
+        S.d[j] = H[j * ld + j];
+        S.red[40] = (sigma > 0.f) ? 1.f / v0 : 0.f;
+      }
     }
     __syncthreads();
-    const float inv_v0 = S.red[40];
     const float t = S.tau[j];
-    for (int i = tid; i < L; i += blockDim.x) {
-      float vi = (i == 0) ? 1.f : H[(j + 1 + i) * ld + j] * inv_v0;
-      if (t == 0.f) vi = (i == 0) ? 1.f : 0.f;
-      S.v[i] = vi;
-      if (i > 0) H[(j + 1 + i) * ld + j] = vi;     // keep v_j for back-transformation
+    if (t == 0.f) continue;                    // column already reduced
+    const float iv = S.red[40];
+    for (int i = tid; i < L; i += nt) S.v[i] = (i == 0) ? 1.f : col[i * ld] * iv;
+    __syncthreads();
+    // p = t A v, A = H[j+1.., j+1..]; a group of 8 lanes per row
+    {
+      const int grp = tid >> 3, sl = tid & 7, ngrp = nt >> 3;
+      for (int r0 = 0; r0 < L; r0 += ngrp) {
+        const int r = r0 + grp;
+        float s0 = 0.f;
+        if (r < L) {
+          const float* hr = H + (j + 1 + r) * ld + (j + 1);
+          for (int c = sl; c < L; c += 8) s0 = fmaf(hr[c], S.v[c], s0);
+        }
+        s0 += __shfl_xor_sync(0xffffffffu, s0, 4);
+        s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
+        s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
+        if (r < L && sl == 0) S.p[r] = t * s0;
+      }
     }
     __syncthreads();
-    if (t == 0.f) continue;
-    // p = t * A v, A = H[j+1.., j+1..]; one warp per row
-    for (int row = wid; row < L; row += nw) {
-      const float* hr = H + (j + 1 + row) * ld + (j + 1);
-      float s = 0.f;
-      for (int c = lane; c < L; c += 32) s = fmaf(hr[c], S.v[c], s);
-      s = warp_sum(s);
-      if (lane == 0) S.p[row] = t * s;
-    }
-    __syncthreads();
+    // K = t/2 v^T p, computed by every warp
     float kp = 0.f;
-    for (int i = tid; i < L; i += blockDim.x) kp = fmaf(S.v[i], S.p[i], kp);
-    const float K = 0.5f * t * block_sum(kp, S.red);
-    for (int i = tid; i < L; i += blockDim.x) S.p[i] = S.p[i] - K * S.v[i];   // w
-    __syncthreads();
-    // A -= v w^T + w v^T
-    for (int x = tid; x < L * L; x += blockDim.x) {
-      const int r = x / L, c = x % L;
-      float* h = H + (j + 1 + r) * ld + (j + 1 + c);
-      *h -= S.v[r] * S.p[c] + S.p[r] * S.v[c];
+    for (int i = lane; i < L; i += 32) kp = fmaf(S.v[i], S.p[i], kp);
+    const float K = 0.5f * t * warp_sum(kp);
+    // A -= v w^T + w v^T with w = p - K v; warp per row, lanes over columns
+    for (int r = wid; r < L; r += nw) {
+      const float vr = S.v[r], wr = S.p[r] - K * vr;
+      float* hr = H + (j + 1 + r) * ld + (j + 1);
+      for (int c = lane; c < L; c += 32) {
+        const float vc = S.v[c];
+        hr[c] -= vr * (S.p[c] - K * vc) + wr * vc;
+      }
     }
+    // keep v_j below the subdiagonal for the back-transformation
+    for (int i = 1 + tid; i < L; i += nt) col[i * ld] = S.v[i];
     __syncthreads();
   }
   if (tid == 0) {
@@ -170,18 +181,19 @@ __device__ __forceinline__ int sturm_count(const float* d, const float* e2, int 
   if (fabsf(q) < pivmin) q = -pivmin;
   c += q < 0.f;
   for (int i = 1; i < k; ++i) {
-    q = (d[i] - x) - e2[i - 1] / q;
+    q = (d[i] - x) - __fdividef(e2[i - 1], q);
     if (fabsf(q) < pivmin) q = -pivmin;
     c += q < 0.f;
   }
   return c;
 }
 
-// Solves (T - lam I) x = y in place (x holds y on entry), using a pivoted
-// tridiagonal LU written to per-vector scratch w[0..5k).
-__device__ void tri_solve_inverse_iteration(const float* d, const float* e, int k, float lam, float tiny,
-                                            float* x, float* w) {
-  float* u0 = w;
+// LU factorisation with row exchanges of the tridiagonal T - lam I, stored
+// in w[0..5k): reciprocal pivots, the two superdiagonals of the upper factor,
+// the multipliers and the exchange flags.  Tiny pivots are replaced by tiny
+// (the usual inverse-iteration safeguard).
+__device__ void tri_factor(const float* d, const float* e, int k, float lam, float tiny, float* w) {
+  float* r0 = w;
   float* u1 = w + k;
   float* u2 = w + 2 * k;
   float* l = w + 3 * k;
@@ -192,39 +204,50 @@ __device__ void tri_solve_inverse_iteration(const float* d, const float* e, int 
     const float a1 = d[i + 1] - lam, c1 = (i + 2 < k) ? e[i + 1] : 0.f;
     if (fabsf(alpha) >= fabsf(sub)) {
       const float piv = (fabsf(alpha) < tiny) ? copysignf(tiny, alpha) : alpha;
-      const float li = sub / piv;
-      u0[i] = piv; u1[i] = beta; u2[i] = 0.f; l[i] = li; sw[i] = 0.f;
+      const float rp = 1.f / piv;
+      const float li = sub * rp;
+      r0[i] = rp; u1[i] = beta; u2[i] = 0.f; l[i] = li; sw[i] = 0.f;
       alpha = a1 - li * beta;
       beta = c1;
     } else {
       const float li = alpha / sub;
-      u0[i] = (fabsf(sub) < tiny) ? copysignf(tiny, sub) : sub;
-      u1[i] = a1; u2[i] = c1; l[i] = li; sw[i] = 1.f;
+      const float piv = (fabsf(sub) < tiny) ? copysignf(tiny, sub) : sub;
+      r0[i] = 1.f / piv; u1[i] = a1; u2[i] = c1; l[i] = li; sw[i] = 1.f;
       alpha = beta - li * a1;
       beta = -li * c1;
     }
   }
-  u0[k - 1] = (fabsf(alpha) < tiny) ? copysignf(tiny, alpha) : alpha;
-  // forward: apply the row exchanges and multipliers
+  r0[k - 1] = 1.f / ((fabsf(alpha) < tiny) ? copysignf(tiny, alpha) : alpha);
+}
+
+// x <- (T - lam I)^{-1} x with the factors of tri_factor.
+__device__ void tri_solve(const float* w, int k, float* x) {
+  const float* r0 = w;
+  const float* u1 = w + k;
+  const float* u2 = w + 2 * k;
+  const float* l = w + 3 * k;
+  const float* sw = w + 4 * k;
   for (int i = 0; i + 1 < k; ++i) {
     if (sw[i] != 0.f) { const float t = x[i]; x[i] = x[i + 1]; x[i + 1] = t; }
     x[i + 1] -= l[i] * x[i];
   }
-  // back substitution with the upper factor (bandwidth 2)
+  float x1 = 0.f, x2 = 0.f;                 // x[i+1], x[i+2]
   for (int i = k - 1; i >= 0; --i) {
-    float s = x[i];
-    if (i + 1 < k) s -= u1[i] * x[i + 1];
-    if (i + 2 < k) s -= u2[i] * x[i + 2];
-    x[i] = s / u0[i];
+    const float v = (x[i] - u1[i] * x1 - u2[i] * x2) * r0[i];
+    x[i] = v;
+    x2 = x1;
+    x1 = v;
   }
 }
 
 // Top-r eigenpairs of the symmetric k x k matrix held in S.H (ld = k+1).
 // Writes eigenvectors as columns of Vout (k x r, row stride ldv) in global
-// memory and eigenvalues (descending) to S.lam.  scratch: 6 * k * r floats.
+// memory and eigenvalues (descending) to S.lam.  work: 6 * k * r floats,
+// in shared memory whenever it fits (the inverse iterations are dependent
+// chains, so their latency decides the kernel's time).
 __device__ void sym_eig_top(EigSmem& S, int k, int r, float* Vout, int ldv, float* scratch) {
   const int ld = k + 1;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5, nt = blockDim.x;
   householder_tridiag(S, k, ld);
   float* e2 = S.p;                        // reuse: squared off-diagonals
   for (int i = tid; i < k; i += blockDim.x) e2[i] = S.e[i] * S.e[i];
@@ -261,22 +284,29 @@ __device__ void sym_eig_top(EigSmem& S, int k, int r, float* Vout, int ldv, floa
   const float tnorm = fmaxf(S.red[2], FLT_MIN);
   const float pivmin = FLT_MIN * fmaxf(1.f, tnorm * tnorm);
   const float pad = 2.f * FLT_EPSILON * tnorm + pivmin;
-  // bisection: warp w finds the (j)-th largest eigenvalue for j = w, w + nw, ...
-  for (int j = wid; j < r; j += nw) {
-    const int t = k - 1 - j;             // ascending index
-    float lo = glo - pad, hi = ghi + pad;
-    for (int it = 0; it < 12; ++it) {
-      const float x = lo + (hi - lo) * (float)(lane + 1) / 33.f;
-      const int cnt = sturm_count(S.d, e2, k, x, pivmin);
-      const unsigned ge = __ballot_sync(0xffffffffu, cnt >= t + 1);
-      const float xs = __shfl_sync(0xffffffffu, x, ge ? (__ffs(ge) - 1) : 31);
-      const int s = ge ? (__ffs(ge) - 1) : 32;
-      const float xprev = __shfl_sync(0xffffffffu, x, s > 0 ? s - 1 : 0);
-      if (s == 32) lo = xs;                          // all points below: lambda in (x_31, hi)
-      else { hi = xs; if (s > 0) lo = xprev; }
-      if (hi - lo <= 2.f * FLT_EPSILON * fmaxf(fabsf(lo), fabsf(hi)) + pivmin) break;
+  // bisection: a group of 8 lanes per eigenvalue evaluates Sturm counts at
+  // 8 interior points of the current interval (9-fold shrink per round)
+  {
+    const int grp = tid >> 3, sl = tid & 7, ngrp = nt >> 3;
+    const unsigned gmask = 0xFFu << ((lane >> 3) * 8);
+    for (int j0 = 0; j0 < r; j0 += ngrp) {
+      const int j = j0 + grp;
+      const bool active = j < r;
+      const int t = active ? k - 1 - j : 0;    // ascending index
+      float lo = glo - pad, hi = ghi + pad;
+      for (int it = 0; it < 10; ++it) {
+        const float x = lo + (hi - lo) * (float)(sl + 1) / 9.f;
+        const int cnt = active ? sturm_count(S.d, e2, k, x, pivmin) : 0;
+        const unsigned ge = (__ballot_sync(0xffffffffu, cnt >= t + 1) & gmask) >> ((lane >> 3) * 8);
+        const int s = ge ? (__ffs(ge) - 1) : 8;
+        const int base = lane & ~7;
+        const float xs = __shfl_sync(0xffffffffu, x, base + (s < 8 ? s : 7));
+        const float xprev = __shfl_sync(0xffffffffu, x, base + (s > 0 ? s - 1 : 0));
+        if (s == 8) lo = xs;
+        else { hi = xs; if (s > 0) lo = xprev; }
+      }
+      if (active && sl == 0) S.lam[j] = 0.5f * (lo + hi);
     }
-    if (lane == 0) S.lam[j] = 0.5f * (lo + hi);
   }
   __syncthreads();
   // inverse iteration: one thread per wanted eigenvector, vectors in scratch
@@ -286,9 +316,10 @@ __device__ void sym_eig_top(EigSmem& S, int k, int r, float* Vout, int ldv, floa
   for (int j = tid; j < r; j += blockDim.x) {
     float* x = X + (size_t)j * k;
     float* w = Wk + (size_t)j * 5 * k;
+    tri_factor(S.d, S.e, k, S.lam[j], tiny, w);
     for (int i = 0; i < k; ++i) x[i] = 1.f + 0.01f * (float)((i * 7 + j * 13) % 11);
     for (int it = 0; it < 3; ++it) {
-      tri_solve_inverse_iteration(S.d, S.e, k, S.lam[j], tiny, x, w);
+      tri_solve(w, k, x);
       float mx = 0.f;
       for (int i = 0; i < k; ++i) mx = fmaxf(mx, fabsf(x[i]));
       const float sc = mx > 0.f ? 1.f / mx : 0.f;
@@ -297,20 +328,27 @@ __device__ void sym_eig_top(EigSmem& S, int k, int r, float* Vout, int ldv, floa
   }
   __syncthreads();
   // Gram-Schmidt (classical, twice) across the r vectors in descending
-  // eigenvalue order; restores orthogonality inside clusters
+  // eigenvalue order; restores orthogonality inside clusters.  Dots by
+  // groups of 8 lanes.
   float* dots = S.v;                   // [r] (r <= k)
+  const int grp = tid >> 3, sl = tid & 7, ngrp = nt >> 3;
   for (int j = 0; j < r; ++j) {
     float* xj = X + (size_t)j * k;
     for (int pass = 0; pass < 2 && j > 0; ++pass) {
-      for (int i2 = wid; i2 < j; i2 += nw) {
-        const float* xi = X + (size_t)i2 * k;
+      for (int i0 = 0; i0 < j; i0 += ngrp) {
+        const int i2 = i0 + grp;
         float pp = 0.f;
-        for (int i = lane; i < k; i += 32) pp = fmaf(xi[i], xj[i], pp);
-        pp = warp_sum(pp);
-        if (lane == 0) dots[i2] = pp;
+        if (i2 < j) {
+          const float* xi = X + (size_t)i2 * k;
+          for (int i = sl; i < k; i += 8) pp = fmaf(xi[i], xj[i], pp);
+        }
+        pp += __shfl_xor_sync(0xffffffffu, pp, 4);
+        pp += __shfl_xor_sync(0xffffffffu, pp, 2);
+        pp += __shfl_xor_sync(0xffffffffu, pp, 1);
+        if (i2 < j && sl == 0) dots[i2] = pp;
       }
       __syncthreads();
-      for (int i = tid; i < k; i += blockDim.x) {
+      for (int i = tid; i < k; i += nt) {
         float s = xj[i];
         for (int i2 = 0; i2 < j; ++i2) s -= dots[i2] * X[(size_t)i2 * k + i];
         xj[i] = s;
@@ -318,29 +356,37 @@ __device__ void sym_eig_top(EigSmem& S, int k, int r, float* Vout, int ldv, floa
       __syncthreads();
     }
     float pp = 0.f;
-    for (int i = tid; i < k; i += blockDim.x) pp = fmaf(xj[i], xj[i], pp);
+    for (int i = tid; i < k; i += nt) pp = fmaf(xj[i], xj[i], pp);
     const float nrm = sqrtf(block_sum(pp, S.red));
     const float inv = nrm > 0.f ? 1.f / nrm : 0.f;
-    for (int i = tid; i < k; i += blockDim.x) xj[i] *= inv;
+    for (int i = tid; i < k; i += nt) xj[i] *= inv;
     __syncthreads();
   }
-  // back-transformation x <- P_0 P_1 ... P_{k-3} x ; one warp per vector
-  for (int j = wid; j < r; j += nw) {
-    float* x = X + (size_t)j * k;
+  // back-transformation x <- P_0 P_1 ... P_{k-3} x; a group of 8 lanes per
+  // vector, reflectors applied from the last to the first
+  for (int j0 = 0; j0 < r; j0 += ngrp) {
+    const int j = j0 + grp;
+    const bool active = j < r;
+    float* x = X + (size_t)(active ? j : 0) * k;
     for (int h = k - 3; h >= 0; --h) {
       const float t = S.tau[h];
       if (t == 0.f) continue;
       const int L = k - h - 1;
       float s = 0.f;
-      for (int i = lane; i < L; i += 32) {
-        const float vi = (i == 0) ? 1.f : S.H[(h + 1 + i) * ld + h];
-        s = fmaf(vi, x[h + 1 + i], s);
-      }
-      s = warp_sum(s) * t;
-      for (int i = lane; i < L; i += 32) {
-        const float vi = (i == 0) ? 1.f : S.H[(h + 1 + i) * ld + h];
-        x[h + 1 + i] -= s * vi;
-      }
+      if (active)
+        for (int i = sl; i < L; i += 8) {
+          const float vi = (i == 0) ? 1.f : S.H[(h + 1 + i) * ld + h];
+          s = fmaf(vi, x[h + 1 + i], s);
+        }
+      s += __shfl_xor_sync(0xffffffffu, s, 4);
+      s += __shfl_xor_sync(0xffffffffu, s, 2);
+      s += __shfl_xor_sync(0xffffffffu, s, 1);
+      s *= t;
+      if (active)
+        for (int i = sl; i < L; i += 8) {
+          const float vi = (i == 0) ? 1.f : S.H[(h + 1 + i) * ld + h];
+          x[h + 1 + i] -= s * vi;
+        }
       __syncwarp();
     }
   }
@@ -355,7 +401,7 @@ __device__ void sym_eig_top(EigSmem& S, int k, int r, float* Vout, int ldv, floa
 // H (k x k, global, row stride ldh) -> top-r eigenvectors V (k x r, ld r).
 __global__ void __launch_bounds__(EIG_THREADS) k_eig_top(const float* __restrict__ Hin, int64_t ldh, int k, int r,
                                                         float* __restrict__ V, float* __restrict__ scratch,
-                                                        float* __restrict__ evals) {
+                                                        float* __restrict__ evals, int work_in_smem) {
   extern __shared__ float sm[];
   EigSmem S;
   S.H = sm;
@@ -371,7 +417,8 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eig_top(const float* __restrict
     S.H[i * (k + 1) + j] = 0.5f * (Hin[(int64_t)i * ldh + j] + Hin[(int64_t)j * ldh + i]);
   }
   __syncthreads();
-  sym_eig_top(S, k, r, V, r, scratch);
+  float* work = work_in_smem ? (S.lam + ((r + 3) & ~3)) : scratch;
+  sym_eig_top(S, k, r, V, r, work);
   if (evals)
     for (int j = threadIdx.x; j < r; j += blockDim.x) evals[j] = S.lam[j];
 }
@@ -398,20 +445,23 @@ __global__ void __launch_bounds__(256) k_apply_basis(const float* __restrict__ Q
 }
 
 // ------------------------------------------------------------ launchers
-size_t eig_scratch_floats(int k, int r) { return (size_t)k * k + (size_t)6 * k * r + (size_t)k * r + 64; }
+size_t eig_scratch_floats(int k, int r) { return (size_t)k * k + (size_t)7 * k * r + 64; }
 
 bool eig_top_ok(int k) { return k >= 1 && k <= EIG_KMAX; }
 
 static size_t eig_smem(int k, int r) { return sizeof(float) * ((size_t)k * (k + 1) + 5 * (size_t)k + 64 + r + 8); }
+static size_t eig_work_bytes(int k, int r) { return sizeof(float) * 6 * (size_t)k * r; }
 
 cudaError_t launch_eig_top(const float* H, int64_t ldh, int k, int r, float* V, float* scratch, float* evals,
                            cudaStream_t st) {
   if (!eig_top_ok(k) || r > k || r < 1) return cudaErrorInvalidValue;
-  const size_t smem = eig_smem(k, r);
+  size_t smem = eig_smem(k, r);
+  const int work_in_smem = (smem + eig_work_bytes(k, r) + 16 <= 226 * 1024) ? 1 : 0;
+  if (work_in_smem) smem += eig_work_bytes(k, r) + 16;
   cudaFuncSetAttribute(k_eig_top, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   ProfScope prof("eig_top", st, 0, 0);
   note_launch("eig_top");
-  k_eig_top<<<1, EIG_THREADS, smem, st>>>(H, ldh, k, r, V, scratch, evals);
+  k_eig_top<<<1, EIG_THREADS, smem, st>>>(H, ldh, k, r, V, scratch, evals, work_in_smem);
   return cudaGetLastError();
 }
 

@@ -31,9 +31,12 @@ class ProfScope {
 };
 
 // ---- SIMT streaming passes (stream_simt.cu)
+// partials (optional): b x n x simt_proj_splits(m, n) floats enabling the
+// row-split form for tall-thin unfoldings
 template <typename TIn, typename TOut>
 cudaError_t simt_proj(const TIn* C, int64_t m, int64_t n, const float* X, int ldx, int b, TOut* S,
-                      int64_t lds, cudaStream_t st);
+                      int64_t lds, cudaStream_t st, float* partials = nullptr);
+int64_t simt_proj_splits(int64_t m, int64_t n);
 template <typename TIn>
 cudaError_t simt_cs(const TIn* C, int64_t m, int64_t n, const float* S, int64_t lds, int b,
                     float* partials, float* out, int64_t ldo, cudaStream_t st);

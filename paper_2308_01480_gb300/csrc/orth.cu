@@ -55,8 +55,17 @@ __device__ void orth_finish(const OrthArgs& a, int nctas, int prod, int fin, flo
     const int row = e / b;
     const bool need = (row < kq) ? (prod & PROD_QZ) : (prod & PROD_ZZ);
     if (!need) continue;
-    float s = 0.f;
-    for (int c = 0; c < nctas; ++c) s += __ldcg(a.parts + (int64_t)c * E + e);
+    // four independent chains keep several loads in flight; fixed order
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    int c = 0;
+    for (; c + 4 <= nctas; c += 4) {
+      s0 += __ldcg(a.parts + (int64_t)c * E + e);
+      s1 += __ldcg(a.parts + (int64_t)(c + 1) * E + e);
+      s2 += __ldcg(a.parts + (int64_t)(c + 2) * E + e);
+      s3 += __ldcg(a.parts + (int64_t)(c + 3) * E + e);
+    }
+    for (; c < nctas; ++c) s0 += __ldcg(a.parts + (int64_t)c * E + e);
+    const float s = (s0 + s1) + (s2 + s3);
     if (row < kq) a.P[e] = s;
     else G[(row - kq) * (b + 1) + e % b] = s;
   }
@@ -105,19 +114,23 @@ __device__ void orth_finish(const OrthArgs& a, int nctas, int prod, int fin, flo
     }
     __syncthreads();
   }
-  // T = R^{-1} (upper triangular); one warp per column
+  // T = R^{-1} (upper triangular) in shared memory, one warp per column,
+  // then copied out
+  float* Ts = diag0 + 64;              // [b][b]
   const int lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
   for (int j = wid; j < b; j += nw) {
     for (int i = j; i >= 0; --i) {
       float s = 0.f;
-      for (int l = i + 1 + lane; l <= j; l += 32) s = fmaf(G[i * (b + 1) + l], a.T[l * b + j], s);
+      for (int l = i + 1 + lane; l <= j; l += 32) s = fmaf(G[i * (b + 1) + l], Ts[l * b + j], s);
       s = warp_sum(s);
       const float v = ((i == j) ? 1.f : 0.f) - s;
-      if (lane == 0) a.T[i * b + j] = v / G[i * (b + 1) + i];
+      if (lane == 0) Ts[i * b + j] = v / G[i * (b + 1) + i];
       __syncwarp();
     }
-    for (int i = j + 1 + lane; i < b; i += 32) a.T[i * b + j] = 0.f;
+    for (int i = j + 1 + lane; i < b; i += 32) Ts[i * b + j] = 0.f;
   }
+  __syncthreads();
+  for (int e = tid; e < b * b; e += blockDim.x) a.T[e] = Ts[e];
 }
 
 __global__ void __launch_bounds__(ORTH_THREADS) k_orth_phase(OrthArgs a, int in_op, int prod, int fin, int out) {
@@ -208,7 +221,7 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_orth_phase(OrthArgs a, int in_
 
 // ------------------------------------------------------------ launchers
 static int64_t orth_rows(int64_t m, int kq, int b) {
-  int64_t rows = imax(16, ceil_div(m, 64));
+  int64_t rows = imax(32, ceil_div(m, 16));
   const int64_t budget = 180 * 1024 / 4 - (int64_t)kq * b - (int64_t)b * b;
   const int64_t per_row = kq + b;
   rows = imin(rows, imax(1, budget / per_row));
@@ -238,7 +251,7 @@ cudaError_t launch_orth_fast(const float* W, int64_t ldw, int64_t m, int b, floa
   a.ticket = ticket;
   a.flag = flag;
   const size_t smem_main = sizeof(float) * ((size_t)a.rows * (kq + b) + (size_t)kq * b + (size_t)b * b);
-  const size_t smem_fin = sizeof(float) * ((size_t)b * (b + 1) + 128);
+  const size_t smem_fin = sizeof(float) * ((size_t)b * (b + 1) + 128 + (size_t)b * b);
   const size_t smem = smem_main > smem_fin ? smem_main : smem_fin;
   cudaFuncSetAttribute(k_orth_phase, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), st);

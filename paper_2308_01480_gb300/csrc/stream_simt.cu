@@ -18,30 +18,36 @@ namespace ttr {
 
 // ---------------------------------------------------------------- proj
 // S[c][col] = sum_i X[i][c] C[i][col];  256 threads = 16 (cols) x 16 (c).
+// With gridDim.y > 1 each CTA row covers rows [y * rows_per, ...) and writes
+// its partial sums to S + y * split_stride (the tall-thin form).
 template <typename TIn, typename TOut, int VB>
 __global__ void __launch_bounds__(256) k_proj(const TIn* __restrict__ C, int64_t m, int64_t n,
                                               const float* __restrict__ X, int ldx, int b,
-                                              TOut* __restrict__ S, int64_t lds) {
+                                              TOut* __restrict__ S, int64_t lds, int64_t rows_per,
+                                              int64_t split_stride) {
   constexpr int TN = 64, RC = 32;
   __shared__ float Cs[RC][TN];
   __shared__ float Xs[RC][16 * VB];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int64_t col0 = (int64_t)blockIdx.x * TN;
+  const int64_t rbeg = (int64_t)blockIdx.y * rows_per;
+  const int64_t rend = imin(m, rbeg + rows_per);
+  S += (int64_t)blockIdx.y * split_stride;
   float acc[VB][4];
 #pragma unroll
   for (int v = 0; v < VB; ++v)
 #pragma unroll
     for (int u = 0; u < 4; ++u) acc[v][u] = 0.f;
-  for (int64_t i0 = 0; i0 < m; i0 += RC) {
+  for (int64_t i0 = rbeg; i0 < rend; i0 += RC) {
     for (int e = threadIdx.x; e < RC * TN; e += 256) {
       int r = e / TN, c = e % TN;
       int64_t gi = i0 + r, gc = col0 + c;
-      Cs[r][c] = (gi < m && gc < n) ? ld_elem(C, gi * n + gc) : 0.f;
+      Cs[r][c] = (gi < rend && gc < n) ? ld_elem(C, gi * n + gc) : 0.f;
     }
     for (int e = threadIdx.x; e < RC * 16 * VB; e += 256) {
       int r = e / (16 * VB), c = e % (16 * VB);
       int64_t gi = i0 + r;
-      Xs[r][c] = (gi < m && c < b) ? X[gi * ldx + c] : 0.f;
+      Xs[r][c] = (gi < rend && c < b) ? X[gi * ldx + c] : 0.f;
     }
     __syncthreads();
 #pragma unroll 8
@@ -324,21 +330,54 @@ cudaError_t launch_reduce_partials_grouped(const float* P, int per, int groups, 
   return cudaGetLastError();
 }
 
+// S (b x n) = sum over row splits of the partials P[y] (b x n), fixed order.
+template <typename TOut>
+__global__ void k_sum_splits(const float* __restrict__ P, int splits, int b, int64_t n, TOut* __restrict__ S,
+                             int64_t lds) {
+  const int64_t E = (int64_t)b * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+    float acc = 0.f;
+    for (int y = 0; y < splits; ++y) acc += P[(int64_t)y * E + e];
+    st_elem(S, (e / n) * lds + e % n, acc);
+  }
+}
+
+int64_t simt_proj_splits(int64_t m, int64_t n) {
+  if (n > 512 || m < 256) return 1;
+  return imin(ceil_div(m, 64), 64);
+}
+
 template <typename TIn, typename TOut>
 cudaError_t simt_proj(const TIn* C, int64_t m, int64_t n, const float* X, int ldx, int b, TOut* S,
-                      int64_t lds, cudaStream_t st) {
+                      int64_t lds, cudaStream_t st, float* partials) {
+  const int64_t splits = partials ? simt_proj_splits(m, n) : 1;
+  if (splits > 1) {
+    // tall-thin unfolding: rows split across CTAs, then a fixed-order sum
+    const int64_t rows_per = ceil_div(m, splits);
+    dim3 grid((unsigned)ceil_div(n, 64), (unsigned)splits);
+    ProfScope prof("proj_simt", st, (double)m * n * sizeof(TIn) + (double)m * b * 4 + (double)b * n * sizeof(TOut),
+                   2.0 * m * n * b);
+    note_launch("proj_simt", 2);
+#define TTR_PS(VB) k_proj<TIn, float, VB><<<grid, 256, 0, st>>>(C, m, n, X, ldx, b, partials, n, rows_per, (int64_t)b * n)
+    if (b <= 16) TTR_PS(1); else if (b <= 32) TTR_PS(2); else if (b <= 48) TTR_PS(3); else if (b <= 64) TTR_PS(4);
+    else return cudaErrorInvalidValue;
+#undef TTR_PS
+    const int64_t E = (int64_t)b * n;
+    k_sum_splits<TOut><<<(int)imin(ceil_div(E, 256), 256), 256, 0, st>>>(partials, (int)splits, b, n, S, lds);
+    return cudaGetLastError();
+  }
   dim3 grid((unsigned)ceil_div(n, 64));
   ProfScope prof("proj_simt", st, (double)m * n * sizeof(TIn) + (double)m * b * 4 + (double)b * n * sizeof(TOut),
                  2.0 * m * n * b);
   note_launch("proj_simt");
   if (b <= 16)
-    k_proj<TIn, TOut, 1><<<grid, 256, 0, st>>>(C, m, n, X, ldx, b, S, lds);
+    k_proj<TIn, TOut, 1><<<grid, 256, 0, st>>>(C, m, n, X, ldx, b, S, lds, m, 0);
   else if (b <= 32)
-    k_proj<TIn, TOut, 2><<<grid, 256, 0, st>>>(C, m, n, X, ldx, b, S, lds);
+    k_proj<TIn, TOut, 2><<<grid, 256, 0, st>>>(C, m, n, X, ldx, b, S, lds, m, 0);
   else if (b <= 48)
-    k_proj<TIn, TOut, 3><<<grid, 256, 0, st>>>(C, m, n, X, ldx, b, S, lds);
+    k_proj<TIn, TOut, 3><<<grid, 256, 0, st>>>(C, m, n, X, ldx, b, S, lds, m, 0);
   else if (b <= 64)
-    k_proj<TIn, TOut, 4><<<grid, 256, 0, st>>>(C, m, n, X, ldx, b, S, lds);
+    k_proj<TIn, TOut, 4><<<grid, 256, 0, st>>>(C, m, n, X, ldx, b, S, lds, m, 0);
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();
@@ -490,10 +529,10 @@ cudaError_t simt_gram(const TIn* C, int64_t m, int64_t n, float* partials, float
 }
 
 // Explicit instantiations.
-template cudaError_t simt_proj<float, float>(const float*, int64_t, int64_t, const float*, int, int, float*, int64_t, cudaStream_t);
-template cudaError_t simt_proj<float, __nv_bfloat16>(const float*, int64_t, int64_t, const float*, int, int, __nv_bfloat16*, int64_t, cudaStream_t);
-template cudaError_t simt_proj<__nv_bfloat16, float>(const __nv_bfloat16*, int64_t, int64_t, const float*, int, int, float*, int64_t, cudaStream_t);
-template cudaError_t simt_proj<__nv_bfloat16, __nv_bfloat16>(const __nv_bfloat16*, int64_t, int64_t, const float*, int, int, __nv_bfloat16*, int64_t, cudaStream_t);
+template cudaError_t simt_proj<float, float>(const float*, int64_t, int64_t, const float*, int, int, float*, int64_t, cudaStream_t, float*);
+template cudaError_t simt_proj<float, __nv_bfloat16>(const float*, int64_t, int64_t, const float*, int, int, __nv_bfloat16*, int64_t, cudaStream_t, float*);
+template cudaError_t simt_proj<__nv_bfloat16, float>(const __nv_bfloat16*, int64_t, int64_t, const float*, int, int, float*, int64_t, cudaStream_t, float*);
+template cudaError_t simt_proj<__nv_bfloat16, __nv_bfloat16>(const __nv_bfloat16*, int64_t, int64_t, const float*, int, int, __nv_bfloat16*, int64_t, cudaStream_t, float*);
 template cudaError_t simt_cs<float>(const float*, int64_t, int64_t, const float*, int64_t, int, float*, float*, int64_t, cudaStream_t);
 template cudaError_t simt_cs<__nv_bfloat16>(const __nv_bfloat16*, int64_t, int64_t, const float*, int64_t, int, float*, float*, int64_t, cudaStream_t);
 template cudaError_t simt_ga<float>(const float*, int64_t, int64_t, const float*, int, int, float*, float*, int64_t, cudaStream_t);

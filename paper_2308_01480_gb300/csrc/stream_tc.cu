@@ -55,6 +55,9 @@ struct TcParams {
   int x_res_bytes;  // ga: resident X^T bytes
   int t_bytes;      // ga: one T buffer
   int mpad;         // ga: padded m (multiple of 64)
+  int chunk_rows;   // proj: rows of C per chunk (multiple of 16)
+  int x_resident;   // proj: X^T loaded once (single chunk)
+  int slack_bytes;  // shared memory after the ring covering MMA reads past short boxes
 };
 
 struct TcShared {
@@ -83,7 +86,7 @@ k_tc_stream(const __grid_constant__ CUtensorMap mapC, const __grid_constant__ CU
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* ring = smem;
-  uint8_t* xres = ring + (size_t)p.stages * p.stage_bytes;     // ga: resident X^T
+  uint8_t* xres = ring + (size_t)p.stages * p.stage_bytes + p.slack_bytes;   // resident X^T
   uint8_t* tbuf = xres + p.x_res_bytes;                         // ga: T buffers
   TcShared* sh = reinterpret_cast<TcShared*>(tbuf + 2 * p.t_bytes);
   volatile int* abortp = &sh->abort_flag;
@@ -128,7 +131,7 @@ k_tc_stream(const __grid_constant__ CUtensorMap mapC, const __grid_constant__ CU
       int64_t last_fill[8];
       for (int s = 0; s < 8; ++s) last_fill[s] = -1;
       bool ok = true;
-      if (OP == OPK_GA) {
+      if (OP == OPK_GA || (OP == OPK_PROJ && p.x_resident)) {
         // resident X^T: mpad/64 boxes of (64 x npad)
         const int nbox = p.mpad / 64;
         mbar_arrive_expect_tx(&sh->xfull, (uint32_t)(nbox * p.x_box_bytes));
@@ -152,13 +155,14 @@ k_tc_stream(const __grid_constant__ CUtensorMap mapC, const __grid_constant__ CU
             for (int b = 0; b < p.mb; ++b)
               tma_load_2d(st + (size_t)b * p.c_box_bytes, &mapC, &sh->full[s], x0, (int)(row0 + 128 * b));
             tma_load_2d(st + (size_t)p.mb * p.c_box_bytes, &mapB, &sh->full[s], x0, 0);
-          } else {  // PROJ: C chunk (2 boxes of 64 cols x 128 rows) + X^T chunk (2 boxes 64 x npad)
-            mbar_arrive_expect_tx(&sh->full[s], (uint32_t)(2 * p.c_box_bytes + 2 * p.x_box_bytes));
+          } else {  // PROJ: C chunk (2 boxes of 64 cols x chunk_rows) [+ X^T chunk (2 boxes 64 x npad)]
+            const int xb = p.x_resident ? 0 : 2;
+            mbar_arrive_expect_tx(&sh->full[s], (uint32_t)(2 * p.c_box_bytes + xb * p.x_box_bytes));
             for (int kb = 0; kb < 2; ++kb)
-              tma_load_2d(st + (size_t)kb * p.c_box_bytes, &mapC, &sh->full[s], x0 + 64 * kb, ch * 128);
-            for (int kb = 0; kb < 2; ++kb)
+              tma_load_2d(st + (size_t)kb * p.c_box_bytes, &mapC, &sh->full[s], x0 + 64 * kb, ch * p.chunk_rows);
+            for (int kb = 0; kb < xb; ++kb)
               tma_load_2d(st + 2 * (size_t)p.c_box_bytes + (size_t)kb * p.x_box_bytes, &mapB, &sh->full[s],
-                          ch * 128 + 64 * kb, 0);
+                          ch * p.chunk_rows + 64 * kb, 0);
           }
           last_fill[s] = fill;
         }
@@ -169,7 +173,7 @@ k_tc_stream(const __grid_constant__ CUtensorMap mapC, const __grid_constant__ CU
           int zero = 0;
           mbar_wait(&sh->full[s], (uint32_t)((last_fill[s] / S) & 1), &zero);
         }
-      if (OP == OPK_GA) { int zero = 0; mbar_wait(&sh->xfull, 0, &zero); }
+      if (OP == OPK_GA || (OP == OPK_PROJ && p.x_resident)) { int zero = 0; mbar_wait(&sh->xfull, 0, &zero); }
     }
   }
   // =========================================================== MMA issuer
@@ -212,6 +216,11 @@ k_tc_stream(const __grid_constant__ CUtensorMap mapC, const __grid_constant__ CU
       } else if (OP == OPK_PROJ) {
         // D1 (128 x npad) = C_tile^T X: A is MN-major (tile columns contiguous)
         const uint32_t idesc = idesc_bf16(128, p.npad, 1, 0);
+        if (p.x_resident) {
+          if (!mbar_wait(&sh->xfull, 0, abortp)) { tc_abort(sh, p.status); ok = false; }
+          tc_fence_after();
+        }
+        const int ksteps = p.chunk_rows / 16;
         for (int64_t it = 0; it < my_tiles && ok; ++it) {
           const int buf = (int)(it & 1);
           const uint32_t use = (uint32_t)(it >> 1);
@@ -223,8 +232,8 @@ k_tc_stream(const __grid_constant__ CUtensorMap mapC, const __grid_constant__ CU
             if (!mbar_wait(&sh->full[s], (uint32_t)((fill / S) & 1), abortp)) { tc_abort(sh, p.status); ok = false; break; }
             tc_fence_after();
             const uint32_t base = smem_u32(ring + (size_t)s * p.stage_bytes);
-            const uint32_t xb = base + 2 * p.c_box_bytes;
-            for (int ks = 0; ks < 8; ++ks) {
+            const uint32_t xb = p.x_resident ? smem_u32(xres) : base + 2 * p.c_box_bytes;
+            for (int ks = 0; ks < ksteps; ++ks) {
               // A: rows 16 ks .. 16 ks + 15 of the chunk; two 64-column atoms p.c_box_bytes apart
               const uint64_t da = smem_desc(base + ks * 2048, p.c_box_bytes, 1024, SW_128B);
               // B: X^T box (npad rows x 64 of m), K offset within the 64-wide atom
@@ -246,7 +255,7 @@ k_tc_stream(const __grid_constant__ CUtensorMap mapC, const __grid_constant__ CU
           const int buf = (int)(it & 1);
           const uint32_t d = tmem + (uint32_t)(buf * 64);
           const uint32_t base = smem_u32(ring + (size_t)s * p.stage_bytes);
-          for (int ks = 0; ks < p.mpad / 16; ++ks) {
+          for (int ks = 0; ks < p.c_box_rows / 16; ++ks) {
             const uint64_t da = smem_desc(base + ks * 2048, p.c_box_bytes, 1024, SW_128B);
             const uint64_t db = smem_desc(xbase + (ks >> 2) * p.x_box_bytes + (ks & 3) * 32, 16, 1024, SW_128B);
             mma_bf16(d, da, db, idesc1, ks > 0 ? 1u : 0u);
@@ -430,7 +439,16 @@ int num_sms() {
 }
 
 size_t tc_smem_bytes(const TcParams& p) {
-  return 1024 + (size_t)p.stages * p.stage_bytes + p.x_res_bytes + 2 * (size_t)p.t_bytes + sizeof(TcShared) + 64;
+  return 1024 + (size_t)p.stages * p.stage_bytes + p.slack_bytes + p.x_res_bytes + 2 * (size_t)p.t_bytes +
+         sizeof(TcShared) + 64;
+}
+
+// Rows of a C box: the 16-rounded row count when it is below 128.
+int box_rows_for(int64_t m, int cap) { return (int)imin(cap, (m + 15) / 16 * 16); }
+
+int stages_for(const TcParams& p, int maxst) {
+  const size_t fixed = 1024 + (size_t)p.slack_bytes + p.x_res_bytes + 2 * (size_t)p.t_bytes + sizeof(TcShared) + 64;
+  return (int)imin(maxst, (int64_t)((SMEM_LIMIT - fixed) / p.stage_bytes));
 }
 
 template <int OP>
@@ -489,13 +507,14 @@ cudaError_t tc_gram(const __nv_bfloat16* C, int64_t m, int64_t n, float* partial
   if (m > 128 || !tc_shape_ok(m, n)) return cudaErrorInvalidValue;
   TcParams p{};
   p.m = m; p.n = n; p.b = (int)m; p.npad = pad16((int)m); p.mb = 1; p.kb = 2;
-  p.c_box_rows = 128; p.c_box_bytes = 128 * 128;
+  p.c_box_rows = box_rows_for(m, 128); p.c_box_bytes = p.c_box_rows * 128;
   p.stage_bytes = 2 * p.c_box_bytes;
+  p.slack_bytes = 16384;
   p.tiles = ceil_div(n, 128);
-  p.stages = 6;
+  p.stages = stages_for(p, 8);
   p.out = partials; p.status = status; p.row_groups = 1;
   CUtensorMap mc;
-  cudaError_t e = make_map(&mc, C, m, n, n, 128);
+  cudaError_t e = make_map(&mc, C, m, n, n, p.c_box_rows);
   if (e != cudaSuccess) return e;
   const int ctas = (int)imin(p.tiles, num_sms());
   {
@@ -522,15 +541,16 @@ cudaError_t tc_cs(const __nv_bfloat16* C, int64_t m, int64_t n, const __nv_bfloa
   p.m = m; p.n = n; p.b = b; p.npad = pad16(b); p.kb = 1;
   p.row_groups = ceil_div(m, 512);
   p.mb = (int)imin(4, ceil_div(ceil_div(m, p.row_groups), 128));
-  p.c_box_rows = 128; p.c_box_bytes = 128 * 128;
+  p.c_box_rows = box_rows_for(m, 128); p.c_box_bytes = p.c_box_rows * 128;
   p.s_box_bytes = p.npad * 128;
   p.stage_bytes = (p.mb * p.c_box_bytes + p.s_box_bytes + 1023) / 1024 * 1024;
+  p.slack_bytes = 16384;
   p.tiles = ceil_div(n, 64);
-  p.stages = (int)imin(8, (SMEM_LIMIT - 4096) / p.stage_bytes);
+  p.stages = stages_for(p, 8);
   if (p.stages < 2) return cudaErrorInvalidValue;
   p.out = partials; p.status = status;
   CUtensorMap mc, ms;
-  cudaError_t e = make_map(&mc, C, m, n, n, 128);
+  cudaError_t e = make_map(&mc, C, m, n, n, p.c_box_rows);
   if (e == cudaSuccess) e = make_map(&ms, S, b, n, lds, p.npad);
   if (e != cudaSuccess) return e;
   const int64_t per = imax(1, imin(p.tiles, num_sms() / p.row_groups));
@@ -564,12 +584,16 @@ cudaError_t tc_proj(const __nv_bfloat16* C, int64_t m, int64_t n, const float* X
   p.lo_off = split ? 32 : 0;
   p.npad = split ? 64 : pad16(b);
   p.kb = 2; p.mb = 1; p.row_groups = 1;
-  p.nchunks = (int)ceil_div(m, 128);
-  p.c_box_rows = 128; p.c_box_bytes = 128 * 128;
+  p.chunk_rows = box_rows_for(m, 128);
+  p.nchunks = (int)ceil_div(m, p.chunk_rows);
+  p.x_resident = p.nchunks == 1 ? 1 : 0;
+  p.mpad = (int)ceil_div(p.chunk_rows, 64) * 64;
+  p.c_box_rows = p.chunk_rows; p.c_box_bytes = p.chunk_rows * 128;
   p.x_box_bytes = p.npad * 128;
-  p.stage_bytes = (2 * p.c_box_bytes + 2 * p.x_box_bytes + 1023) / 1024 * 1024;
+  p.x_res_bytes = p.x_resident ? (p.mpad / 64) * p.x_box_bytes : 0;
+  p.stage_bytes = (2 * p.c_box_bytes + (p.x_resident ? 0 : 2 * p.x_box_bytes) + 1023) / 1024 * 1024;
   p.tiles = ceil_div(n, 128);
-  p.stages = (int)imin(8, (SMEM_LIMIT - 4096) / p.stage_bytes);
+  p.stages = stages_for(p, 8);
   p.out_bf16 = s_bf16; p.ld_out = lds; p.out = S; p.status = status;
   const int rows = p.npad;
   const int64_t ldt = (m + 7) / 8 * 8;
@@ -577,7 +601,7 @@ cudaError_t tc_proj(const __nv_bfloat16* C, int64_t m, int64_t n, const float* X
   cudaError_t e = prep_xt(X, ldx, m, b, split, p.lo_off, rows, ldt, Xt, st);
   if (e != cudaSuccess) return e;
   CUtensorMap mc, mx;
-  e = make_map(&mc, C, m, n, n, 128);
+  e = make_map(&mc, C, m, n, n, p.chunk_rows);
   if (e == cudaSuccess) e = make_map(&mx, Xt, rows, m, ldt, p.npad);
   if (e != cudaSuccess) return e;
   const int ctas = (int)imin(p.tiles, num_sms());
@@ -604,16 +628,17 @@ cudaError_t tc_ga(const __nv_bfloat16* C, int64_t m, int64_t n, const float* X, 
   TcParams p{};
   p.m = m; p.n = n; p.b = b; p.npad = pad16(b);
   p.kb = 2; p.row_groups = 1;
-  p.mpad = (int)ceil_div(m, 128) * 128;
-  p.mb = p.mpad / 128;
-  p.c_box_rows = p.mpad; p.c_box_bytes = p.mpad * 128;
+  p.c_box_rows = box_rows_for(m, 256);
+  p.mpad = (int)ceil_div(p.c_box_rows, 64) * 64;
+  p.mb = (int)ceil_div(m, 128);
+  p.c_box_bytes = p.c_box_rows * 128;
   p.x_box_bytes = p.npad * 128;
   p.x_res_bytes = (p.mpad / 64) * p.x_box_bytes;
   p.t_bytes = p.npad / 8 * 2048;
   p.stage_bytes = 2 * p.c_box_bytes;
+  p.slack_bytes = 16384;
   p.tiles = ceil_div(n, 128);
-  const int fixed = 1024 + p.x_res_bytes + 2 * p.t_bytes + (int)sizeof(TcShared) + 64;
-  p.stages = (int)imin(8, (SMEM_LIMIT - fixed) / p.stage_bytes);
+  p.stages = stages_for(p, 8);
   if (p.stages < 2) return cudaErrorInvalidValue;
   p.out = partials; p.status = status;
   const int64_t ldt = (m + 7) / 8 * 8;
@@ -621,7 +646,7 @@ cudaError_t tc_ga(const __nv_bfloat16* C, int64_t m, int64_t n, const float* X, 
   cudaError_t e = prep_xt(X, ldx, m, b, 0, 0, p.npad, ldt, Xt, st);
   if (e != cudaSuccess) return e;
   CUtensorMap mc, mx;
-  e = make_map(&mc, C, m, n, n, p.mpad);
+  e = make_map(&mc, C, m, n, n, p.c_box_rows);
   if (e == cudaSuccess) e = make_map(&mx, Xt, p.npad, m, ldt, p.npad);
   if (e != cudaSuccess) return e;
   const int ctas = (int)imin(p.tiles, num_sms());
