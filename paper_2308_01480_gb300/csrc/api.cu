@@ -227,7 +227,10 @@ tt_status run_mode(const Plan& P, int k, const TIn* C, char* ws, const float* om
     // robust path as fallback (run only if the fast path flagged a
     // breakdown); the one-CTA path alone when the dimension cap truncates
     auto orth = [&](const float* Z, int64_t ldz, int zc, int kq0, int c, uint64_t sd) -> tt_status {
-      if (c == zc && ttr::orth_fast_ok(M.m, kq0, zc)) {
+      if (c == zc && ttr::orth_cluster_ok(M.m, kq0, zc)) {
+        TTR_CUDA(ttr::launch_orth_cluster(Z, ldz, M.m, zc, Q, kq, kq0, flag, st));
+        TTR_CUDA(ttr::launch_orth_block(Z, ldz, M.m, zc, Q, kq, kq0, c, small, sd, status, flag, st));
+      } else if (c == zc && ttr::orth_fast_ok(M.m, kq0, zc)) {
         TTR_CUDA(ttr::launch_orth_fast(Z, ldz, M.m, zc, Q, kq, kq0, small, ticket, flag, st));
         TTR_CUDA(ttr::launch_orth_block(Z, ldz, M.m, zc, Q, kq, kq0, c, small, sd, status, flag, st));
       } else {

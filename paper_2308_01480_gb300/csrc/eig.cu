@@ -15,7 +15,7 @@
 
 namespace ttr {
 
-constexpr int EIG_THREADS = 256;
+constexpr int EIG_THREADS = 1024;
 constexpr int EIG_KMAX = 224;   // H (k x (k+1) floats) must fit shared memory
 
 // ------------------------------------------------------------ partial A^T B
@@ -92,73 +92,76 @@ struct EigSmem {
 // stride ld).  Afterwards d/e hold T, and column j of H below the
 // subdiagonal holds the reflector v_j (with implicit leading 1), tau[j] its
 // scale: P_j = I - tau_j v_j v_j^T acting on indices j+1..k-1.
-// Four barriers per column: reflector, v, p = tau A v, rank-2 update.
+// Three barriers per column: warp 0 forms the reflector and v; then
+// p = tau A v (groups of 8 lanes per row); then the rank-2 update
+// A -= v w^T + w v^T with w = p - (tau/2)(v^T p) v (a warp per row).
 __device__ void householder_tridiag(EigSmem& S, int k, int ld) {
   float* H = S.H;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nt = blockDim.x, nw = nt >> 5;
+  const int grp = tid >> 3, sl = tid & 7, ngrp = nt >> 3;
   for (int j = 0; j + 2 < k; ++j) {
     const int L = k - j - 1;                   // reflector length
     float* col = H + (j + 1) * ld + j;         // x_i = col[i * ld]
     if (wid == 0) {
       float part = 0.f;
+#pragma unroll 4
       for (int i = 1 + lane; i < L; i += 32) {
         const float x = col[i * ld];
         part = fmaf(x, x, part);
       }
       const float sigma = warp_sum(part);
+      const float x0 = col[0];
+      float t = 0.f, iv = 0.f, beta = x0;
+      if (sigma > 0.f) {
+        const float mu = sqrtf(x0 * x0 + sigma);
+        const float v0 = (x0 <= 0.f) ? x0 - mu : -sigma / (x0 + mu);
+        t = 2.f * v0 * v0 / (sigma + v0 * v0);
+        beta = mu;
+        iv = 1.f / v0;
+      }
+      if (t != 0.f)
+        for (int i = lane; i < L; i += 32) S.v[i] = (i == 0) ? 1.f : col[i * ld] * iv;
       if (lane == 0) {
-        const float x0 = col[0];
-        float t = 0.f, v0 = 1.f, beta = x0;
-        if (sigma > 0.f) {
-          const float mu = sqrtf(x0 * x0 + sigma);
-          v0 = (x0 <= 0.f) ? x0 - mu : -sigma / (x0 + mu);
-          t = 2.f * v0 * v0 / (sigma + v0 * v0);
-          beta = mu;
-        }
         S.tau[j] = t;
         S.e[j] = beta;
         S.d[j] = H[j * ld + j];
-        S.red[40] = (sigma > 0.f) ? 1.f / v0 : 0.f;
       }
     }
     __syncthreads();
     const float t = S.tau[j];
     if (t == 0.f) continue;                    // column already reduced
-    const float iv = S.red[40];
-    for (int i = tid; i < L; i += nt) S.v[i] = (i == 0) ? 1.f : col[i * ld] * iv;
-    __syncthreads();
-    // p = t A v, A = H[j+1.., j+1..]; a group of 8 lanes per row
-    {
-      const int grp = tid >> 3, sl = tid & 7, ngrp = nt >> 3;
-      for (int r0 = 0; r0 < L; r0 += ngrp) {
-        const int r = r0 + grp;
-        float s0 = 0.f;
-        if (r < L) {
-          const float* hr = H + (j + 1 + r) * ld + (j + 1);
-          for (int c = sl; c < L; c += 8) s0 = fmaf(hr[c], S.v[c], s0);
+    for (int r0 = 0; r0 < L; r0 += ngrp) {
+      const int r = r0 + grp;
+      float s0 = 0.f, s1 = 0.f;
+      if (r < L) {
+        const float* hr = H + (j + 1 + r) * ld + (j + 1);
+        int c = sl;
+        for (; c + 8 < L; c += 16) {
+          s0 = fmaf(hr[c], S.v[c], s0);
+          s1 = fmaf(hr[c + 8], S.v[c + 8], s1);
         }
-        s0 += __shfl_xor_sync(0xffffffffu, s0, 4);
-        s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
-        s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
-        if (r < L && sl == 0) S.p[r] = t * s0;
+        if (c < L) s0 = fmaf(hr[c], S.v[c], s0);
       }
+      s0 += s1;
+      s0 += __shfl_xor_sync(0xffffffffu, s0, 4);
+      s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
+      s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
+      if (r < L && sl == 0) S.p[r] = t * s0;
     }
     __syncthreads();
-    // K = t/2 v^T p, computed by every warp
     float kp = 0.f;
     for (int i = lane; i < L; i += 32) kp = fmaf(S.v[i], S.p[i], kp);
     const float K = 0.5f * t * warp_sum(kp);
-    // A -= v w^T + w v^T with w = p - K v; warp per row, lanes over columns
     for (int r = wid; r < L; r += nw) {
       const float vr = S.v[r], wr = S.p[r] - K * vr;
       float* hr = H + (j + 1 + r) * ld + (j + 1);
+#pragma unroll 4
       for (int c = lane; c < L; c += 32) {
         const float vc = S.v[c];
         hr[c] -= vr * (S.p[c] - K * vc) + wr * vc;
       }
     }
-    // keep v_j below the subdiagonal for the back-transformation
-    for (int i = 1 + tid; i < L; i += nt) col[i * ld] = S.v[i];
+    for (int i = 1 + tid; i < L; i += nt) col[i * ld] = S.v[i];   // keep v_j
     __syncthreads();
   }
   if (tid == 0) {
@@ -284,29 +287,22 @@ __device__ void sym_eig_top(EigSmem& S, int k, int r, float* Vout, int ldv, floa
   const float tnorm = fmaxf(S.red[2], FLT_MIN);
   const float pivmin = FLT_MIN * fmaxf(1.f, tnorm * tnorm);
   const float pad = 2.f * FLT_EPSILON * tnorm + pivmin;
-  // bisection: a group of 8 lanes per eigenvalue evaluates Sturm counts at
-  // 8 interior points of the current interval (9-fold shrink per round)
-  {
-    const int grp = tid >> 3, sl = tid & 7, ngrp = nt >> 3;
-    const unsigned gmask = 0xFFu << ((lane >> 3) * 8);
-    for (int j0 = 0; j0 < r; j0 += ngrp) {
-      const int j = j0 + grp;
-      const bool active = j < r;
-      const int t = active ? k - 1 - j : 0;    // ascending index
-      float lo = glo - pad, hi = ghi + pad;
-      for (int it = 0; it < 10; ++it) {
-        const float x = lo + (hi - lo) * (float)(sl + 1) / 9.f;
-        const int cnt = active ? sturm_count(S.d, e2, k, x, pivmin) : 0;
-        const unsigned ge = (__ballot_sync(0xffffffffu, cnt >= t + 1) & gmask) >> ((lane >> 3) * 8);
-        const int s = ge ? (__ffs(ge) - 1) : 8;
-        const int base = lane & ~7;
-        const float xs = __shfl_sync(0xffffffffu, x, base + (s < 8 ? s : 7));
-        const float xprev = __shfl_sync(0xffffffffu, x, base + (s > 0 ? s - 1 : 0));
-        if (s == 8) lo = xs;
-        else { hi = xs; if (s > 0) lo = xprev; }
-      }
-      if (active && sl == 0) S.lam[j] = 0.5f * (lo + hi);
+  // bisection: a warp per eigenvalue evaluates Sturm counts at 32 interior
+  // points of the current interval (33-fold shrink per round)
+  for (int j = wid; j < r; j += nw) {
+    const int t = k - 1 - j;                   // ascending index
+    float lo = glo - pad, hi = ghi + pad;
+    for (int it = 0; it < 7; ++it) {
+      const float x = lo + (hi - lo) * (float)(lane + 1) * (1.f / 33.f);
+      const int cnt = sturm_count(S.d, e2, k, x, pivmin);
+      const unsigned ge = __ballot_sync(0xffffffffu, cnt >= t + 1);
+      const int sidx = ge ? (__ffs(ge) - 1) : 32;
+      const float xs = __shfl_sync(0xffffffffu, x, sidx < 32 ? sidx : 31);
+      const float xprev = __shfl_sync(0xffffffffu, x, sidx > 0 ? sidx - 1 : 0);
+      if (sidx == 32) lo = xs;
+      else { hi = xs; if (sidx > 0) lo = xprev; }
     }
+    if (lane == 0) S.lam[j] = 0.5f * (lo + hi);
   }
   __syncthreads();
   // inverse iteration: one thread per wanted eigenvector, vectors in scratch
@@ -318,7 +314,7 @@ __device__ void sym_eig_top(EigSmem& S, int k, int r, float* Vout, int ldv, floa
     float* w = Wk + (size_t)j * 5 * k;
     tri_factor(S.d, S.e, k, S.lam[j], tiny, w);
     for (int i = 0; i < k; ++i) x[i] = 1.f + 0.01f * (float)((i * 7 + j * 13) % 11);
-    for (int it = 0; it < 3; ++it) {
+    for (int it = 0; it < 2; ++it) {
       tri_solve(w, k, x);
       float mx = 0.f;
       for (int i = 0; i < k; ++i) mx = fmaxf(mx, fabsf(x[i]));
@@ -328,30 +324,28 @@ __device__ void sym_eig_top(EigSmem& S, int k, int r, float* Vout, int ldv, floa
   }
   __syncthreads();
   // Gram-Schmidt (classical, twice) across the r vectors in descending
-  // eigenvalue order; restores orthogonality inside clusters.  Dots by
-  // groups of 8 lanes.
+  // eigenvalue order; restores orthogonality inside clusters
   float* dots = S.v;                   // [r] (r <= k)
-  const int grp = tid >> 3, sl = tid & 7, ngrp = nt >> 3;
   for (int j = 0; j < r; ++j) {
     float* xj = X + (size_t)j * k;
     for (int pass = 0; pass < 2 && j > 0; ++pass) {
-      for (int i0 = 0; i0 < j; i0 += ngrp) {
-        const int i2 = i0 + grp;
+      for (int i2 = wid; i2 < j; i2 += nw) {
+        const float* xi = X + (size_t)i2 * k;
         float pp = 0.f;
-        if (i2 < j) {
-          const float* xi = X + (size_t)i2 * k;
-          for (int i = sl; i < k; i += 8) pp = fmaf(xi[i], xj[i], pp);
-        }
-        pp += __shfl_xor_sync(0xffffffffu, pp, 4);
-        pp += __shfl_xor_sync(0xffffffffu, pp, 2);
-        pp += __shfl_xor_sync(0xffffffffu, pp, 1);
-        if (i2 < j && sl == 0) dots[i2] = pp;
+        for (int i = lane; i < k; i += 32) pp = fmaf(xi[i], xj[i], pp);
+        pp = warp_sum(pp);
+        if (lane == 0) dots[i2] = pp;
       }
       __syncthreads();
       for (int i = tid; i < k; i += nt) {
-        float s = xj[i];
-        for (int i2 = 0; i2 < j; ++i2) s -= dots[i2] * X[(size_t)i2 * k + i];
-        xj[i] = s;
+        float s0 = xj[i], s1 = 0.f;
+        int i2 = 0;
+        for (; i2 + 1 < j; i2 += 2) {
+          s0 -= dots[i2] * X[(size_t)i2 * k + i];
+          s1 -= dots[i2 + 1] * X[(size_t)(i2 + 1) * k + i];
+        }
+        if (i2 < j) s0 -= dots[i2] * X[(size_t)i2 * k + i];
+        xj[i] = s0 + s1;
       }
       __syncthreads();
     }
@@ -362,31 +356,26 @@ __device__ void sym_eig_top(EigSmem& S, int k, int r, float* Vout, int ldv, floa
     for (int i = tid; i < k; i += nt) xj[i] *= inv;
     __syncthreads();
   }
-  // back-transformation x <- P_0 P_1 ... P_{k-3} x; a group of 8 lanes per
-  // vector, reflectors applied from the last to the first
-  for (int j0 = 0; j0 < r; j0 += ngrp) {
-    const int j = j0 + grp;
-    const bool active = j < r;
-    float* x = X + (size_t)(active ? j : 0) * k;
+  // back-transformation x <- P_0 P_1 ... P_{k-3} x; a warp per vector,
+  // reflectors applied from the last to the first
+  for (int j = wid; j < r; j += nw) {
+    float* x = X + (size_t)j * k;
     for (int h = k - 3; h >= 0; --h) {
       const float t = S.tau[h];
       if (t == 0.f) continue;
       const int L = k - h - 1;
-      float s = 0.f;
-      if (active)
-        for (int i = sl; i < L; i += 8) {
-          const float vi = (i == 0) ? 1.f : S.H[(h + 1 + i) * ld + h];
-          s = fmaf(vi, x[h + 1 + i], s);
-        }
-      s += __shfl_xor_sync(0xffffffffu, s, 4);
-      s += __shfl_xor_sync(0xffffffffu, s, 2);
-      s += __shfl_xor_sync(0xffffffffu, s, 1);
-      s *= t;
-      if (active)
-        for (int i = sl; i < L; i += 8) {
-          const float vi = (i == 0) ? 1.f : S.H[(h + 1 + i) * ld + h];
-          x[h + 1 + i] -= s * vi;
-        }
+      float s0 = 0.f, s1 = 0.f;
+      int i = lane;
+      for (; i + 32 < L; i += 64) {
+        s0 = fmaf((i == 0) ? 1.f : S.H[(h + 1 + i) * ld + h], x[h + 1 + i], s0);
+        s1 = fmaf(S.H[(h + 1 + i + 32) * ld + h], x[h + 1 + i + 32], s1);
+      }
+      if (i < L) s0 = fmaf((i == 0) ? 1.f : S.H[(h + 1 + i) * ld + h], x[h + 1 + i], s0);
+      const float sc = warp_sum(s0 + s1) * t;
+      for (int i2 = lane; i2 < L; i2 += 32) {
+        const float vi = (i2 == 0) ? 1.f : S.H[(h + 1 + i2) * ld + h];
+        x[h + 1 + i2] -= sc * vi;
+      }
       __syncwarp();
     }
   }

@@ -86,6 +86,11 @@ size_t orth_fast_scratch_floats(int64_t m, int kq, int b);
 cudaError_t launch_orth_fast(const float* W, int64_t ldw, int64_t m, int b, float* Q, int64_t ldq, int kq,
                              float* scratch, unsigned* ticket, int* flag, cudaStream_t st);
 
+// ---- block orthonormalisation on one thread-block cluster (orth_cluster.cu)
+bool orth_cluster_ok(int64_t m, int kq, int b);
+cudaError_t launch_orth_cluster(const float* W, int64_t ldw, int64_t m, int b, float* Q, int64_t ldq, int kq,
+                                int* flag, cudaStream_t st);
+
 // ---- Rayleigh-Ritz through a tridiagonal eigensolver (eig.cu)
 bool eig_top_ok(int k);
 size_t rr_fast_scratch_floats(int64_t m, int k, int r);

@@ -15,6 +15,7 @@
 // The shift s = 11 (m b + b (b + 1)) u tr(G) follows Fukaya et al. (2020),
 // with tr(G) bounding ||Z||_2^2.  A Cholesky pivot below 1e-6 of its
 // diagonal raises a flag; the one-CTA robust path then redoes the block.
+#include "chol.cuh"
 #include "common.cuh"
 #include "kernels.h"
 
@@ -93,43 +94,10 @@ __device__ void orth_finish(const OrthArgs& a, int nctas, int prod, int fin, flo
     for (int i = tid; i < b; i += blockDim.x) G[i * (b + 1) + i] += shift;
     __syncthreads();
   }
-  // Cholesky G = R^T R in place (upper triangle of G becomes R); a pivot
-  // below 1e-6 of the block's own diagonal (taken before any shift or
-  // projection) flags the block for the robust path
-  for (int j = 0; j < b; ++j) {
-    float dj = G[j * (b + 1) + j];
-    if (!(dj > 1e-6f * diag0[j])) {
-      if (tid == 0) atomicExch(a.flag, 1);
-      dj = 1.f;
-    }
-    const float rj = sqrtf(dj);
-    __syncthreads();
-    for (int i = j + 1 + tid; i < b; i += blockDim.x) G[j * (b + 1) + i] /= rj;
-    if (tid == 0) G[j * (b + 1) + j] = rj;
-    __syncthreads();
-    const int L = b - j - 1;
-    for (int x = tid; x < L * L; x += blockDim.x) {
-      const int i = j + 1 + x / L, l = j + 1 + x % L;
-      if (l >= i) G[i * (b + 1) + l] -= G[j * (b + 1) + i] * G[j * (b + 1) + l];
-    }
-    __syncthreads();
-  }
-  // T = R^{-1} (upper triangular) in shared memory, one warp per column,
-  // then copied out
-  float* Ts = diag0 + 64;              // [b][b]
-  const int lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
-  for (int j = wid; j < b; j += nw) {
-    for (int i = j; i >= 0; --i) {
-      float s = 0.f;
-      for (int l = i + 1 + lane; l <= j; l += 32) s = fmaf(G[i * (b + 1) + l], Ts[l * b + j], s);
-      s = warp_sum(s);
-      const float v = ((i == j) ? 1.f : 0.f) - s;
-      if (lane == 0) Ts[i * b + j] = v / G[i * (b + 1) + i];
-      __syncwarp();
-    }
-    for (int i = j + 1 + lane; i < b; i += 32) Ts[i * b + j] = 0.f;
-  }
-  __syncthreads();
+  // Cholesky and triangular inverse in shared memory, then T to global
+  float* Rs = diag0 + 64;              // [b][b]
+  float* Ts = Rs + b * b;              // [b][b]
+  chol_inv_cta(G, b + 1, b, diag0, Rs, b, Ts, b, a.flag, true);
   for (int e = tid; e < b * b; e += blockDim.x) a.T[e] = Ts[e];
 }
 
@@ -251,7 +219,7 @@ cudaError_t launch_orth_fast(const float* W, int64_t ldw, int64_t m, int b, floa
   a.ticket = ticket;
   a.flag = flag;
   const size_t smem_main = sizeof(float) * ((size_t)a.rows * (kq + b) + (size_t)kq * b + (size_t)b * b);
-  const size_t smem_fin = sizeof(float) * ((size_t)b * (b + 1) + 128 + (size_t)b * b);
+  const size_t smem_fin = sizeof(float) * ((size_t)b * (b + 1) + 128 + 2 * (size_t)b * b);
   const size_t smem = smem_main > smem_fin ? smem_main : smem_fin;
   cudaFuncSetAttribute(k_orth_phase, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), st);

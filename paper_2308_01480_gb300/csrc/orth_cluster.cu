@@ -1,0 +1,268 @@
+// Block orthonormalisation of one Krylov block (Alg. 3 step 5) in a single
+// launch on one thread-block cluster.
+//
+// The NC CTAs of the cluster split the m rows of the block Z (and of the
+// basis Q).  Each phase transforms the CTA's rows, forms the CTA's share of
+// Q^T Z and/or Z^T Z in its own shared memory, and after one cluster barrier
+// every CTA sums all NC shares in rank order through distributed shared
+// memory (so all CTAs hold identical sums and repeat the small b x b
+// factorisations themselves).  Shares are double-buffered by phase parity,
+// so one barrier per phase suffices.  The sequence is that of orth.cu:
+//   A: Z = W;                 P1 = Q^T Z
+//   B: Z -= Q P1;             P2 = Q^T Z                 (block Gram-Schmidt twice)
+//   C: Z -= Q P2;             R1 = chol(Z^T Z + s I)     (shifted CholeskyQR)
+//   D: Z = Z R1^-1;           P3 = Q^T Z, R2 = chol(Z^T Z - P3^T P3)
+//   E: Z = (Z - Q P3) R2^-1;  R3 = chol(Z^T Z)
+//   F: X = Z R3^-1 -> Q[:, kq:kq+b]
+// (C, D, E, F without Q terms for the first block).  A pivot below 1e-6 of
+// its diagonal sets the breakdown flag for the one-CTA robust path.
+// All products use 4 x 4 register tiles over shared arrays whose row
+// strides are padded to multiples of 4 with zeros.
+#include <cooperative_groups.h>
+
+#include "chol.cuh"
+#include "common.cuh"
+#include "kernels.h"
+
+namespace cg = cooperative_groups;
+
+namespace ttr {
+
+constexpr int OC_THREADS = 512;
+
+struct ClusterOrthArgs {
+  const float* W;
+  int64_t ldw;
+  float* Q;
+  int64_t ldq;
+  int kq;
+  int64_t m;
+  int b;
+  int64_t rows;     // rows per CTA
+  int* flag;
+};
+
+__host__ __device__ inline int pad4(int x) { return (x + 3) & ~3; }
+
+// Shared-memory layout (floats), kp = pad4(kq), bp = pad4(b), rp = pad4(rows):
+//   share[2][(kp + bp) * bp] | P[kp * bp] | G[b * (b + 1)] | T[bp * bp] | R[b * b] (sizes padded to 4)
+//   | diag0[64] | red[64] | Z[rp * bp] | Z2[rp * bp] | Qc[rp * kp]
+__host__ __device__ inline size_t oc_smem_floats(int kq, int b, int64_t rows) {
+  const size_t kp = pad4(kq), bp = pad4(b), rp = pad4((int)rows);
+  return 2 * (kp + bp) * bp + kp * bp + pad4(b * (b + 1)) + bp * bp + pad4(b * b) + 128 + 2 * rp * bp + rp * kp;
+}
+
+// out[t][j] = sum_{i < rows} A[i][t] B[i][j], t < ta (multiple of 4), j < bp;
+// row strides lda, ldb, ldo are multiples of 4 (16-byte aligned rows).
+__device__ void tn_tile(const float* A, int lda, int ta, const float* B, int ldb, int bp, int rows, float* out,
+                        int ldo) {
+  const int tt = ta >> 2, tj = bp >> 2;
+  for (int tile = threadIdx.x; tile < tt * tj; tile += blockDim.x) {
+    const int t0 = (tile / tj) * 4, j0 = (tile % tj) * 4;
+    float acc[4][4] = {};
+    for (int i = 0; i < rows; ++i) {
+      const float4 x = *reinterpret_cast<const float4*>(A + i * lda + t0);
+      const float4 v = *reinterpret_cast<const float4*>(B + i * ldb + j0);
+      const float av[4] = {x.x, x.y, x.z, x.w}, bv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) acc[u][w] = fmaf(av[u], bv[w], acc[u][w]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      *reinterpret_cast<float4*>(out + (t0 + u) * ldo + j0) = make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
+  }
+}
+
+// Y[i][j] = scale * sum_{t < kk} X[i][t] M[t][j] (+ Y0[i][j]), i < rows
+// (multiple of 4), j < bp; row strides multiples of 4.
+__device__ void nn_tile(const float* X, int ldx, int kk, const float* M, int ldm, int rows, int bp, float* Y,
+                        int ldy, const float* Y0, float scale) {
+  const int ti = rows >> 2, tj = bp >> 2;
+  for (int tile = threadIdx.x; tile < ti * tj; tile += blockDim.x) {
+    const int i0 = (tile / tj) * 4, j0 = (tile % tj) * 4;
+    float acc[4][4] = {};
+    for (int t = 0; t < kk; ++t) {
+      const float4 v = *reinterpret_cast<const float4*>(M + t * ldm + j0);
+      const float bv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float x = X[(i0 + u) * ldx + t];
+#pragma unroll
+        for (int w = 0; w < 4; ++w) acc[u][w] = fmaf(x, bv[w], acc[u][w]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      float4 r = make_float4(acc[u][0] * scale, acc[u][1] * scale, acc[u][2] * scale, acc[u][3] * scale);
+      if (Y0) {
+        const float4 y = *reinterpret_cast<const float4*>(Y0 + (i0 + u) * ldy + j0);
+        r.x += y.x; r.y += y.y; r.z += y.z; r.w += y.w;
+      }
+      *reinterpret_cast<float4*>(Y + (i0 + u) * ldy + j0) = r;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(OC_THREADS) k_orth_cluster(ClusterOrthArgs a) {
+  extern __shared__ __align__(16) float sm[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int kq = a.kq, b = a.b, tid = threadIdx.x;
+  const int kp = pad4(kq), bp = pad4(b), rp = pad4((int)a.rows);
+  const unsigned rank = cl.block_rank();
+  const int64_t r0 = (int64_t)rank * a.rows;
+  const int rc = (int)imax(0, imin(a.rows, a.m - r0));
+  const int E = (kp + bp) * bp;
+  float* share0 = sm;
+  float* share1 = share0 + E;
+  float* P = share1 + E;
+  float* G = P + kp * bp;
+  float* T = G + pad4(b * (b + 1));      // every region starts 16-byte aligned
+  float* R = T + bp * bp;
+  float* diag0 = R + pad4(b * b);
+  float* red = diag0 + 64;
+  float* Zc = red + 64;        // current rows
+  float* Zn = Zc + rp * bp;    // scratch rows
+  float* Qc = Zn + rp * bp;
+  const bool report = rank == 0;
+
+  // zero-padded copies of the CTA's rows of Q and W; zero T and P
+  for (int x = tid; x < rp * kp; x += blockDim.x) {
+    const int i = x / kp, t = x % kp;
+    Qc[x] = (i < rc && t < kq) ? a.Q[(r0 + i) * a.ldq + t] : 0.f;
+  }
+  for (int x = tid; x < rp * bp; x += blockDim.x) {
+    const int i = x / bp, j = x % bp;
+    Zc[x] = (i < rc && j < b) ? a.W[(r0 + i) * a.ldw + j] : 0.f;
+    Zn[x] = 0.f;
+  }
+  for (int x = tid; x < bp * bp; x += blockDim.x) T[x] = 0.f;
+  for (int x = tid; x < kp * bp; x += blockDim.x) P[x] = 0.f;
+  __syncthreads();
+
+  int phase = 0;
+  // shares of Q^T Z (rows < kp) and/or Z^T Z (rows kp..kp+bp) over this
+  // CTA's rows, then the rank-ordered sum into P and G
+  auto reduce = [&](bool qz, bool zz) {
+    float* mine = (phase & 1) ? share1 : share0;
+    if (qz) tn_tile(Qc, kp, kp, Zc, bp, bp, rp, mine, bp);
+    if (zz) tn_tile(Zc, bp, bp, Zc, bp, bp, rp, mine + kp * bp, bp);
+    cl.sync();
+    const unsigned nc = cl.num_blocks();
+    const int e0 = qz ? 0 : kp * bp, e1 = zz ? E : kp * bp;
+    for (int e = e0 + tid; e < e1; e += blockDim.x) {
+      float s = 0.f;
+#pragma unroll 8
+      for (unsigned r = 0; r < nc; ++r) s += cl.map_shared_rank(mine, r)[e];
+      const int row = e / bp, j = e % bp;
+      if (row < kp) P[e] = s;
+      else if (row - kp < b && j < b) G[(row - kp) * (b + 1) + j] = s;
+    }
+    __syncthreads();
+    ++phase;
+  };
+  auto swap = [&]() { float* t = Zc; Zc = Zn; Zn = t; };
+  auto sub_q = [&]() {     // Z = Z - Q P
+    nn_tile(Qc, kp, kp, P, bp, rp, bp, Zn, bp, Zc, -1.f);
+    __syncthreads();
+    swap();
+  };
+  auto mul_t = [&]() {     // Z = Z T
+    nn_tile(Zc, bp, bp, T, bp, rp, bp, Zn, bp, nullptr, 1.f);
+    __syncthreads();
+    swap();
+  };
+  auto set_diag0 = [&]() {
+    for (int i = tid; i < b; i += blockDim.x) diag0[i] = G[i * (b + 1) + i];
+    __syncthreads();
+  };
+  auto factor = [&]() { chol_inv_cta(G, b + 1, b, diag0, R, b, T, bp, a.flag, report); };
+
+  if (kq > 0) {
+    reduce(true, false);                       // A
+    sub_q();
+    reduce(true, false);                       // B
+    sub_q();
+  }
+  reduce(false, true);                         // C
+  set_diag0();
+  {
+    float tr = 0.f;
+    for (int i = tid; i < b; i += blockDim.x) tr += G[i * (b + 1) + i];
+    tr = block_sum(tr, red);
+    const float shift = 11.f * ((float)a.m * b + (float)b * (b + 1)) * 5.9604645e-08f * tr;
+    __syncthreads();
+    for (int i = tid; i < b; i += blockDim.x) G[i * (b + 1) + i] += shift;
+  }
+  factor();
+  mul_t();
+  reduce(kq > 0, true);                        // D
+  set_diag0();
+  if (kq > 0) {
+    for (int e = tid; e < b * b; e += blockDim.x) {
+      const int i = e / b, j = e % b;
+      float s = 0.f;
+      for (int t = 0; t < kq; ++t) s = fmaf(P[t * bp + i], P[t * bp + j], s);
+      G[i * (b + 1) + j] -= s;
+    }
+  }
+  factor();
+  if (kq > 0) sub_q();
+  mul_t();
+  reduce(false, true);                         // E
+  set_diag0();
+  factor();
+  mul_t();                                     // F
+  for (int x = tid; x < rc * b; x += blockDim.x) {
+    const int i = x / b, j = x % b;
+    a.Q[(r0 + i) * a.ldq + kq + j] = Zc[i * bp + j];
+  }
+  cl.sync();   // no CTA leaves while others may still read its shares
+}
+
+// ------------------------------------------------------------ launcher
+static int oc_cluster_size(int64_t m) {
+  if (m <= 64) return 1;
+  if (m <= 256) return 4;
+  return 8;
+}
+
+bool orth_cluster_ok(int64_t m, int kq, int b) {
+  if (b > 64 || kq > 256) return false;
+  const int64_t rows = ceil_div(m, oc_cluster_size(m));
+  return oc_smem_floats(kq, b, rows) * 4 <= 200 * 1024;
+}
+
+cudaError_t launch_orth_cluster(const float* W, int64_t ldw, int64_t m, int b, float* Q, int64_t ldq, int kq,
+                                int* flag, cudaStream_t st) {
+  if (!orth_cluster_ok(m, kq, b)) return cudaErrorInvalidValue;
+  ClusterOrthArgs a;
+  a.W = W; a.ldw = ldw; a.Q = Q; a.ldq = ldq; a.kq = kq; a.m = m; a.b = b; a.flag = flag;
+  const int nc = oc_cluster_size(m);
+  a.rows = ceil_div(m, nc);
+  const size_t smem = oc_smem_floats(kq, b, a.rows) * 4;
+  cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_orth_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nc);
+  cfg.blockDim = dim3(OC_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = nc;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  ProfScope prof("orth_cluster", st, 0, 0);
+  note_launch("orth_cluster");
+  e = cudaLaunchKernelEx(&cfg, k_orth_cluster, a);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+}  // namespace ttr
