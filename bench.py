@@ -34,13 +34,17 @@ CONFIG_ID = 3
 # ncu DRAM traffic (read + write bytes per launch) of the dominant kernel, by
 # kernel family, with the profile summary it comes from; None when the
 # kernel changed after the capture.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # 13 launches of one decomposition: 908 MB of dram__bytes_read.sum +
+    # dram__bytes_write.sum (ncu, this bench's command, -k regex:k_tc_stream)
+    "proj_tc": 69.9e6,
+}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
@@ -63,7 +67,7 @@ def measured_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons, sampled every 50 ms."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -78,7 +82,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
@@ -135,6 +139,17 @@ def rel_error_dev(A64, cores):
     for s in range(0, dims[0], 8):
         num += float(torch.sum((Am[s:s + 8] - F[s:s + 8] @ M) ** 2))
     return float(np.sqrt(num) / float(torch.linalg.norm(Am)))
+
+
+def workload_config(w, world):
+    return {
+        "workload": f"{w.name}: 40^5 tensor, TT ranks 20 (0.8^j slices) + 5% Gaussian noise; "
+                    "BF16 storage and remainders, ranks 20, p=10, q=4",
+        "dims": list(w.dims), "ranks": list(w.ranks), "oversample": w.oversample, "q": w.q,
+        "omega": "Philox4x32-10 + Box-Muller, seed %d" % w.omega_seed,
+        "l2": "input (204.8 MB BF16) larger than L2 (129 MB); no flush",
+        "parallelism": f"replicas{world}" if world > 1 else "single GPU",
+    }
 
 
 def time_steps(fn, steps, warmup, sync_all):
@@ -268,14 +283,7 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "bf16",
         "data": "synthetic (seeded; paper's datasets unavailable)",
-        "config": {
-            "workload": f"{w.name}: 40^5 tensor, TT ranks 20 (0.8^j slices) + 5% Gaussian noise; "
-                        "BF16 storage and remainders, ranks 20, p=10, q=4",
-            "dims": list(w.dims), "ranks": list(ranks), "oversample": p, "q": q,
-            "omega": "Philox4x32-10 + Box-Muller on device, seed %d" % seed,
-            "l2": "input (204.8 MB BF16) larger than L2 (129 MB); no flush",
-            "parallelism": f"replicas{world}" if world > 1 else "single GPU",
-        },
+        "config": workload_config(w, world),
         "tt_error": {"bf16": eps_bf, "fp32": eps_32},
         "fp32_form": {"ms_per_step": ms32 / fp32_steps, "decompositions_per_s": fp32_steps / (ms32 * 1e-3),
                       "tt_error": eps_32, "speedup_bf16_over_fp32": (ms32 / fp32_steps) / (ms_max / args.steps)},
@@ -308,13 +316,14 @@ def oracle_step(A, w):
     oracle.tt_rbki(A, w.ranks, w.oversample, w.q, seed=w.omega_seed)
 
 
-def cpu_baseline(A, w):
+def cpu_baseline(A, w, reps=2):
     t0 = time.time()
-    oracle_step(A, w)
+    for _ in range(reps):
+        oracle_step(A, w)
     dt = time.time() - t0
-    return {"value": 1.0 / dt, "unit": "decompositions/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "one full decomposition of the same workload by the float64 numpy oracle "
-                      "(BLAS/LAPACK threads = all host cores)", "seconds": dt}
+    return {"value": reps / dt, "unit": "decompositions/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{reps} full decompositions of the same workload (same tensor, ranks, p, q, seed) "
+                      "by the float64 numpy oracle (BLAS/LAPACK threads = all host cores)", "seconds": dt}
 
 
 def run_reference(args):
@@ -334,7 +343,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": v, "unit": "decompositions/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic (seeded)", "config": {"workload": w.name},
+        "data": "synthetic (seeded; paper's datasets unavailable)", "config": workload_config(w, world),
         "cpu_baseline": {"value": v, "unit": "decompositions/s", "cores": os.cpu_count(), "kind": "oracle",
                          "sample": "one full decomposition per step by the float64 numpy oracle"},
         "e2e": {"value": v, "unit": "decompositions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
