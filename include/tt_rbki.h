@@ -20,8 +20,9 @@
  *  - Pointers documented as "device" must be device-accessible CUDA memory
  *    of the current device; "host" pointers are ordinary host memory.
  *  - The caller owns every buffer: the input tensor, the cores, the
- *    workspace.  No entry point allocates device memory, and none keeps a
- *    pointer after it returns.
+ *    workspace.  No entry point allocates device memory (the batched graph
+ *    form's CUDA graph excepted), and none keeps a pointer after it returns
+ *    (the graph keeps the device pointers it was built with).
  *  - All device work is enqueued on `stream` (a cudaStream_t passed as
  *    void*, NULL = legacy default stream).  Entry points do not synchronise
  *    the stream; results are ready once the stream has reached that point.
@@ -86,7 +87,10 @@ typedef struct {
                            sketch + Krylov passes; the result is the same
                            exact truncated SVD.  0: always run the Krylov
                            passes with the dimension cap.                     */
-  int32_t reserved[5];  /* must be zero                                       */
+  int32_t batch_streams;/* batched entry points: number of concurrent worker
+                           streams the problems are spread over (1..64);
+                           0 (default) = 16.  Ignored by single problems.    */
+  int32_t reserved[4];  /* must be zero                                       */
 } tt_options;
 
 /* Fills *opts with the defaults described above. */
@@ -158,6 +162,75 @@ TT_API tt_status tt_rbki_device_status(const void* workspace, void* stream, int*
 
 /* Message describing the last error returned on the calling thread. */
 TT_API const char* tt_rbki_last_error(void);
+
+/* ------------------------------------------------------------------------
+ * Batched form.  The paper decomposes one tensor per call; this runs many
+ * independent TT-rBKI problems (Alg. 3 each, Omega from each problem's
+ * seed) of uneven order, mode sizes and ranks in one call.  Problems are
+ * spread over opts->batch_streams concurrent worker streams (longest
+ * estimated cost first, each to the least-loaded worker) forked from and
+ * joined back to `stream`, so that the small-algebra kernels of different
+ * problems, which each occupy only a few SMs, run side by side.  Problems on
+ * the same worker run one after another and share that worker's part of
+ * the workspace.  The result of every problem is bit-identical to
+ * tt_rbki_decompose of that problem alone with the same options.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+  const void* tensor;        /* device, prod(dims) elements of opts->storage,
+                                row-major                                      */
+  const int64_t* dims;       /* host, d mode sizes (read during the call only) */
+  const int64_t* ranks;      /* host, d-1 target ranks                         */
+  float* const* cores_out;   /* host array of d device pointers, as in
+                                tt_rbki_decompose                              */
+  int64_t* ranks_out;        /* host, d+1 entries, or NULL                     */
+  uint64_t omega_seed;       /* seed of this problem's Omega_k                 */
+  int32_t d;                 /* order >= 2                                     */
+  int32_t oversample;        /* p >= 0                                         */
+  int32_t q;                 /* Krylov depth >= 0                              */
+  int32_t reserved;          /* must be zero                                   */
+} tt_problem;
+
+/* Workspace bytes for tt_rbki_decompose_batched / _graph_create with these
+ * problems and options (count status areas of 256 bytes plus one region per
+ * worker, sized for the largest problem it runs). */
+TT_API tt_status tt_rbki_batched_workspace_size(int count, const tt_problem* problems,
+                                                const tt_options* opts, size_t* bytes);
+
+/*
+ * Enqueues all `count` problems on `stream` (fork/join over the library's
+ * worker streams of the current device, created on first use and kept for
+ * the life of the process).  Every problem is checked on the host first; if
+ * any is invalid nothing is enqueued, per_problem[i] (host, count entries,
+ * may be NULL) receives each problem's status and the first error is
+ * returned.  The workspace (device, 256-byte aligned) must not be used by
+ * another call until the stream has passed this one.
+ * Errors: as tt_rbki_decompose, per problem; TT_EINVAL for count < 0 or
+ * batch_streams outside [0, 64].
+ */
+TT_API tt_status tt_rbki_decompose_batched(int count, const tt_problem* problems, void* workspace,
+                                           size_t ws_bytes, void* stream, const tt_options* opts,
+                                           tt_status* per_problem);
+
+/* Device status word of each problem of the last batch that used `workspace`
+ * (synchronises `stream`): device_status[i] receives TT_OK, TT_ENONFINITE,
+ * TT_EBREAKDOWN or TT_ETIMEOUT for problem i. */
+TT_API tt_status tt_rbki_batched_device_status(const void* workspace, int count, void* stream,
+                                               int* device_status);
+
+/*
+ * The same batch captured once into an executable CUDA graph, so that the
+ * whole batch is one cudaGraphLaunch.  The graph records the device
+ * pointers of the problems and the workspace: launch it again after
+ * refilling the same input buffers.  Creating it enqueues no work; it is
+ * the one entry point that allocates (the executable graph, inside CUDA).
+ * Release it with tt_rbki_graph_destroy once no launch of it is pending.
+ */
+typedef struct tt_graph_t* tt_graph;
+TT_API tt_status tt_rbki_batched_graph_create(int count, const tt_problem* problems, void* workspace,
+                                              size_t ws_bytes, const tt_options* opts,
+                                              tt_status* per_problem, tt_graph* graph);
+TT_API tt_status tt_rbki_graph_launch(tt_graph graph, void* stream);
+TT_API tt_status tt_rbki_graph_destroy(tt_graph graph);
 
 /* ------------------------------------------------------------------------
  * Step-level entry points.  Each runs one kernel family of the path on
@@ -239,6 +312,15 @@ TT_API tt_status tt_pass(int op, const void* C, int c_dtype, int64_t m, int64_t 
  */
 TT_API tt_status tt_gram_apply_noalloc(const void* C, int c_dtype, int64_t m, int64_t n, int b,
                                        const float* x, float* y, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Test aid (no counterpart in the paper).  Fills the shared memory of every
+ * SM with the 32-bit pattern `bits` (e.g. a NaN) by launching maximal CTAs
+ * on `stream`, so that a kernel launched afterwards which reads shared
+ * memory it never wrote sees that pattern.  Used by the tests in place of
+ * a memory-checking tool.  Errors: TT_ECUDA.
+ * ---------------------------------------------------------------------- */
+TT_API tt_status tt_debug_fill_shared(uint32_t bits, void* stream);
 
 /* ------------------------------------------------------------------------
  * Kernel accounting for benchmarks (no counterpart in the paper).

@@ -13,7 +13,8 @@ from ._native import (TT_BF16, TT_F32, TT_PASS_GRAM, TT_PASS_GRAMAPPLY,  # noqa:
 
 __all__ = ["decompose", "workspace_size", "core_sizes", "omega_generate", "permute_convert",
            "tt_pass", "device_status", "options", "profile_begin", "profile_end", "TTError", "TT_F32",
-           "TT_BF16"]
+           "TT_BF16", "Problem", "batched_workspace_size", "decompose_batched", "batched_device_status",
+           "BatchGraph"]
 
 
 def _torch():
@@ -36,13 +37,14 @@ def _stream_handle(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def options(storage=N.TT_F32, remainder=None, exhaust_gram=True):
+def options(storage=N.TT_F32, remainder=None, exhaust_gram=True, batch_streams=0):
     """tt_options with the given fields (remainder None = same as storage)."""
     o = N.TTOptions()
     N.check(N.lib().tt_rbki_default_options(ctypes.byref(o)))
     o.storage = int(storage)
     o.remainder = -1 if remainder is None else int(remainder)
     o.exhaust_gram = 1 if exhaust_gram else 0
+    o.batch_streams = int(batch_streams)
     return o
 
 
@@ -127,6 +129,12 @@ def profile_end():
                                        flops=arr[i].flops) for i in range(n.value)}
 
 
+def debug_fill_shared(bits=0x7FC00000, stream=None):
+    """Fill every SM's shared memory with a 32-bit pattern (default: a quiet
+    NaN) so that later reads of never-written shared memory show up."""
+    N.check(N.lib().tt_debug_fill_shared(ctypes.c_uint32(bits), _stream_handle(stream)))
+
+
 def device_status(workspace, stream=None):
     """Device status word of the last decomposition that used `workspace`."""
     out = ctypes.c_int()
@@ -162,25 +170,144 @@ def permute_convert(src, perm=None, dst_dtype=None, stream=None):
     return out
 
 
-def tt_pass(op, C, b=None, x=None, y_dtype=None, stream=None):
+def pass_workspace_size(op, m, n, b, c_dtype):
+    nbytes = ctypes.c_size_t()
+    N.check(N.lib().tt_pass_workspace_size(int(op), int(m), int(n), int(b), int(c_dtype), ctypes.byref(nbytes)))
+    return nbytes.value
+
+
+def tt_pass(op, C, b=None, x=None, y_dtype=None, stream=None, workspace=None, out=None):
     """One streaming pass over the unfolding C (2-D CUDA tensor), see tt_pass
     in the header.  Returns the output tensor."""
     torch = _torch()
     m, n = C.shape
     if op == N.TT_PASS_GRAM:
         b = 0
-        out = torch.empty((m, m), dtype=torch.float32, device=C.device)
+        shape, dt = (m, m), torch.float32
     elif op == N.TT_PASS_PROJECT:
         b = x.shape[1]
-        out = torch.empty((b, n), dtype=y_dtype or torch.float32, device=C.device)
+        shape, dt = (b, n), y_dtype or torch.float32
     else:
         b = x.shape[1]
-        out = torch.empty((m, b), dtype=torch.float32, device=C.device)
-    nbytes = ctypes.c_size_t()
-    N.check(N.lib().tt_pass_workspace_size(int(op), m, n, int(b), _dtype_code(C), ctypes.byref(nbytes)))
-    ws = torch.empty(nbytes.value, dtype=torch.uint8, device=C.device)
+        shape, dt = (m, b), torch.float32
+    if out is None:
+        out = torch.empty(shape, dtype=dt, device=C.device)
+    need = pass_workspace_size(op, m, n, b, _dtype_code(C))
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=C.device)
     N.check(N.lib().tt_pass(int(op), ctypes.c_void_p(C.data_ptr()), _dtype_code(C), m, n, int(b),
                             ctypes.c_void_p(x.data_ptr() if x is not None else 0),
                             ctypes.c_void_p(out.data_ptr()), _dtype_code(out),
-                            ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_handle(stream)))
+                            ctypes.c_void_p(workspace.data_ptr()), workspace.numel(), _stream_handle(stream)))
     return out
+
+
+class Problem:
+    """One problem of a batch: a contiguous CUDA tensor (dtype = the batch's
+    storage), target ranks r_1..r_{d-1}, p, q and the Omega seed.  The cores
+    (float32 CUDA tensors (r_{k-1}, I_k, r_k)) are allocated here unless
+    given."""
+
+    def __init__(self, tensor, ranks, oversample, q, omega_seed, cores=None):
+        torch = _torch()
+        if not tensor.is_cuda or not tensor.is_contiguous():
+            raise ValueError("tensor must be a contiguous CUDA tensor")
+        self.tensor = tensor
+        self.dims = list(tensor.shape)
+        self.ranks = list(ranks)
+        self.oversample, self.q, self.omega_seed = int(oversample), int(q), int(omega_seed)
+        rr, _ = core_sizes(self.dims, self.ranks)
+        self.rr = rr
+        if cores is None:
+            cores = [torch.empty((rr[k], self.dims[k], rr[k + 1]), dtype=torch.float32, device=tensor.device)
+                     for k in range(len(self.dims))]
+        self.cores = cores
+
+
+def _problem_array(problems):
+    """ctypes tt_problem array plus the host arrays it points to (kept alive
+    by the caller for the duration of the C call)."""
+    arr = (N.TTProblem * len(problems))()
+    keep = []
+    for i, pb in enumerate(problems):
+        dims, ranks = N.i64_array(pb.dims), N.i64_array(pb.ranks)
+        cores = N.ptr_array([c.data_ptr() for c in pb.cores])
+        rout = (ctypes.c_int64 * (len(pb.dims) + 1))()
+        keep += [dims, ranks, cores, rout]
+        arr[i].tensor = pb.tensor.data_ptr()
+        arr[i].dims = ctypes.cast(dims, ctypes.POINTER(ctypes.c_int64))
+        arr[i].ranks = ctypes.cast(ranks, ctypes.POINTER(ctypes.c_int64))
+        arr[i].cores_out = ctypes.cast(cores, ctypes.POINTER(ctypes.c_void_p))
+        arr[i].ranks_out = ctypes.cast(rout, ctypes.POINTER(ctypes.c_int64))
+        arr[i].omega_seed = pb.omega_seed
+        arr[i].d, arr[i].oversample, arr[i].q, arr[i].reserved = len(pb.dims), pb.oversample, pb.q, 0
+    return arr, keep
+
+
+def batched_workspace_size(problems, opts):
+    arr, _keep = _problem_array(problems)
+    nbytes = ctypes.c_size_t()
+    N.check(N.lib().tt_rbki_batched_workspace_size(len(problems), arr, ctypes.byref(opts), ctypes.byref(nbytes)))
+    return nbytes.value
+
+
+def _batch_ws(problems, opts, workspace):
+    torch = _torch()
+    need = batched_workspace_size(problems, opts)
+    if workspace is None or workspace.numel() < need:
+        dev = problems[0].tensor.device if problems else torch.device("cuda")
+        workspace = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+    return workspace
+
+
+def decompose_batched(problems, opts, workspace=None, stream=None):
+    """Enqueues every problem (tt_rbki_decompose_batched); returns the
+    workspace used (read device statuses from it)."""
+    workspace = _batch_ws(problems, opts, workspace)
+    arr, _keep = _problem_array(problems)
+    per = (ctypes.c_int * max(1, len(problems)))()
+    N.check(N.lib().tt_rbki_decompose_batched(len(problems), arr, ctypes.c_void_p(workspace.data_ptr()),
+                                              workspace.numel(), _stream_handle(stream), ctypes.byref(opts),
+                                              per))
+    return workspace
+
+
+def batched_device_status(workspace, count, stream=None):
+    out = (ctypes.c_int * max(1, count))()
+    N.check(N.lib().tt_rbki_batched_device_status(ctypes.c_void_p(workspace.data_ptr()), int(count),
+                                                  _stream_handle(stream), out))
+    return list(out)[:count]
+
+
+class BatchGraph:
+    """The batch captured into one executable CUDA graph
+    (tt_rbki_batched_graph_create); launch() replays it on a stream."""
+
+    def __init__(self, problems, opts, workspace=None):
+        self.problems = list(problems)
+        self.workspace = _batch_ws(self.problems, opts, workspace)
+        arr, _keep = _problem_array(self.problems)
+        per = (ctypes.c_int * max(1, len(self.problems)))()
+        h = ctypes.c_void_p()
+        N.check(N.lib().tt_rbki_batched_graph_create(len(self.problems), arr,
+                                                     ctypes.c_void_p(self.workspace.data_ptr()),
+                                                     self.workspace.numel(), ctypes.byref(opts), per,
+                                                     ctypes.byref(h)))
+        self._h = h
+
+    def launch(self, stream=None):
+        N.check(N.lib().tt_rbki_graph_launch(self._h, _stream_handle(stream)))
+
+    def device_status(self, stream=None):
+        return batched_device_status(self.workspace, len(self.problems), stream)
+
+    def close(self):
+        if self._h:
+            N.check(N.lib().tt_rbki_graph_destroy(self._h))
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -20,7 +20,16 @@ STATUS_NAMES = {0: "TT_OK", 1: "TT_EINVAL", 2: "TT_ENOMEM", 3: "TT_ECUDA", 4: "T
 
 class TTOptions(ctypes.Structure):
     _fields_ = [("storage", ctypes.c_int32), ("remainder", ctypes.c_int32),
-                ("exhaust_gram", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("exhaust_gram", ctypes.c_int32), ("batch_streams", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
+
+
+class TTProblem(ctypes.Structure):
+    _fields_ = [("tensor", ctypes.c_void_p), ("dims", ctypes.POINTER(ctypes.c_int64)),
+                ("ranks", ctypes.POINTER(ctypes.c_int64)), ("cores_out", ctypes.POINTER(ctypes.c_void_p)),
+                ("ranks_out", ctypes.POINTER(ctypes.c_int64)), ("omega_seed", ctypes.c_uint64),
+                ("d", ctypes.c_int32), ("oversample", ctypes.c_int32), ("q", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class TTKernelStat(ctypes.Structure):
@@ -51,6 +60,16 @@ _SIGNATURES = {
                                  _vpp, _i64p, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(TTOptions)],
                                 ctypes.c_int),
     "tt_rbki_device_status": ([_vp, _vp, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "tt_rbki_batched_workspace_size": ([ctypes.c_int, ctypes.POINTER(TTProblem), ctypes.POINTER(TTOptions),
+                                        ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "tt_rbki_decompose_batched": ([ctypes.c_int, ctypes.POINTER(TTProblem), _vp, ctypes.c_size_t, _vp,
+                                   ctypes.POINTER(TTOptions), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "tt_rbki_batched_device_status": ([_vp, ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "tt_rbki_batched_graph_create": ([ctypes.c_int, ctypes.POINTER(TTProblem), _vp, ctypes.c_size_t,
+                                      ctypes.POINTER(TTOptions), ctypes.POINTER(ctypes.c_int), _vpp],
+                                     ctypes.c_int),
+    "tt_rbki_graph_launch": ([_vp, _vp], ctypes.c_int),
+    "tt_rbki_graph_destroy": ([_vp], ctypes.c_int),
     "tt_rbki_last_error": ([], ctypes.c_char_p),
     "tt_permute_convert": ([_vp, ctypes.c_int, _i64p, _i64p, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                             _vp, ctypes.c_int, _vp], ctypes.c_int),
@@ -60,6 +79,7 @@ _SIGNATURES = {
                                 ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "tt_gram_apply_noalloc": ([_vp, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, _vp, _vp,
                                _vp], ctypes.c_int),
+    "tt_debug_fill_shared": ([ctypes.c_uint32, _vp], ctypes.c_int),
     "tt_rbki_profile_begin": ([ctypes.c_int], ctypes.c_int),
     "tt_rbki_profile_end": ([ctypes.POINTER(TTKernelStat), ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
                             ctypes.c_int),

@@ -2,7 +2,10 @@
 // layout and the mode loop of Alg. 3.  Everything is enqueued on the
 // caller's stream without a host round trip.
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <type_traits>
 #include <string>
 #include <vector>
@@ -54,7 +57,7 @@ tt_status resolve_options(const tt_options* in, tt_options* out) {
   if (out->storage != TT_F32 && out->storage != TT_BF16) return fail(TT_EINVAL, "options.storage must be TT_F32 or TT_BF16");
   if (out->remainder < 0) out->remainder = out->storage;
   if (out->remainder != TT_F32 && out->remainder != TT_BF16) return fail(TT_EINVAL, "options.remainder must be TT_F32 or TT_BF16");
-  for (int i = 0; i < 5; ++i)
+  for (int i = 0; i < 4; ++i)
     if (out->reserved[i] != 0) return fail(TT_EINVAL, "options.reserved must be zero");
   return TT_OK;
 }
@@ -179,8 +182,8 @@ tt_status build_plan(const int64_t* dims, int d, const int64_t* ranks, int p, in
 }
 
 template <typename TIn>
-tt_status run_mode(const Plan& P, int k, const TIn* C, char* ws, const float* omega_explicit, uint64_t seed,
-                   float* core, cudaStream_t st) {
+tt_status run_mode(const Plan& P, int k, const TIn* C, char* ws, int* status, const float* omega_explicit,
+                   uint64_t seed, float* core, cudaStream_t st) {
   const ModePlan& M = P.modes[k];
   constexpr bool kBf16 = std::is_same<TIn, __nv_bfloat16>::value;
   const bool use_tc = kBf16 && ttr::tc_shape_ok(M.m, M.n);
@@ -189,7 +192,6 @@ tt_status run_mode(const Plan& P, int k, const TIn* C, char* ws, const float* om
   float* part = (float*)(ws + P.off_part);
   float* U = (float*)(ws + P.off_U);
   float* small = (float*)(ws + P.off_small);
-  int* status = (int*)(ws + P.off_status);
   const int r = M.r_out;
   if (M.gram_route) {
     float* G = (float*)(ws + P.off_G);
@@ -282,27 +284,25 @@ tt_status run_mode(const Plan& P, int k, const TIn* C, char* ws, const float* om
   return TT_OK;
 }
 
-tt_status decompose_impl(const void* tensor, const int64_t* dims, int d, const int64_t* ranks, int oversample,
-                         int q, const float* const* omegas, uint64_t seed, float* const* cores_out,
-                         int64_t* ranks_out, void* workspace, size_t ws_bytes, void* stream,
-                         const tt_options* opts) {
-  Plan P;
-  tt_status s = build_plan(dims, d, ranks, oversample, q, opts, P);
-  if (s != TT_OK) return s;
+// Argument checks of one problem that need no workspace (Alg. 3 inputs).
+tt_status check_problem(const Plan& P, const void* tensor, const float* const* omegas, float* const* cores_out) {
   if (!tensor) return fail(TT_EINVAL, "tensor is NULL");
   if (!cores_out) return fail(TT_EINVAL, "cores_out is NULL");
-  for (int k = 0; k < d; ++k)
+  for (int k = 0; k < P.d; ++k)
     if (!cores_out[k]) return fail(TT_EINVAL, "cores_out[k] is NULL");
-  if (!workspace) return fail(TT_EINVAL, "workspace is NULL");
-  if (((uintptr_t)workspace & 255) != 0) return fail(TT_EINVAL, "workspace must be 256-byte aligned");
-  if (ws_bytes < P.total) return fail(TT_ENOMEM, "workspace too small");
   if (omegas)
-    for (int k = 0; k < d - 1; ++k)
+    for (int k = 0; k < P.d - 1; ++k)
       if (!omegas[k] && !P.modes[k].gram_route) return fail(TT_EINVAL, "omegas[k] is NULL");
-  cudaStream_t st = (cudaStream_t)stream;
-  char* ws = (char*)workspace;
-  int* status = (int*)(ws + P.off_status);
-  TTR_CUDA(cudaMemsetAsync(status, 0, 256, st));   // status, breakdown flag, orth ticket
+  return TT_OK;
+}
+
+// Enqueues the whole mode loop of Alg. 3 for one problem on `st`.  `ws`
+// holds P.total bytes (its own status area unused); `status` points to the
+// problem's 256-byte status area, cleared by the caller.
+tt_status enqueue_problem(const Plan& P, const void* tensor, const float* const* omegas, uint64_t seed,
+                          float* const* cores_out, char* ws, int* status, cudaStream_t st) {
+  tt_status s = TT_OK;
+  const int d = P.d;
   for (int k = 0; k < d - 1; ++k) {
     const void* C;
     int dt;
@@ -315,9 +315,9 @@ tt_status decompose_impl(const void* tensor, const int64_t* dims, int d, const i
     }
     const float* om = omegas ? omegas[k] : nullptr;
     if (dt == TT_BF16)
-      s = run_mode<__nv_bfloat16>(P, k, (const __nv_bfloat16*)C, ws, om, seed, cores_out[k], st);
+      s = run_mode<__nv_bfloat16>(P, k, (const __nv_bfloat16*)C, ws, status, om, seed, cores_out[k], st);
     else
-      s = run_mode<float>(P, k, (const float*)C, ws, om, seed, cores_out[k], st);
+      s = run_mode<float>(P, k, (const float*)C, ws, status, om, seed, cores_out[k], st);
     if (s != TT_OK) return s;
   }
   // Alg. 3 step 12: last core = last remainder
@@ -326,9 +326,183 @@ tt_status decompose_impl(const void* tensor, const int64_t* dims, int d, const i
   TTR_CUDA(ttr::launch_last_core(Rlast, P.remainder, last, cores_out[d - 1], status, st));
   for (int k = 0; k < d; ++k)
     TTR_CUDA(ttr::launch_check_finite(cores_out[k], P.rr[k] * P.dims[k] * P.rr[k + 1], status, st));
+  return TT_OK;
+}
+
+tt_status decompose_impl(const void* tensor, const int64_t* dims, int d, const int64_t* ranks, int oversample,
+                         int q, const float* const* omegas, uint64_t seed, float* const* cores_out,
+                         int64_t* ranks_out, void* workspace, size_t ws_bytes, void* stream,
+                         const tt_options* opts) {
+  Plan P;
+  tt_status s = build_plan(dims, d, ranks, oversample, q, opts, P);
+  if (s != TT_OK) return s;
+  s = check_problem(P, tensor, omegas, cores_out);
+  if (s != TT_OK) return s;
+  if (!workspace) return fail(TT_EINVAL, "workspace is NULL");
+  if (((uintptr_t)workspace & 255) != 0) return fail(TT_EINVAL, "workspace must be 256-byte aligned");
+  if (ws_bytes < P.total) return fail(TT_ENOMEM, "workspace too small");
+  cudaStream_t st = (cudaStream_t)stream;
+  char* ws = (char*)workspace;
+  int* status = (int*)(ws + P.off_status);
+  TTR_CUDA(cudaMemsetAsync(status, 0, 256, st));   // status, breakdown flag, orth ticket
+  s = enqueue_problem(P, tensor, omegas, seed, cores_out, ws, status, st);
+  if (s != TT_OK) return s;
   if (ranks_out)
     for (int k = 0; k <= d; ++k) ranks_out[k] = P.rr[k];
   return TT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched form: independent problems spread over concurrent worker streams
+// (one fork/join on the caller's stream), so that the small-problem kernels,
+// which each occupy a few SMs, run side by side.  Problems are assigned to
+// workers by longest-processing-time-first on an estimated cost; problems
+// that share a worker run one after another and share its workspace region.
+
+constexpr int kMaxWorkers = 64;
+constexpr int kDefaultWorkers = 16;
+
+struct BatchLayout {
+  std::vector<Plan> plans;
+  std::vector<std::vector<int>> order;   // problem indices per worker, in run order
+  std::vector<size_t> worker_off;        // byte offset of each worker's region
+  size_t status_bytes = 0, total = 0;
+  int workers = 0;
+};
+
+// Estimated microseconds of one problem on one worker: bytes streamed at a
+// per-worker share of HBM plus a fixed latency per small-algebra launch.
+double plan_cost(const Plan& P) {
+  double us = 0;
+  for (int k = 0; k < P.d - 1; ++k) {
+    const ModePlan& M = P.modes[k];
+    const double e = (double)esize(k == 0 ? P.storage : P.remainder);
+    const double passes = M.gram_route ? 2.0 : 2.0 + 2.0 * (double)M.blocks.size();
+    us += passes * (double)M.m * (double)M.n * e / 1.0e6;
+    us += M.gram_route ? 60.0 : 50.0 * (double)M.blocks.size() + 30.0 + 0.02 * (double)M.kq * M.kq;
+  }
+  return us + 10.0;
+}
+
+tt_status batch_layout(int count, const tt_problem* pr, const tt_options* opts, tt_status* per_problem,
+                       BatchLayout& L) {
+  if (count < 0) return fail(TT_EINVAL, "count must be >= 0");
+  if (count > 0 && !pr) return fail(TT_EINVAL, "problems is NULL");
+  tt_options o;
+  tt_status s = resolve_options(opts, &o);
+  if (s != TT_OK) return s;
+  if (o.batch_streams < 0 || o.batch_streams > kMaxWorkers)
+    return fail(TT_EINVAL, "options.batch_streams must be in [0, 64]");
+  L.plans.assign(count, Plan());
+  tt_status first = TT_OK;
+  std::string first_msg;
+  for (int i = 0; i < count; ++i) {
+    s = (pr[i].reserved != 0) ? fail(TT_EINVAL, "problem.reserved must be zero")
+                              : build_plan(pr[i].dims, pr[i].d, pr[i].ranks, pr[i].oversample, pr[i].q, &o,
+                                           L.plans[i]);
+    if (s == TT_OK) s = check_problem(L.plans[i], pr[i].tensor, nullptr, pr[i].cores_out);
+    if (per_problem) per_problem[i] = s;
+    if (s != TT_OK && first == TT_OK) {
+      first = s;
+      first_msg = "problem " + std::to_string(i) + ": " + g_last_error;
+    }
+  }
+  if (first != TT_OK) return fail(first, first_msg);
+  const int want = o.batch_streams > 0 ? o.batch_streams : kDefaultWorkers;
+  L.workers = std::max(1, std::min(want, count));
+  std::vector<std::pair<double, int>> cost(count);
+  for (int i = 0; i < count; ++i) cost[i] = {plan_cost(L.plans[i]), i};
+  std::stable_sort(cost.begin(), cost.end(), [](const std::pair<double, int>& a, const std::pair<double, int>& b) {
+    return a.first > b.first;
+  });
+  std::vector<double> load(L.workers, 0.0);
+  std::vector<size_t> need(L.workers, 0);
+  L.order.assign(L.workers, {});
+  for (const auto& c : cost) {
+    const int w = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    load[w] += c.first;
+    L.order[w].push_back(c.second);
+    need[w] = std::max(need[w], L.plans[c.second].total);
+  }
+  L.status_bytes = align_up((size_t)count * 256);
+  size_t off = L.status_bytes;
+  L.worker_off.assign(L.workers, 0);
+  for (int w = 0; w < L.workers; ++w) {
+    L.worker_off[w] = off;
+    off += align_up(need[w]);
+  }
+  L.total = std::max<size_t>(off, 256);
+  return TT_OK;
+}
+
+struct WorkerPool {
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> joins;
+  cudaEvent_t fork = nullptr;
+};
+std::mutex g_pool_mu;
+std::map<int, WorkerPool> g_pools;
+
+// Worker streams of the current device (created once, kept for the process).
+tt_status worker_pool(int workers, WorkerPool** out) {
+  int dev = 0;
+  TTR_CUDA(cudaGetDevice(&dev));
+  WorkerPool& W = g_pools[dev];
+  if (!W.fork) TTR_CUDA(cudaEventCreateWithFlags(&W.fork, cudaEventDisableTiming));
+  while ((int)W.streams.size() < workers) {
+    cudaStream_t s;
+    cudaEvent_t e;
+    TTR_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    TTR_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    W.streams.push_back(s);
+    W.joins.push_back(e);
+  }
+  *out = &W;
+  return TT_OK;
+}
+
+// Enqueues the batch: clear the status areas, fork, run every worker's
+// problems, join back onto `st`.  Caller holds g_pool_mu.
+tt_status enqueue_batch(const BatchLayout& L, const tt_problem* pr, char* ws, cudaStream_t st) {
+  const int count = (int)L.plans.size();
+  if (count == 0) return TT_OK;
+  WorkerPool* W = nullptr;
+  tt_status s = worker_pool(L.workers, &W);
+  if (s != TT_OK) return s;
+  TTR_CUDA(cudaMemsetAsync(ws, 0, L.status_bytes, st));
+  TTR_CUDA(cudaEventRecord(W->fork, st));
+  for (int w = 0; w < L.workers; ++w) TTR_CUDA(cudaStreamWaitEvent(W->streams[w], W->fork, 0));
+  // issue round-robin over workers so that every worker has work queued early
+  size_t most = 0;
+  for (const auto& o : L.order) most = std::max(most, o.size());
+  tt_status err = TT_OK;
+  for (size_t j = 0; j < most && err == TT_OK; ++j)
+    for (int w = 0; w < L.workers && err == TT_OK; ++w) {
+      if (j >= L.order[w].size()) continue;
+      const int i = L.order[w][j];
+      int* status = (int*)(ws + (size_t)i * 256);
+      err = enqueue_problem(L.plans[i], pr[i].tensor, nullptr, pr[i].omega_seed, pr[i].cores_out,
+                            ws + L.worker_off[w], status, W->streams[w]);
+    }
+  // always join, so that a capture in progress stays well formed
+  for (int w = 0; w < L.workers; ++w) {
+    TTR_CUDA(cudaEventRecord(W->joins[w], W->streams[w]));
+    TTR_CUDA(cudaStreamWaitEvent(st, W->joins[w], 0));
+  }
+  return err;
+}
+
+tt_status check_batch_ws(const BatchLayout& L, void* workspace, size_t ws_bytes) {
+  if (!workspace) return fail(TT_EINVAL, "workspace is NULL");
+  if (((uintptr_t)workspace & 255) != 0) return fail(TT_EINVAL, "workspace must be 256-byte aligned");
+  if (ws_bytes < L.total) return fail(TT_ENOMEM, "workspace too small");
+  return TT_OK;
+}
+
+void fill_ranks_out(const BatchLayout& L, const tt_problem* pr) {
+  for (size_t i = 0; i < L.plans.size(); ++i)
+    if (pr[i].ranks_out)
+      for (int k = 0; k <= L.plans[i].d; ++k) pr[i].ranks_out[k] = L.plans[i].rr[k];
 }
 
 }  // namespace
@@ -548,6 +722,100 @@ tt_status tt_pass(int op, const void* C, int c_dtype, int64_t m, int64_t n, int 
       else TTR_CUDA(ttr::simt_gram<float>((const float*)C, m, n, part, (float*)y, st));
       break;
   }
+  return TT_OK;
+}
+
+tt_status tt_rbki_batched_workspace_size(int count, const tt_problem* problems, const tt_options* opts,
+                                         size_t* bytes) {
+  if (!bytes) return fail(TT_EINVAL, "bytes is NULL");
+  BatchLayout L;
+  tt_status s = batch_layout(count, problems, opts, nullptr, L);
+  if (s != TT_OK) return s;
+  *bytes = L.total;
+  return TT_OK;
+}
+
+tt_status tt_rbki_decompose_batched(int count, const tt_problem* problems, void* workspace, size_t ws_bytes,
+                                    void* stream, const tt_options* opts, tt_status* per_problem) {
+  BatchLayout L;
+  tt_status s = batch_layout(count, problems, opts, per_problem, L);
+  if (s != TT_OK) return s;
+  s = check_batch_ws(L, workspace, ws_bytes);
+  if (s != TT_OK) return s;
+  {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    s = enqueue_batch(L, problems, (char*)workspace, (cudaStream_t)stream);
+  }
+  if (s != TT_OK) return s;
+  fill_ranks_out(L, problems);
+  return TT_OK;
+}
+
+tt_status tt_rbki_batched_device_status(const void* workspace, int count, void* stream, int* device_status) {
+  if (!workspace || (count > 0 && !device_status)) return fail(TT_EINVAL, "NULL argument");
+  if (count <= 0) return TT_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  TTR_CUDA(cudaMemcpy2DAsync(device_status, sizeof(int), workspace, 256, sizeof(int), (size_t)count,
+                             cudaMemcpyDeviceToHost, st));
+  TTR_CUDA(cudaStreamSynchronize(st));
+  return TT_OK;
+}
+
+struct tt_graph_t {
+  cudaGraphExec_t exec = nullptr;
+};
+
+tt_status tt_rbki_batched_graph_create(int count, const tt_problem* problems, void* workspace, size_t ws_bytes,
+                                       const tt_options* opts, tt_status* per_problem, tt_graph* graph) {
+  if (!graph) return fail(TT_EINVAL, "graph is NULL");
+  *graph = nullptr;
+  BatchLayout L;
+  tt_status s = batch_layout(count, problems, opts, per_problem, L);
+  if (s != TT_OK) return s;
+  s = check_batch_ws(L, workspace, ws_bytes);
+  if (s != TT_OK) return s;
+  cudaStream_t cs;
+  TTR_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) {
+      cudaStreamDestroy(cs);
+      return fail(TT_ECUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e));
+    }
+    s = enqueue_batch(L, problems, (char*)workspace, cs);
+    e = cudaStreamEndCapture(cs, &g);
+    if (s == TT_OK && e != cudaSuccess) s = fail(TT_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+  }
+  cudaStreamDestroy(cs);
+  if (s != TT_OK) {
+    if (g) cudaGraphDestroy(g);
+    return s;
+  }
+  tt_graph out = new tt_graph_t;
+  cudaError_t e = cudaGraphInstantiate(&out->exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    delete out;
+    return fail(TT_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+  }
+  fill_ranks_out(L, problems);
+  *graph = out;
+  return TT_OK;
+}
+
+tt_status tt_rbki_graph_launch(tt_graph graph, void* stream) {
+  if (!graph || !graph->exec) return fail(TT_EINVAL, "graph is NULL");
+  TTR_CUDA(cudaGraphLaunch(graph->exec, (cudaStream_t)stream));
+  return TT_OK;
+}
+
+tt_status tt_rbki_graph_destroy(tt_graph graph) {
+  if (!graph) return TT_OK;
+  cudaError_t e = graph->exec ? cudaGraphExecDestroy(graph->exec) : cudaSuccess;
+  delete graph;
+  if (e != cudaSuccess) return fail(TT_ECUDA, std::string("cudaGraphExecDestroy: ") + cudaGetErrorString(e));
   return TT_OK;
 }
 

@@ -221,6 +221,9 @@ __device__ void tri_factor(const float* d, const float* e, int k, float lam, flo
     }
   }
   r0[k - 1] = 1.f / ((fabsf(alpha) < tiny) ? copysignf(tiny, alpha) : alpha);
+  // the last row has no superdiagonal entries: the back substitution reads
+  // them (times zero), so they must be finite
+  u1[k - 1] = 0.f; u2[k - 1] = 0.f; l[k - 1] = 0.f; sw[k - 1] = 0.f;
 }
 
 // x <- (T - lam I)^{-1} x with the factors of tri_factor.

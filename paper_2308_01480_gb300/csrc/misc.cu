@@ -172,3 +172,41 @@ cudaError_t launch_permute(const void* src, int sdt, void* dst, int ddt, const i
 }
 
 }  // namespace ttr
+
+// ---------------------------------------------------------------- test aid
+namespace ttr {
+
+// Every CTA fills its whole dynamic shared memory with `value`; with one
+// maximal CTA per SM and several waves, each SM's shared memory ends up
+// holding the pattern, so a later kernel that reads shared memory it never
+// wrote sees it.
+__global__ void k_fill_shared(uint32_t bits, int words) {
+  extern __shared__ uint32_t fill_sm[];
+  volatile uint32_t* p = fill_sm;   // volatile: the stores are the point
+  for (int i = threadIdx.x; i < words; i += blockDim.x) p[i] = bits;
+}
+
+}  // namespace ttr
+
+extern "C" tt_status tt_debug_fill_shared(uint32_t bits, void* stream) {
+  int dev = 0, sms = 0, maxsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    ttr::set_last_error("tt_debug_fill_shared: device query failed");
+    return TT_ECUDA;
+  }
+  const size_t bytes = (size_t)maxsm / 16 * 16;
+  if (cudaFuncSetAttribute(ttr::k_fill_shared, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+      cudaSuccess) {
+    ttr::set_last_error("tt_debug_fill_shared: cudaFuncSetAttribute failed");
+    return TT_ECUDA;
+  }
+  ttr::k_fill_shared<<<4 * sms, 1024, bytes, (cudaStream_t)stream>>>(bits, (int)(bytes / 4));
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    ttr::set_last_error(cudaGetErrorString(e));
+    return TT_ECUDA;
+  }
+  return TT_OK;
+}

@@ -139,3 +139,30 @@ CONFIGS = {
                 TENSOR_SEED_BASE + 4, OMEGA_SEED_BASE + 4, "power",
                 noise=0.01, notes="f(i)=1/(i1+i2+i3+i4+1), 134.2M entries, 1% noise"),
 }
+
+
+# Batched form: each problem's mode vector is resampled until the tensor has
+# at most this many entries (an unconstrained order-6 tensor with modes up to
+# 64 would hold ~7e10 entries, far from "about 2 GB" for the whole batch).
+BATCH_ENTRY_CAP = 1 << 24
+
+
+def batch_workloads(count=256, seed=TENSOR_SEED_BASE + 5, omega_seed=OMEGA_SEED_BASE + 5):
+    """Independent problems of the batched form: order uniform in 3..6,
+    modes uniform in 8..64 (resampled until the entry count is at most
+    BATCH_ENTRY_CAP), per-bond TT ranks uniform in 2..16 for both the
+    generating cores and the target, 5% Gaussian noise, p = 5, q = 2, BF16
+    storage.  Problem i gets tensor seed seed*1000 + i and Omega seed
+    omega_seed*1000 + i."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        d = int(rng.integers(3, 7))
+        while True:
+            dims = tuple(int(x) for x in rng.integers(8, 65, size=d))
+            if int(np.prod(dims, dtype=np.int64)) <= BATCH_ENTRY_CAP:
+                break
+        ranks = tuple(int(x) for x in rng.integers(2, 17, size=d - 1))
+        out.append(Workload(f"batch{i}", dims, ranks, 5, 2, "bf16", seed * 1000 + i, omega_seed * 1000 + i,
+                            "tt", ranks, noise=0.05))
+    return out

@@ -94,3 +94,85 @@ def test_workspace_size_grows_with_problem(L):
     assert 0 < nb1.value < nb2.value
     # 32^5 FP32: two remainder buffers of r_1 n_1 = 10 * 32^4 floats at least
     assert nb2.value >= 2 * 10 * 32 ** 4 * 4
+
+
+def _problems(specs, keep):
+    """tt_problem array for workspace sizing (fake, never dereferenced
+    device pointers; sizing reads only the host arrays)."""
+    arr = (N.TTProblem * len(specs))()
+    for i, (dims, ranks, p, q) in enumerate(specs):
+        da, ra = N.i64_array(dims), N.i64_array(ranks)
+        cores = N.ptr_array([4096 * (j + 1) for j in range(len(dims))])
+        keep += [da, ra, cores]
+        arr[i].tensor = 1 << 20
+        arr[i].dims = ctypes.cast(da, ctypes.POINTER(ctypes.c_int64))
+        arr[i].ranks = ctypes.cast(ra, ctypes.POINTER(ctypes.c_int64))
+        arr[i].cores_out = ctypes.cast(cores, ctypes.POINTER(ctypes.c_void_p))
+        arr[i].d, arr[i].oversample, arr[i].q = len(dims), p, q
+    return arr
+
+
+def _single_ws(L, dims, ranks, p, q, opts):
+    nb = ctypes.c_size_t()
+    assert L.tt_rbki_workspace_size(N.i64_array(dims), len(dims), N.i64_array(ranks), p, q, ctypes.byref(opts),
+                                    ctypes.byref(nb)) == N.TT_OK
+    return nb.value
+
+
+def _opts(L, streams):
+    o = N.TTOptions()
+    L.tt_rbki_default_options(ctypes.byref(o))
+    o.storage = N.TT_BF16
+    o.batch_streams = streams
+    return o
+
+
+SPECS = [((16, 16, 16, 16), (4, 4, 4), 5, 2), ((37, 29, 41), (5, 6), 3, 3), ((64, 8, 64, 8), (9, 12, 5), 5, 2)]
+
+
+def test_batched_workspace_layout(L):
+    """One 256-byte status area per problem plus one region per worker,
+    sized for the largest problem the worker runs."""
+    keep = []
+    arr = _problems(SPECS, keep)
+    singles = [_single_ws(L, d, r, p, q, _opts(L, 0)) for d, r, p, q in SPECS]
+    nb = ctypes.c_size_t()
+    assert L.tt_rbki_batched_workspace_size(1, arr, ctypes.byref(_opts(L, 0)), ctypes.byref(nb)) == N.TT_OK
+    assert nb.value == 256 + singles[0]
+    assert L.tt_rbki_batched_workspace_size(3, arr, ctypes.byref(_opts(L, 1)), ctypes.byref(nb)) == N.TT_OK
+    assert nb.value == 768 + max(singles)
+    assert L.tt_rbki_batched_workspace_size(3, arr, ctypes.byref(_opts(L, 3)), ctypes.byref(nb)) == N.TT_OK
+    assert nb.value == 768 + sum(singles)
+    assert L.tt_rbki_batched_workspace_size(3, arr, ctypes.byref(_opts(L, 2)), ctypes.byref(nb)) == N.TT_OK
+    assert 768 + max(singles) <= nb.value <= 768 + sum(singles)
+    assert L.tt_rbki_batched_workspace_size(0, None, ctypes.byref(_opts(L, 0)), ctypes.byref(nb)) == N.TT_OK
+
+
+def test_batched_invalid_arguments(L):
+    keep = []
+    arr = _problems(SPECS, keep)
+    nb = ctypes.c_size_t()
+    assert L.tt_rbki_batched_workspace_size(-1, arr, None, ctypes.byref(nb)) == N.TT_EINVAL
+    assert L.tt_rbki_batched_workspace_size(2, None, None, ctypes.byref(nb)) == N.TT_EINVAL
+    assert L.tt_rbki_batched_workspace_size(3, arr, ctypes.byref(_opts(L, 65)), ctypes.byref(nb)) == N.TT_EINVAL
+    arr[1].reserved = 1
+    assert L.tt_rbki_batched_workspace_size(3, arr, None, ctypes.byref(nb)) == N.TT_EINVAL
+    assert b"problem 1" in L.tt_rbki_last_error()
+    arr[1].reserved = 0
+    bad = N.i64_array([4, 0])
+    keep.append(bad)
+    arr[2].ranks = ctypes.cast(bad, ctypes.POINTER(ctypes.c_int64))
+    arr[2].d = 3
+    per = (ctypes.c_int * 3)()
+    # invalid problem: rejected on the host with per-problem statuses, before any device call
+    assert L.tt_rbki_decompose_batched(3, arr, ctypes.c_void_p(256), 1 << 30, None, None, per) == N.TT_EINVAL
+    assert list(per) == [N.TT_OK, N.TT_OK, N.TT_EINVAL]
+    arr[2].tensor = None
+    arr[2].ranks = arr[0].ranks
+    assert L.tt_rbki_decompose_batched(3, arr, ctypes.c_void_p(256), 1 << 30, None, None, per) == N.TT_EINVAL
+    assert b"tensor is NULL" in L.tt_rbki_last_error()
+    h = ctypes.c_void_p()
+    assert L.tt_rbki_graph_launch(None, None) == N.TT_EINVAL
+    assert L.tt_rbki_graph_destroy(None) == N.TT_OK
+    assert L.tt_rbki_batched_graph_create(3, arr, ctypes.c_void_p(256), 1 << 30, None, per,
+                                          ctypes.byref(h)) == N.TT_EINVAL
