@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
+    ap.add_argument("--config", type=int, default=CONFIG_ID, choices=sorted(W.CONFIGS),
+                    help="workload (default: the 40^5 BF16 workload the metric is quoted on)")
     return ap.parse_args()
 
 
@@ -142,14 +144,26 @@ def rel_error_dev(A64, cores):
 
 
 def workload_config(w, world):
+    nbytes = w.numel * 2
     return {
-        "workload": f"{w.name}: 40^5 tensor, TT ranks 20 (0.8^j slices) + 5% Gaussian noise; "
-                    "BF16 storage and remainders, ranks 20, p=10, q=4",
+        "workload": f"{w.name}: {w.notes}; BF16 storage and remainders, "
+                    f"ranks {w.ranks[0]}, p={w.oversample}, q={w.q}",
         "dims": list(w.dims), "ranks": list(w.ranks), "oversample": w.oversample, "q": w.q,
         "omega": "Philox4x32-10 + Box-Muller, seed %d" % w.omega_seed,
-        "l2": "input (204.8 MB BF16) larger than L2 (129 MB); no flush",
+        "l2": (f"input ({nbytes / 1e6:.1f} MB BF16) larger than L2 (129 MB); no flush" if nbytes > 129e6
+               else f"input ({nbytes / 1e6:.1f} MB BF16) fits L2; no flush"),
         "parallelism": f"replicas{world}" if world > 1 else "single GPU",
     }
+
+
+def max_over_ranks(x, dist, device=None):
+    """Largest value of x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def time_steps(fn, steps, warmup, sync_all):
@@ -189,7 +203,7 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    w = W.CONFIGS[CONFIG_ID]
+    w = W.CONFIGS[args.config]
     t0 = time.time()
     A = W.make_tensor(w)                     # float64 host tensor, seeded
     gen_s = time.time() - t0
@@ -226,11 +240,7 @@ def run_ours(args):
     clk = clocks.stop()
     if tt.device_status(ws_bf) != 0:
         raise RuntimeError("device status not OK after the BF16 runs")
-    ms_max = ms
-    if dist is not None:
-        tmax = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        ms_max = float(tmax.item())
+    ms_max = max_over_ranks(ms, dist, dev)
 
     # ---- FP32 form on the same tensor (comparison point)
     fp32_steps = max(1, min(args.steps, 5))
@@ -330,7 +340,7 @@ def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
         return
-    w = W.CONFIGS[CONFIG_ID]
+    w = W.CONFIGS[args.config]
     A = W.make_tensor(w)
     for _ in range(args.warmup):
         oracle_step(A, w)

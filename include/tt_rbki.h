@@ -284,6 +284,21 @@ TT_API tt_status tt_pass(int op, const void* C, int c_dtype, int64_t m, int64_t 
                   const float* x, void* y, int y_dtype, void* workspace, size_t ws_bytes,
                   void* stream);
 
+/*
+ * Top-r eigenpairs of a small symmetric matrix: the Rayleigh-Ritz step of
+ * Alg. 3 (steps 6-8) takes the r largest eigenpairs of H = Q^T C C^T Q.
+ *   H       device, k x k float32, row stride ldh >= k; only (H + H^T)/2 is
+ *           used.  1 <= r <= k <= 224.
+ *   V       device, k x r float32 row-major: eigenvectors as columns, in
+ *           descending eigenvalue order, orthonormal.
+ *   evals   device, r float32 eigenvalues, descending (may be NULL).
+ *   workspace / ws_bytes: device scratch of tt_sym_eig_workspace_size bytes.
+ * Errors: TT_EINVAL, TT_EUNSUPPORTED (k > 224), TT_ENOMEM, TT_ECUDA.
+ */
+TT_API tt_status tt_sym_eig_workspace_size(int k, int r, size_t* bytes);
+TT_API tt_status tt_sym_eig_top(const float* H, int64_t ldh, int k, int r, float* V, float* evals,
+                                void* workspace, size_t ws_bytes, void* stream);
+
 /* ------------------------------------------------------------------------
  * Allocation-free Gram-apply.  The paper has no counterpart: this entry
  * point exists for deployment, not for the method.
@@ -321,6 +336,14 @@ TT_API tt_status tt_gram_apply_noalloc(const void* C, int c_dtype, int64_t m, in
  * a memory-checking tool.  Errors: TT_ECUDA.
  * ---------------------------------------------------------------------- */
 TT_API tt_status tt_debug_fill_shared(uint32_t bits, void* stream);
+
+/* Test aid: runs, on `stream`, one wait of the kind every tensor-core kernel
+ * uses (an mbarrier wait bounded at about two seconds) on a barrier that
+ * nothing ever completes, so the wait gives up and records TT_ETIMEOUT in
+ * the 256-byte status area at `workspace` (device; read it back with
+ * tt_rbki_device_status).  Exercises the timeout path without a fault; the
+ * context stays usable.  Errors: TT_EINVAL, TT_ECUDA. */
+TT_API tt_status tt_debug_wait_timeout(void* workspace, void* stream);
 
 /* ------------------------------------------------------------------------
  * Kernel accounting for benchmarks (no counterpart in the paper).

@@ -129,10 +129,34 @@ def profile_end():
                                        flops=arr[i].flops) for i in range(n.value)}
 
 
+def sym_eig_top(H, r, stream=None):
+    """Top-r eigenpairs of the symmetric part of the k x k CUDA float32
+    matrix H (the Rayleigh-Ritz eigensolver).  Returns (V (k x r), evals)."""
+    torch = _torch()
+    k = H.shape[0]
+    if H.dtype != torch.float32 or not H.is_cuda or H.dim() != 2 or H.shape[1] != k or H.stride(1) != 1:
+        raise ValueError("H must be a k x k float32 CUDA matrix with unit column stride")
+    nbytes = ctypes.c_size_t()
+    N.check(N.lib().tt_sym_eig_workspace_size(int(k), int(r), ctypes.byref(nbytes)))
+    ws = torch.empty(nbytes.value, dtype=torch.uint8, device=H.device)
+    V = torch.empty((k, r), dtype=torch.float32, device=H.device)
+    ev = torch.empty((r,), dtype=torch.float32, device=H.device)
+    N.check(N.lib().tt_sym_eig_top(ctypes.c_void_p(H.data_ptr()), H.stride(0), int(k), int(r),
+                                   ctypes.c_void_p(V.data_ptr()), ctypes.c_void_p(ev.data_ptr()),
+                                   ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_handle(stream)))
+    return V, ev
+
+
 def debug_fill_shared(bits=0x7FC00000, stream=None):
     """Fill every SM's shared memory with a 32-bit pattern (default: a quiet
     NaN) so that later reads of never-written shared memory show up."""
     N.check(N.lib().tt_debug_fill_shared(ctypes.c_uint32(bits), _stream_handle(stream)))
+
+
+def debug_wait_timeout(workspace, stream=None):
+    """Run one bounded mbarrier wait that can never complete; the status
+    area at the start of `workspace` then reads TT_ETIMEOUT."""
+    N.check(N.lib().tt_debug_wait_timeout(ctypes.c_void_p(workspace.data_ptr()), _stream_handle(stream)))
 
 
 def device_status(workspace, stream=None):

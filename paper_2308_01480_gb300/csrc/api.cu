@@ -225,12 +225,12 @@ tt_status run_mode(const Plan& P, int k, const TIn* C, char* ws, int* status, co
     const uint64_t rseed = 0x5EEDull * (uint64_t)(k + 1);
     int* flag = status + 1;
     unsigned* ticket = reinterpret_cast<unsigned*>(status + 2);
-    // orthonormalise a block: multi-CTA CholeskyQR path with the one-CTA
-    // robust path as fallback (run only if the fast path flagged a
-    // breakdown); the one-CTA path alone when the dimension cap truncates
+    // orthonormalise a block: cluster (or multi-CTA) CholeskyQR path with
+    // the one-CTA robust path as fallback, run only if the fast path flagged
+    // a breakdown; the one-CTA path alone for shapes neither fast path takes
     auto orth = [&](const float* Z, int64_t ldz, int zc, int kq0, int c, uint64_t sd) -> tt_status {
-      if (c == zc && ttr::orth_cluster_ok(M.m, kq0, zc)) {
-        TTR_CUDA(ttr::launch_orth_cluster(Z, ldz, M.m, zc, Q, kq, kq0, flag, st));
+      if (ttr::orth_cluster_ok(M.m, kq0, zc)) {
+        TTR_CUDA(ttr::launch_orth_cluster(Z, ldz, M.m, zc, c, Q, kq, kq0, flag, st));
         TTR_CUDA(ttr::launch_orth_block(Z, ldz, M.m, zc, Q, kq, kq0, c, small, sd, status, flag, st));
       } else if (c == zc && ttr::orth_fast_ok(M.m, kq0, zc)) {
         TTR_CUDA(ttr::launch_orth_fast(Z, ldz, M.m, zc, Q, kq, kq0, small, ticket, flag, st));
@@ -816,6 +816,26 @@ tt_status tt_rbki_graph_destroy(tt_graph graph) {
   cudaError_t e = graph->exec ? cudaGraphExecDestroy(graph->exec) : cudaSuccess;
   delete graph;
   if (e != cudaSuccess) return fail(TT_ECUDA, std::string("cudaGraphExecDestroy: ") + cudaGetErrorString(e));
+  return TT_OK;
+}
+
+tt_status tt_sym_eig_workspace_size(int k, int r, size_t* bytes) {
+  if (!bytes) return fail(TT_EINVAL, "bytes is NULL");
+  if (k < 1 || r < 1 || r > k) return fail(TT_EINVAL, "need 1 <= r <= k");
+  if (!ttr::eig_top_ok(k)) return fail(TT_EUNSUPPORTED, "k must be <= 224");
+  *bytes = align_up(ttr::eig_scratch_floats(k, r) * 4);
+  return TT_OK;
+}
+
+tt_status tt_sym_eig_top(const float* H, int64_t ldh, int k, int r, float* V, float* evals, void* workspace,
+                         size_t ws_bytes, void* stream) {
+  size_t need = 0;
+  tt_status s = tt_sym_eig_workspace_size(k, r, &need);
+  if (s != TT_OK) return s;
+  if (!H || !V) return fail(TT_EINVAL, "NULL argument");
+  if (ldh < k) return fail(TT_EINVAL, "ldh < k");
+  if (!workspace || ws_bytes < need) return fail(TT_ENOMEM, "workspace too small");
+  TTR_CUDA(ttr::launch_eig_top(H, ldh, k, r, V, (float*)workspace, evals, (cudaStream_t)stream));
   return TT_OK;
 }
 

@@ -50,4 +50,171 @@ __device__ inline void chol_inv_cta(float* G, int ldg, int b, const float* diag0
   __syncthreads();
 }
 
+
+// Same contract as chol_inv_cta for b <= 32, computed by warp 0 alone:
+// lane l holds column l of the upper triangle of G in registers while it is
+// factored (rows of R travel between lanes by shuffles), R goes to shared
+// memory, then lane l forms column l of T = R^{-1} by back substitution
+// with R read back as broadcasts.  Pivot square roots and reciprocals use
+// the hardware reciprocal square root (a few ulp), which the following
+// Cholesky QR passes absorb.  The CTA synchronises before (G complete) and
+// after (R, T written).
+__device__ __forceinline__ void chol_inv_warp32(const float* G, int ldg, int b, const float* diag0, float* R, int ldr,
+                                       float* T, int ldt, int* flag, bool report) {
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const unsigned full = 0xffffffffu;
+    const int l = threadIdx.x;
+    float rinv = 1.f;                       // 1 / R[l][l]
+    {
+      float a[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) a[i] = (i <= l && l < b) ? G[i * ldg + l] : 0.f;
+      const float d0 = (l < b) ? diag0[l] : 1.f;
+      bool bad = false;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        if (j < b) {
+          float djj = __shfl_sync(full, a[j], j);
+          const float dref = __shfl_sync(full, d0, j);
+          if (!(djj > 1e-6f * dref)) {
+            bad = true;
+            djj = 1.f;
+          }
+          const float inv = rsqrtf(djj);
+          if (l == j) rinv = inv;
+          const float rjl = (l == j) ? djj * inv : ((l > j) ? a[j] * inv : 0.f);   // R[j][l]
+          a[j] = rjl;
+#pragma unroll
+          for (int i = j + 1; i < 32; ++i) {
+            const float rji = __shfl_sync(full, rjl, i);                  // R[j][i]
+            a[i] = fmaf(-rji, rjl, a[i]);
+          }
+        }
+      }
+      if (report && bad && l == 0) atomicExch(flag, 1);
+      if (l < b) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+          if (i < b) R[i * ldr + l] = (i <= l) ? a[i] : 0.f;
+      }
+    }
+    __syncwarp();
+    // column l of T = R^{-1}; the reciprocal pivots come from their lanes
+    float t[32];
+#pragma unroll
+    for (int i = 31; i >= 0; --i) {
+      const float ri = __shfl_sync(full, rinv, i);
+      if (i < b) {
+        float s0 = (i == l) ? 1.f : 0.f, s1 = 0.f;
+#pragma unroll
+        for (int k = i + 1; k < 32; ++k)
+          if (k < b) {
+            if ((k - i) & 1) s0 = fmaf(-R[i * ldr + k], t[k], s0);
+            else s1 = fmaf(-R[i * ldr + k], t[k], s1);
+          }
+        t[i] = (i <= l && l < b) ? (s0 + s1) * ri : 0.f;
+      } else {
+        t[i] = 0.f;
+      }
+    }
+    if (l < b) {
+#pragma unroll
+      for (int i = 0; i < 32; ++i)
+        if (i < b) T[i * ldt + l] = t[i];
+    }
+  }
+  __syncthreads();
+}
+
+// Out-of-line copy: one instance of the unrolled factorisation per kernel
+// however many call sites it has (keeps register budgets and instruction
+// footprints small).
+static __device__ __noinline__ void chol_inv_warp32_call(const float* G, int ldg, int b, const float* diag0,
+                                                         float* R, int ldr, float* T, int ldt, int* flag,
+                                                         bool report) {
+  chol_inv_warp32(G, ldg, b, diag0, R, ldr, T, ldt, flag, report);
+}
+
+// Pivoted variant for a block that keeps only c <= b columns (the Krylov
+// dimension cap): greedy symmetric pivoting on the largest remaining
+// diagonal of G (b x b, full symmetric storage, row stride ldg) selects c
+// columns; R (c x c, row stride ldr) is the Cholesky factor of the selected
+// columns' Gram and Tf (b x bt, row stride ldt, zeroed here) maps the b
+// columns to the c kept ones: Tf[perm[i]][j] = (R^{-1})[i][j] for i, j < c.
+// perm (b ints of shared memory) receives the pivot order.  A pivot below
+// 1e-6 of its original diagonal (or non-positive) raises *flag when report.
+__device__ inline void pchol_select_cta(float* G, int ldg, int b, int c, const float* diag0, float* R, int ldr,
+                                        float* Tf, int ldt, int bt, int* perm, float* dsw, int* flag,
+                                        bool report) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  __shared__ int s_piv;
+  for (int i = tid; i < b; i += blockDim.x) {
+    perm[i] = i;
+    dsw[i] = diag0[i];
+  }
+  __syncthreads();
+  for (int j = 0; j < c; ++j) {
+    if (wid == 0) {
+      float best = -1.f;
+      int bi = j;
+      for (int i = j + lane; i < b; i += 32) {
+        const float v = G[i * ldg + i];
+        if (v > best) { best = v; bi = i; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (lane == 0) s_piv = bi;
+    }
+    __syncthreads();
+    const int pv = s_piv;
+    if (pv != j) {
+      // symmetric swap of rows and columns j <-> pv
+      for (int l = tid; l < b; l += blockDim.x) {
+        const float t = G[j * ldg + l]; G[j * ldg + l] = G[pv * ldg + l]; G[pv * ldg + l] = t;
+      }
+      __syncthreads();
+      for (int l = tid; l < b; l += blockDim.x) {
+        const float t = G[l * ldg + j]; G[l * ldg + j] = G[l * ldg + pv]; G[l * ldg + pv] = t;
+      }
+      if (tid == 0) {
+        const int t = perm[j]; perm[j] = perm[pv]; perm[pv] = t;
+        const float d = dsw[j]; dsw[j] = dsw[pv]; dsw[pv] = d;
+      }
+      __syncthreads();
+    }
+    float dj = G[j * ldg + j];
+    if (!(dj > 1e-6f * dsw[j])) {
+      if (report && tid == 0) atomicExch(flag, 1);
+      dj = 1.f;
+    }
+    const float rj = sqrtf(dj), inv = 1.f / rj, inv2 = inv * inv;
+    for (int l = j + tid; l < c; l += blockDim.x) R[j * ldr + l] = (l == j) ? rj : G[j * ldg + l] * inv;
+    for (int l = tid; l < j; l += blockDim.x) R[j * ldr + l] = 0.f;
+    // full trailing update (later swaps need whole rows and columns)
+    for (int i = j + 1 + wid; i < b; i += nw) {
+      const float gi = G[j * ldg + i] * inv2;
+      for (int l = j + 1 + lane; l < b; l += 32) G[i * ldg + l] -= gi * G[j * ldg + l];
+    }
+    __syncthreads();
+  }
+  for (int x = tid; x < b * ldt; x += blockDim.x) Tf[x] = 0.f;
+  __syncthreads();
+  // (R^{-1}) column by column; row i of it lands on row perm[i] of Tf
+  for (int col = tid; col < c; col += blockDim.x) {
+    float t[64];
+    for (int i = col; i >= 0; --i) {
+      float s0 = (i == col) ? 1.f : 0.f;
+      for (int l = i + 1; l <= col; ++l) s0 -= R[i * ldr + l] * t[l];
+      t[i] = s0 / R[i * ldr + i];
+    }
+    for (int i = 0; i <= col; ++i) Tf[perm[i] * ldt + col] = t[i];
+  }
+  (void)bt;
+  __syncthreads();
+}
+
 }  // namespace ttr

@@ -447,6 +447,7 @@ static size_t eig_work_bytes(int k, int r) { return sizeof(float) * 6 * (size_t)
 cudaError_t launch_eig_top(const float* H, int64_t ldh, int k, int r, float* V, float* scratch, float* evals,
                            cudaStream_t st) {
   if (!eig_top_ok(k) || r > k || r < 1) return cudaErrorInvalidValue;
+  if (eig_reg_ok(k, r)) return launch_eig_reg(H, ldh, k, r, V, r, evals, scratch, st);
   size_t smem = eig_smem(k, r);
   const int work_in_smem = (smem + eig_work_bytes(k, r) + 16 <= 226 * 1024) ? 1 : 0;
   if (work_in_smem) smem += eig_work_bytes(k, r) + 16;

@@ -1,0 +1,537 @@
+// Top-r eigenpairs of the small symmetric Rayleigh-Ritz matrix (Alg. 3
+// steps 6-8), k <= 160, in two one-CTA kernels.  The first holds H in
+// registers: NW warps, thread (warp w, lane l) owning the entries
+// (w + NW a, l + 32 c), a < 32 KT / NW, c < KT = ceil(k / 32).  The second (16 warps, so
+// that the register-resident Cholesky of step 4 fits) does steps 2-5.
+//
+//  1. Householder tridiagonalisation.  Per column two barriers: the owners
+//     of column j publish it; every warp forms the same reflector v; each
+//     warp reduces its rows of p = tau H v across its lanes; then every
+//     thread applies H -= v w^T + w v^T to its entries, w = p - (tau/2)
+//     (v^T p) v.  The reflectors are kept in shared memory.
+//  2. Bisection by Sturm counts: one round with a count at each of 1024
+//     points over the Gershgorin interval, then a warp per wanted
+//     eigenvalue refines its bracket by 33-point multisection.
+//  3. Inverse iteration on the tridiagonal T (pivoted LU), one thread per
+//     wanted eigenvalue, two rounds of one solve each, and
+//  4. after each round an orthonormalisation of the r vectors by Cholesky
+//     QR twice (columns in descending eigenvalue order, so the result is
+//     the Gram-Schmidt basis), or Gram-Schmidt twice when a Cholesky pivot
+//     is too small.
+//  5. Back-transformation by the stored reflectors, a warp per vector with
+//     the vector in registers.
+#include <float.h>
+
+#include <utility>
+
+#include "chol.cuh"
+#include "common.cuh"
+#include "kernels.h"
+
+namespace ttr {
+
+namespace {
+
+constexpr int ER_KTMAX = 5;
+
+// Compile-time loop: f(integral_constant<int, 0>) ... f(<N - 1>), so that
+// register-tile indices are constants however large the unrolled body.
+template <int I>
+struct CIdx {
+  __host__ __device__ constexpr operator int() const { return I; }
+};
+template <typename F, int... I>
+__device__ __forceinline__ void sfor_impl(F& f, std::integer_sequence<int, I...>) {
+  (f(CIdx<I>{}), ...);
+}
+template <int N, typename F>
+__device__ __forceinline__ void sfor(F&& f) {
+  sfor_impl(f, std::make_integer_sequence<int, N>{});
+}
+
+__device__ __forceinline__ float warp_min_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ float warp_max_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ int warp_min_i(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Number of eigenvalues of T = (d, e) below x (Sturm sequence of the LDL^T
+// pivots); e2 holds the squared off-diagonal.
+__device__ __forceinline__ int sturm(const float* d, const float* e2, int k, float x, float pivmin) {
+  int c = 0;
+  float q = d[0] - x;
+  if (fabsf(q) < pivmin) q = -pivmin;
+  c += q < 0.f;
+#pragma unroll 4
+  for (int i = 1; i < k; ++i) {
+    q = (d[i] - x) - __fdividef(e2[i - 1], q);
+    if (fabsf(q) < pivmin) q = -pivmin;
+    c += q < 0.f;
+  }
+  return c;
+}
+
+// Pivoted LU of T - lam I into w[0..5k) (reciprocal pivots, two upper
+// diagonals, multipliers, exchange flags); tiny pivots replaced by +-tiny.
+__device__ void tri_lu(const float* d, const float* e, int k, float lam, float tiny, float* w) {
+  float* r0 = w;
+  float* u1 = w + k;
+  float* u2 = w + 2 * k;
+  float* l = w + 3 * k;
+  float* sw = w + 4 * k;
+  float alpha = d[0] - lam, beta = (k > 1) ? e[0] : 0.f;
+  for (int i = 0; i + 1 < k; ++i) {
+    const float sub = e[i];
+    const float a1 = d[i + 1] - lam, c1 = (i + 2 < k) ? e[i + 1] : 0.f;
+    if (fabsf(alpha) >= fabsf(sub)) {
+      const float piv = (fabsf(alpha) < tiny) ? copysignf(tiny, alpha) : alpha;
+      const float rp = __fdividef(1.f, piv);
+      const float li = sub * rp;
+      r0[i] = rp; u1[i] = beta; u2[i] = 0.f; l[i] = li; sw[i] = 0.f;
+      alpha = fmaf(-li, beta, a1);
+      beta = c1;
+    } else {
+      const float rs = __fdividef(1.f, (fabsf(sub) < tiny) ? copysignf(tiny, sub) : sub);
+      const float li = alpha * rs;
+      r0[i] = rs; u1[i] = a1; u2[i] = c1; l[i] = li; sw[i] = 1.f;
+      alpha = fmaf(-li, a1, beta);
+      beta = -li * c1;
+    }
+  }
+  r0[k - 1] = __fdividef(1.f, (fabsf(alpha) < tiny) ? copysignf(tiny, alpha) : alpha);
+  u1[k - 1] = 0.f; u2[k - 1] = 0.f; l[k - 1] = 0.f; sw[k - 1] = 0.f;
+}
+
+__device__ void tri_lu_solve(const float* w, int k, float* x) {
+  const float* r0 = w;
+  const float* u1 = w + k;
+  const float* u2 = w + 2 * k;
+  const float* l = w + 3 * k;
+  const float* sw = w + 4 * k;
+  float xi = x[0];
+  for (int i = 0; i + 1 < k; ++i) {
+    float xn = x[i + 1];
+    if (sw[i] != 0.f) { const float t = xi; xi = xn; xn = t; }
+    x[i] = xi;
+    xi = fmaf(-l[i], xi, xn);
+  }
+  x[k - 1] = xi;
+  float x1 = 0.f, x2 = 0.f;
+  for (int i = k - 1; i >= 0; --i) {
+    const float v = (x[i] - u1[i] * x1 - u2[i] * x2) * r0[i];
+    x[i] = v;
+    x2 = x1;
+    x1 = v;
+  }
+}
+
+}  // namespace
+
+// Shared-memory floats of k_eig_vectors for k (padded to KM = 32 KT) and r.
+__host__ __device__ inline size_t er_smem_floats(int KM, int k, int r) {
+  return (size_t)k * k + 4 * (size_t)KM + 32 + 64 + 1024 + 2 * (size_t)r * (k + 1) + (size_t)r * 5 * k +
+         3 * 33 * 32 + 8;
+}
+
+// Step 1 in one CTA of 32 warps: T = (d, e) and the reflectors (row j of
+// Vg = v_j, tau[j]) to global scratch.
+template <int KT, int NW>
+__global__ void __launch_bounds__(32 * NW, 1) k_eig_tridiag(const float* __restrict__ Hin, int64_t ldh, int k,
+                                                           float* __restrict__ Vg, float* __restrict__ tau_g,
+                                                           float* __restrict__ d_g, float* __restrict__ e_g) {
+  constexpr int KM = 32 * KT;
+  constexpr int NT = 32 * NW;
+  constexpr int RA = KM / NW;
+  __shared__ __align__(16) float xcol[2 * KM];
+  __shared__ __align__(16) float pbuf[2 * KM];
+  float* Vs = Vg;
+  float* tau = tau_g;
+  float* d = d_g;
+  float* e = e_g;
+  const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 5;
+
+  // ---------------------------------------------------------------- 1
+  float A[RA][KT];
+  sfor<RA>([&](auto a) {
+    sfor<KT>([&](auto c) {
+      const int i = ty + NW * a, j = lane + 32 * c;
+      A[a][c] = (i < k && j < k) ? 0.5f * (Hin[(int64_t)i * ldh + j] + Hin[(int64_t)j * ldh + i]) : 0.f;
+    });
+  });
+  for (int x = tid; x < k * k; x += NT) Vs[x] = 0.f;
+  __syncthreads();
+  for (int j = 0; j + 2 < k; ++j) {
+    float* xc = xcol + (j & 1) * KM;
+    float* pb = pbuf + (j & 1) * KM;
+    if (lane == (j & 31)) {
+      sfor<RA>([&](auto a) {
+        float val = 0.f;
+        sfor<KT>([&](auto c) {
+          if (c == (j >> 5)) val = A[a][c];
+        });
+        const int i = ty + NW * a;
+        xc[i] = (i > j && i < k) ? val : 0.f;
+        if (i == j) d[j] = val;
+      });
+    }
+    __syncthreads();
+    float part = 0.f;
+#pragma unroll
+    for (int c = 0; c < KT; ++c) {
+      const int i = lane + 32 * c;
+      if (i >= j + 2) {
+        const float x = xc[i];
+        part = fmaf(x, x, part);
+      }
+    }
+    const float sigma = warp_sum(part);
+    const float x0 = xc[j + 1];
+    float t = 0.f, iv = 0.f, beta = x0;
+    if (sigma > 0.f) {
+      const float mu = sqrtf(fmaf(x0, x0, sigma));
+      const float v0 = (x0 <= 0.f) ? x0 - mu : __fdividef(-sigma, x0 + mu);
+      t = __fdividef(2.f * v0 * v0, fmaf(v0, v0, sigma));
+      beta = mu;
+      iv = __fdividef(1.f, v0);
+    }
+    if (tid == 0) {
+      tau[j] = t;
+      e[j] = beta;
+    }
+    if (t == 0.f) continue;              // same decision in every thread
+    float vc[KT];
+#pragma unroll
+    for (int c = 0; c < KT; ++c) {
+      const int i = lane + 32 * c;
+      vc[c] = (i == j + 1) ? 1.f : ((i > j + 1) ? xc[i] * iv : 0.f);
+    }
+    {
+      float s[RA];
+      sfor<RA>([&](auto a) {
+        float acc = 0.f;
+        sfor<KT>([&](auto c) { acc = fmaf(A[a][c], vc[c], acc); });
+        s[a] = acc;
+      });
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int a = 0; a < RA; ++a) s[a] += __shfl_xor_sync(0xffffffffu, s[a], o);
+      if (lane == 0) {
+#pragma unroll
+        for (int a = 0; a < RA; ++a) {
+          const int i = ty + NW * a;
+          pb[i] = (i > j && i < k) ? t * s[a] : 0.f;
+        }
+      }
+    }
+    if (ty == 0) {
+#pragma unroll
+      for (int c = 0; c < KT; ++c) {
+        const int i = lane + 32 * c;
+        if (i < k) Vs[(size_t)j * k + i] = vc[c];
+      }
+    }
+    __syncthreads();
+    float kp = 0.f;
+#pragma unroll
+    for (int c = 0; c < KT; ++c) kp = fmaf(vc[c], pb[lane + 32 * c], kp);
+    const float K = 0.5f * t * warp_sum(kp);
+    float wc[KT];
+#pragma unroll
+    for (int c = 0; c < KT; ++c) wc[c] = fmaf(-K, vc[c], pb[lane + 32 * c]);
+    // rank-2 update, one row of the tile at a time (v_i, w_i from shared)
+    sfor<RA>([&](auto a) {
+      const int i = ty + NW * a;
+      const float vi = (i == j + 1) ? 1.f : ((i > j + 1) ? xc[i] * iv : 0.f);
+      const float wi = fmaf(-K, vi, pb[i]);
+      sfor<KT>([&](auto c) { A[a][c] -= fmaf(vi, wc[c], wi * vc[c]); });
+    });
+  }
+  // trailing 2 x 2 (or 1 x 1) block, written by the owners of its entries
+  // (static tile indices keep the tile in registers)
+  sfor<RA>([&](auto a) {
+    sfor<KT>([&](auto c) {
+      const int i = ty + NW * a, jj = lane + 32 * c;
+      if (k >= 2 && i == k - 2 && jj == k - 2) d[k - 2] = A[a][c];
+      if (k >= 2 && i == k - 1 && jj == k - 2) e[k - 2] = A[a][c];
+      if (i == k - 1 && jj == k - 1) d[k - 1] = A[a][c];
+    });
+  });
+  if (tid == 0) {
+    if (k >= 2) tau[k - 2] = 0.f;
+    e[k - 1] = 0.f;
+    tau[k - 1] = 0.f;
+  }
+  __syncthreads();
+}
+
+// Steps 2-5 in one CTA of 16 warps, from T and the reflectors in global
+// scratch (the reflectors are staged in shared memory).
+template <int KT>
+__global__ void __launch_bounds__(512, 1) k_eig_vectors(const float* __restrict__ Vg, const float* __restrict__ tau_g,
+                                                       const float* __restrict__ d_g, const float* __restrict__ e_g,
+                                                       int k, int r, float* __restrict__ V, int ldv,
+                                                       float* __restrict__ evals) {
+  constexpr int NW = 16;
+  constexpr int KM = 32 * KT;
+  constexpr int NT = 32 * NW;
+  extern __shared__ __align__(16) float sm[];
+  float* Vs = sm;                         // [k][k], row j = reflector v_j
+  float* tau = Vs + (size_t)k * k;        // [KM]
+  float* d = tau + KM;                    // [KM]
+  float* e = d + KM;                      // [KM]
+  float* e2 = e + KM;                     // [KM]
+  float* lam = e2 + KM;                   // [32]
+  float* red = lam + 32;                  // [64]
+  int* cnt = reinterpret_cast<int*>(red + 64);   // [1024]
+  float* X = reinterpret_cast<float*>(cnt + 1024);   // [r][k + 1]
+  float* X2 = X + (size_t)r * (k + 1);    // [r][k + 1]
+  float* Wk = X2 + (size_t)r * (k + 1);   // [r][5k] inverse-iteration factors
+  float* G = Wk + (size_t)r * 5 * k;      // [32][33]
+  float* Rm = G + 33 * 32;                // [32][32]
+  float* Tm = Rm + 33 * 32;               // [32][32]
+  int* sflag = reinterpret_cast<int*>(Tm + 33 * 32);
+  const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 5;
+  const int ldx = k + 1;
+  for (int x = tid; x < k * k; x += NT) Vs[x] = Vg[x];
+  for (int i = tid; i < k; i += NT) {
+    tau[i] = tau_g[i];
+    d[i] = d_g[i];
+    e[i] = e_g[i];
+  }
+  if (tid == 0) *sflag = 0;
+  __syncthreads();
+
+  // ---------------------------------------------------------------- 2
+  float glo = FLT_MAX, ghi = -FLT_MAX, amax = 0.f;
+  for (int i = tid; i < k; i += NT) {
+    const float off = (i > 0 ? fabsf(e[i - 1]) : 0.f) + fabsf(e[i]);
+    glo = fminf(glo, d[i] - off);
+    ghi = fmaxf(ghi, d[i] + off);
+    amax = fmaxf(amax, fmaxf(fabsf(d[i]), fabsf(e[i])));
+    e2[i] = e[i] * e[i];
+  }
+  glo = warp_min_f(glo);
+  ghi = warp_max_f(ghi);
+  amax = warp_max_f(amax);
+  if (lane == 0) {
+    red[ty] = glo;
+    red[32 + ty] = ghi;
+    cnt[ty] = __float_as_int(amax);
+  }
+  __syncthreads();
+  glo = warp_min_f(lane < NW ? red[lane] : FLT_MAX);
+  ghi = warp_max_f(lane < NW ? red[32 + lane] : -FLT_MAX);
+  amax = warp_max_f(lane < NW ? __int_as_float(cnt[lane]) : 0.f);
+  __syncthreads();
+  const float tnorm = fmaxf(amax, FLT_MIN);
+  const float pivmin = FLT_MIN * fmaxf(1.f, tnorm * tnorm);
+  const float pad = 2.f * FLT_EPSILON * tnorm + pivmin;
+  const float lo0 = glo - pad, hi0 = ghi + pad;
+  const float step = (hi0 - lo0) * (1.f / (float)(NT + 1));
+  cnt[tid] = sturm(d, e2, k, fmaf((float)(tid + 1), step, lo0), pivmin);
+  __syncthreads();
+  for (int jj = ty; jj < r; jj += NW) {
+    const int want = k - jj;             // count reaching k - j brackets the j-th largest
+    int first = NT;
+    for (int u = 0; u < NW; ++u) {
+      const int tt = lane * NW + u;
+      if (cnt[tt] >= want) {
+        first = tt;
+        break;
+      }
+    }
+    first = warp_min_i(first);
+    float lo = (first == 0) ? lo0 : fmaf((float)first, step, lo0);
+    float hi = (first == NT) ? hi0 : fmaf((float)(first + 1), step, lo0);
+    for (int it = 0; it < 4; ++it) {
+      const float x = lo + (hi - lo) * (float)(lane + 1) * (1.f / 33.f);
+      const int c = sturm(d, e2, k, x, pivmin);
+      const unsigned ge = __ballot_sync(0xffffffffu, c >= want);
+      const int sidx = ge ? (__ffs(ge) - 1) : 32;
+      const float xs = __shfl_sync(0xffffffffu, x, sidx < 32 ? sidx : 31);
+      const float xp = __shfl_sync(0xffffffffu, x, sidx > 0 ? sidx - 1 : 0);
+      if (sidx == 32) lo = xs;
+      else {
+        hi = xs;
+        if (sidx > 0) lo = xp;
+      }
+    }
+    if (lane == 0) lam[jj] = 0.5f * (lo + hi);
+  }
+  __syncthreads();
+
+  // ---------------------------------------------------------------- 3
+  // Two rounds of one inverse-iteration solve per vector followed by an
+  // orthonormalisation of all r vectors (a subspace iteration): for nearly
+  // equal eigenvalues the solves pull every vector towards the same
+  // eigenvector, and orthonormalising after each single solve keeps the
+  // remainders inside the cluster's invariant subspace.
+  const float tiny = FLT_EPSILON * tnorm + pivmin;
+  float* cur = X;
+  float* nxt = X2;
+  for (int round = 0; round < 2; ++round) {
+    if (tid < r) {
+      float* x = cur + (size_t)tid * ldx;
+      float* w = Wk + (size_t)tid * 5 * k;
+      if (round == 0) {
+        tri_lu(d, e, k, lam[tid], tiny, w);
+        for (int i = 0; i < k; ++i) x[i] = 1.f + 0.01f * (float)((i * 7 + tid * 13) % 11);
+      }
+      tri_lu_solve(w, k, x);
+      float mx = 0.f;
+      for (int i = 0; i < k; ++i) mx = fmaxf(mx, fabsf(x[i]));
+      const float sc = mx > 0.f ? 1.f / mx : 0.f;
+      for (int i = 0; i < k; ++i) x[i] *= sc;
+    }
+    __syncthreads();
+
+  // ---------------------------------------------------------------- 4
+    if (tid == 0) *sflag = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int x = tid; x < r * r; x += NT) {
+        const int a = x / r, b = x % r;
+        if (b >= a) {
+          float s0 = 0.f, s1 = 0.f;
+          const float* xa = cur + (size_t)a * ldx;
+          const float* xb = cur + (size_t)b * ldx;
+          int i = 0;
+          for (; i + 1 < k; i += 2) {
+            s0 = fmaf(xa[i], xb[i], s0);
+            s1 = fmaf(xa[i + 1], xb[i + 1], s1);
+          }
+          if (i < k) s0 = fmaf(xa[i], xb[i], s0);
+          G[a * 33 + b] = s0 + s1;
+        }
+      }
+      __syncthreads();
+      if (tid < r) red[tid] = G[tid * 33 + tid];
+      chol_inv_warp32_call(G, 33, r, red, Rm, 33, Tm, 33, sflag, true);
+      if (*sflag) break;                  // uniform: fall back below
+      // nxt[j][i] = sum_{a <= j} cur[a][i] T[a][j]
+      for (int x = tid; x < r * k; x += NT) {
+        const int j = x / k, i = x % k;
+        float s = 0.f;
+        for (int a = 0; a <= j; ++a) s = fmaf(cur[(size_t)a * ldx + i], Tm[a * 33 + j], s);
+        nxt[(size_t)j * ldx + i] = s;
+      }
+      __syncthreads();
+      float* tmp = cur; cur = nxt; nxt = tmp;
+    }
+    if (*sflag) {
+      // Gram-Schmidt twice in descending eigenvalue order (a Cholesky pass
+      // that was applied leaves the span of each leading set unchanged)
+      for (int j = 0; j < r; ++j) {
+        float* xj = cur + (size_t)j * ldx;
+        for (int pass = 0; pass < 2 && j > 0; ++pass) {
+          for (int i2 = ty; i2 < j; i2 += NW) {
+            const float* xi = cur + (size_t)i2 * ldx;
+            float pp = 0.f;
+            for (int i = lane; i < k; i += 32) pp = fmaf(xi[i], xj[i], pp);
+            pp = warp_sum(pp);
+            if (lane == 0) G[i2] = pp;
+          }
+          __syncthreads();
+          for (int i = tid; i < k; i += NT) {
+            float s0 = xj[i];
+            for (int i2 = 0; i2 < j; ++i2) s0 = fmaf(-G[i2], cur[(size_t)i2 * ldx + i], s0);
+            xj[i] = s0;
+          }
+          __syncthreads();
+        }
+        float pp = 0.f;
+        for (int i = tid; i < k; i += NT) pp = fmaf(xj[i], xj[i], pp);
+        const float nrm = sqrtf(block_sum(pp, red));
+        const float inv = nrm > 0.f ? 1.f / nrm : 0.f;
+        for (int i = tid; i < k; i += NT) xj[i] *= inv;
+        __syncthreads();
+      }
+    }
+    __syncthreads();
+  }
+
+  // ---------------------------------------------------------------- 5
+  for (int jj = ty; jj < r; jj += NW) {
+    float xv[KT];
+    const float* src = cur + (size_t)jj * ldx;
+#pragma unroll
+    for (int c = 0; c < KT; ++c) {
+      const int i = lane + 32 * c;
+      xv[c] = (i < k) ? src[i] : 0.f;
+    }
+    for (int h = k - 3; h >= 0; --h) {
+      const float th = tau[h];
+      if (th == 0.f) continue;
+      const float* vh = Vs + (size_t)h * k;
+      float vv[KT];
+      float dp = 0.f;
+#pragma unroll
+      for (int c = 0; c < KT; ++c) {
+        const int i = lane + 32 * c;
+        vv[c] = (i < k) ? vh[i] : 0.f;
+        dp = fmaf(vv[c], xv[c], dp);
+      }
+      const float sc = th * warp_sum(dp);
+#pragma unroll
+      for (int c = 0; c < KT; ++c) xv[c] = fmaf(-sc, vv[c], xv[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < KT; ++c) {
+      const int i = lane + 32 * c;
+      if (i < k) V[(size_t)i * ldv + jj] = xv[c];
+    }
+    if (evals && lane == 0) evals[jj] = lam[jj];
+  }
+}
+
+// ------------------------------------------------------------ launcher
+static int er_kt(int k) { return (k + 31) / 32; }
+
+bool eig_reg_ok(int k, int r) {
+  if (k < 1 || r < 1 || r > 32 || r > k || k > 32 * ER_KTMAX) return false;
+  return er_smem_floats(32 * er_kt(k), k, r) * 4 <= 227 * 1024;
+}
+
+template <int KT>
+static cudaError_t launch_kt(const float* H, int64_t ldh, int k, int r, float* V, int ldv, float* evals,
+                             float* scratch, cudaStream_t st) {
+  float* Vg = scratch;
+  float* tau = Vg + (size_t)k * k;
+  float* d = tau + k;
+  float* e = d + k;
+  k_eig_tridiag<KT, 32><<<1, 1024, 0, st>>>(H, ldh, k, Vg, tau, d, e);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  const size_t smem = er_smem_floats(32 * KT, k, r) * 4;
+  err = cudaFuncSetAttribute(k_eig_vectors<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  k_eig_vectors<KT><<<1, 512, smem, st>>>(Vg, tau, d, e, k, r, V, ldv, evals);
+  return cudaGetLastError();
+}
+
+// scratch: k * k + 3 k floats (device)
+cudaError_t launch_eig_reg(const float* H, int64_t ldh, int k, int r, float* V, int ldv, float* evals,
+                           float* scratch, cudaStream_t st) {
+  if (!eig_reg_ok(k, r)) return cudaErrorInvalidValue;
+  ProfScope prof("eig_top", st, 0, 0);
+  note_launch("eig_top", 2);
+  switch (er_kt(k)) {
+    case 1: return launch_kt<1>(H, ldh, k, r, V, ldv, evals, scratch, st);
+    case 2: return launch_kt<2>(H, ldh, k, r, V, ldv, evals, scratch, st);
+    case 3: return launch_kt<3>(H, ldh, k, r, V, ldv, evals, scratch, st);
+    case 4: return launch_kt<4>(H, ldh, k, r, V, ldv, evals, scratch, st);
+    default: return launch_kt<5>(H, ldh, k, r, V, ldv, evals, scratch, st);
+  }
+}
+
+}  // namespace ttr

@@ -88,12 +88,22 @@ cudaError_t launch_orth_fast(const float* W, int64_t ldw, int64_t m, int b, floa
 
 // ---- block orthonormalisation on one thread-block cluster (orth_cluster.cu)
 bool orth_cluster_ok(int64_t m, int kq, int b);
-cudaError_t launch_orth_cluster(const float* W, int64_t ldw, int64_t m, int b, float* Q, int64_t ldq, int kq,
+// c <= b columns are kept (c < b: the Krylov dimension cap)
+cudaError_t launch_orth_cluster(const float* W, int64_t ldw, int64_t m, int b, int c, float* Q, int64_t ldq, int kq,
                                 int* flag, cudaStream_t st);
+
+// ---- register-tiled symmetric eigensolver, k <= 160, r <= 32 (eig_reg.cu)
+bool eig_reg_ok(int k, int r);
+// scratch: k * k + 3 k floats
+cudaError_t launch_eig_reg(const float* H, int64_t ldh, int k, int r, float* V, int ldv, float* evals,
+                           float* scratch, cudaStream_t st);
 
 // ---- Rayleigh-Ritz through a tridiagonal eigensolver (eig.cu)
 bool eig_top_ok(int k);
 size_t rr_fast_scratch_floats(int64_t m, int k, int r);
+size_t eig_scratch_floats(int k, int r);
+cudaError_t launch_eig_top(const float* H, int64_t ldh, int k, int r, float* V, float* scratch, float* evals,
+                           cudaStream_t st);
 cudaError_t launch_rr_fast(const float* Q, const float* W, int64_t ld, int64_t m, int k, int r, int identity_q,
                            float* scratch, float* U, float* core, cudaStream_t st);
 size_t rr_scratch_floats(int k);

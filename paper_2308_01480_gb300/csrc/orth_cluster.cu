@@ -14,8 +14,15 @@
 //   D: Z = Z R1^-1;           P3 = Q^T Z, R2 = chol(Z^T Z - P3^T P3)
 //   E: Z = (Z - Q P3) R2^-1;  R3 = chol(Z^T Z)
 //   F: X = Z R3^-1 -> Q[:, kq:kq+b]
-// (C, D, E, F without Q terms for the first block).  A pivot below 1e-6 of
+// (C, D, E, F without Q terms for the first block).  The Krylov power
+// blocks are typically far from orthogonal (their columns lean towards the
+// dominant directions), so the shift is always applied.  A pivot below 1e-6 of
 // its diagonal sets the breakdown flag for the one-CTA robust path.
+// When the Krylov dimension cap keeps only c < b columns, the projected Z
+// has (with probability one) rank c: its range is the part of range(C), or
+// of R^m, not yet in span(Q).  Phase C then selects c columns by greedy
+// diagonal pivoting of the shifted Cholesky, which spans that range, and
+// D-F carry c columns.
 // All products use 4 x 4 register tiles over shared arrays whose row
 // strides are padded to multiples of 4 with zeros.
 #include <cooperative_groups.h>
@@ -39,6 +46,7 @@ struct ClusterOrthArgs {
   int64_t m;
   int b;
   int64_t rows;     // rows per CTA
+  int c;            // columns kept (c <= b; c < b under the dimension cap)
   int* flag;
 };
 
@@ -46,10 +54,10 @@ __host__ __device__ inline int pad4(int x) { return (x + 3) & ~3; }
 
 // Shared-memory layout (floats), kp = pad4(kq), bp = pad4(b), rp = pad4(rows):
 //   share[2][(kp + bp) * bp] | P[kp * bp] | G[b * (b + 1)] | T[bp * bp] | R[b * b] (sizes padded to 4)
-//   | diag0[64] | red[64] | Z[rp * bp] | Z2[rp * bp] | Qc[rp * kp]
+//   | diag0[64] | red[64] | perm[64] | dsw[64] | Z[rp * bp] | Z2[rp * bp] | Qc[rp * kp]
 __host__ __device__ inline size_t oc_smem_floats(int kq, int b, int64_t rows) {
   const size_t kp = pad4(kq), bp = pad4(b), rp = pad4((int)rows);
-  return 2 * (kp + bp) * bp + kp * bp + pad4(b * (b + 1)) + bp * bp + pad4(b * b) + 128 + 2 * rp * bp + rp * kp;
+  return 2 * (kp + bp) * bp + kp * bp + pad4(b * (b + 1)) + bp * bp + pad4(b * b) + 256 + 2 * rp * bp + rp * kp;
 }
 
 // out[t][j] = sum_{i < rows} A[i][t] B[i][j], t < ta (multiple of 4), j < bp;
@@ -122,7 +130,9 @@ __global__ void __launch_bounds__(OC_THREADS) k_orth_cluster(ClusterOrthArgs a) 
   float* R = T + bp * bp;
   float* diag0 = R + pad4(b * b);
   float* red = diag0 + 64;
-  float* Zc = red + 64;        // current rows
+  int* perm = reinterpret_cast<int*>(red + 64);
+  float* dsw = red + 128;
+  float* Zc = red + 192;       // current rows
   float* Zn = Zc + rp * bp;    // scratch rows
   float* Qc = Zn + rp * bp;
   const bool report = rank == 0;
@@ -177,7 +187,34 @@ __global__ void __launch_bounds__(OC_THREADS) k_orth_cluster(ClusterOrthArgs a) 
     for (int i = tid; i < b; i += blockDim.x) diag0[i] = G[i * (b + 1) + i];
     __syncthreads();
   };
-  auto factor = [&]() { chol_inv_cta(G, b + 1, b, diag0, R, b, T, bp, a.flag, report); };
+  const int c = a.c;
+  auto factor = [&](int bc, int* fl, bool rep) {
+    if (bc < b) {
+      for (int x = tid; x < bp * bp; x += blockDim.x) T[x] = 0.f;
+      __syncthreads();
+    }
+    if (bc <= 32)
+      chol_inv_warp32_call(G, b + 1, bc, diag0, R, b, T, bp, fl, rep);
+    else
+      chol_inv_cta(G, b + 1, bc, diag0, R, b, T, bp, fl, rep);
+  };
+  auto write_q = [&](int cols) {
+    for (int x = tid; x < rc * cols; x += blockDim.x) {
+      const int i = x / cols, j = x % cols;
+      a.Q[(r0 + i) * a.ldq + kq + j] = Zc[i * bp + j];
+    }
+  };
+  // G <- G - P^T P over the first cols columns (Pythagorean update after a
+  // projection that has not been applied yet)
+  auto sub_ptp = [&](int cols) {
+    if (kq == 0) return;
+    for (int e = tid; e < cols * cols; e += blockDim.x) {
+      const int i = e / cols, j = e % cols;
+      float s = 0.f;
+      for (int t = 0; t < kq; ++t) s = fmaf(P[t * bp + i], P[t * bp + j], s);
+      G[i * (b + 1) + j] -= s;
+    }
+  };
 
   if (kq > 0) {
     reduce(true, false);                       // A
@@ -188,35 +225,32 @@ __global__ void __launch_bounds__(OC_THREADS) k_orth_cluster(ClusterOrthArgs a) 
   reduce(false, true);                         // C
   set_diag0();
   {
-    float tr = 0.f;
-    for (int i = tid; i < b; i += blockDim.x) tr += G[i * (b + 1) + i];
-    tr = block_sum(tr, red);
-    const float shift = 11.f * ((float)a.m * b + (float)b * (b + 1)) * 5.9604645e-08f * tr;
-    __syncthreads();
-    for (int i = tid; i < b; i += blockDim.x) G[i * (b + 1) + i] += shift;
-  }
-  factor();
-  mul_t();
-  reduce(kq > 0, true);                        // D
-  set_diag0();
-  if (kq > 0) {
-    for (int e = tid; e < b * b; e += blockDim.x) {
-      const int i = e / b, j = e % b;
-      float s = 0.f;
-      for (int t = 0; t < kq; ++t) s = fmaf(P[t * bp + i], P[t * bp + j], s);
-      G[i * (b + 1) + j] -= s;
+    // shifted Cholesky QR, then two Cholesky QR passes (the first with the
+    // re-projection)
+    {
+      float tr = 0.f;
+      for (int i = tid; i < b; i += blockDim.x) tr += G[i * (b + 1) + i];
+      tr = block_sum(tr, red);
+      const float shift = 11.f * ((float)a.m * b + (float)b * (b + 1)) * 5.9604645e-08f * tr;
+      __syncthreads();
+      for (int i = tid; i < b; i += blockDim.x) G[i * (b + 1) + i] += shift;
     }
-  }
-  factor();
-  if (kq > 0) sub_q();
-  mul_t();
-  reduce(false, true);                         // E
-  set_diag0();
-  factor();
-  mul_t();                                     // F
-  for (int x = tid; x < rc * b; x += blockDim.x) {
-    const int i = x / b, j = x % b;
-    a.Q[(r0 + i) * a.ldq + kq + j] = Zc[i * bp + j];
+    if (c < b)
+      pchol_select_cta(G, b + 1, b, c, diag0, R, b, T, bp, bp, perm, dsw, a.flag, report);
+    else
+      factor(b, a.flag, report);
+    mul_t();
+    reduce(kq > 0, true);                      // D
+    set_diag0();
+    sub_ptp(c);
+    factor(c, a.flag, report);
+    if (kq > 0) sub_q();
+    mul_t();
+    reduce(false, true);                       // E
+    set_diag0();
+    factor(c, a.flag, report);
+    mul_t();                                   // F
+    write_q(c);
   }
   cl.sync();   // no CTA leaves while others may still read its shares
 }
@@ -234,11 +268,11 @@ bool orth_cluster_ok(int64_t m, int kq, int b) {
   return oc_smem_floats(kq, b, rows) * 4 <= 200 * 1024;
 }
 
-cudaError_t launch_orth_cluster(const float* W, int64_t ldw, int64_t m, int b, float* Q, int64_t ldq, int kq,
+cudaError_t launch_orth_cluster(const float* W, int64_t ldw, int64_t m, int b, int c, float* Q, int64_t ldq, int kq,
                                 int* flag, cudaStream_t st) {
-  if (!orth_cluster_ok(m, kq, b)) return cudaErrorInvalidValue;
+  if (!orth_cluster_ok(m, kq, b) || c < 1 || c > b) return cudaErrorInvalidValue;
   ClusterOrthArgs a;
-  a.W = W; a.ldw = ldw; a.Q = Q; a.ldq = ldq; a.kq = kq; a.m = m; a.b = b; a.flag = flag;
+  a.W = W; a.ldw = ldw; a.Q = Q; a.ldq = ldq; a.kq = kq; a.m = m; a.b = b; a.c = c; a.flag = flag;
   const int nc = oc_cluster_size(m);
   a.rows = ceil_div(m, nc);
   const size_t smem = oc_smem_floats(kq, b, a.rows) * 4;

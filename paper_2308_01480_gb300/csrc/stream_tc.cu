@@ -660,3 +660,41 @@ cudaError_t tc_ga(const __nv_bfloat16* C, int64_t m, int64_t n, const float* X, 
 }
 
 }  // namespace ttr
+
+// ---------------------------------------------------------------- test aid
+namespace ttr {
+
+// One thread waits, with the bounded wait every tensor-core kernel uses, on
+// an mbarrier that nothing ever arrives on; the wait gives up after about
+// two seconds and the status word records TT_ETIMEOUT.
+__global__ void k_wait_selftest(int* status) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::fence_barrier_init();
+    int no_abort = 0;
+    if (!tc::mbar_wait(&bar, 0, &no_abort)) set_status(status, TT_ETIMEOUT);
+  }
+}
+
+}  // namespace ttr
+
+extern "C" tt_status tt_debug_wait_timeout(void* workspace, void* stream) {
+  if (!workspace) {
+    ttr::set_last_error("workspace is NULL");
+    return TT_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  int* status = (int*)workspace;
+  if (cudaMemsetAsync(status, 0, 256, st) != cudaSuccess) {
+    ttr::set_last_error("cudaMemsetAsync failed");
+    return TT_ECUDA;
+  }
+  ttr::k_wait_selftest<<<1, 32, 0, st>>>(status);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    ttr::set_last_error(cudaGetErrorString(e));
+    return TT_ECUDA;
+  }
+  return TT_OK;
+}
