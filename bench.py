@@ -34,11 +34,7 @@ CONFIG_ID = 3
 # ncu DRAM traffic (read + write bytes per launch) of the dominant kernel, by
 # kernel family, with the profile summary it comes from; None when the
 # kernel changed after the capture.
-NCU_TRAFFIC = {
-    # 13 launches of one decomposition: 908 MB of dram__bytes_read.sum +
-    # dram__bytes_write.sum (ncu, this bench's command, -k regex:k_tc_stream)
-    "proj_tc": 69.9e6,
-}
+NCU_TRAFFIC = {}
 
 
 def parse():

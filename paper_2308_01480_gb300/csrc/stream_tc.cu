@@ -28,6 +28,7 @@ using namespace tc;
 
 constexpr int TC_THREADS = 192;
 constexpr int SMEM_LIMIT = 227 * 1024;
+constexpr int SMEM_HALF = 113 * 1024;   // two CTAs per SM
 
 enum : int { OPK_GRAM = 0, OPK_CS = 1, OPK_PROJ = 2, OPK_GA = 3 };
 
@@ -81,7 +82,7 @@ __device__ __forceinline__ void tc_abort(TcShared* sh, int* status) {
 
 // ---------------------------------------------------------------- kernel
 template <int OP>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+__global__ void __launch_bounds__(TC_THREADS, 2)
 k_tc_stream(const __grid_constant__ CUtensorMap mapC, const __grid_constant__ CUtensorMap mapB, TcParams p) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -128,8 +129,6 @@ k_tc_stream(const __grid_constant__ CUtensorMap mapC, const __grid_constant__ CU
   // =========================================================== producer
   if (warp == 0) {
     if (lane == 0) {
-      int64_t last_fill[8];
-      for (int s = 0; s < 8; ++s) last_fill[s] = -1;
       bool ok = true;
       if (OP == OPK_GA || (OP == OPK_PROJ && p.x_resident)) {
         // resident X^T: mpad/64 boxes of (64 x npad)
@@ -164,14 +163,15 @@ k_tc_stream(const __grid_constant__ CUtensorMap mapC, const __grid_constant__ CU
               tma_load_2d(st + 2 * (size_t)p.c_box_bytes + (size_t)kb * p.x_box_bytes, &mapB, &sh->full[s],
                           ch * p.chunk_rows + 64 * kb, 0);
           }
-          last_fill[s] = fill;
         }
       }
-      // drain: every issued copy must land before the CTA can exit
+      // drain: every issued copy must land before the CTA can exit (the
+      // last fill of stage s is the largest f < fill with f = s mod S)
       for (int s = 0; s < S; ++s)
-        if (last_fill[s] >= 0) {
+        if (s < fill) {
+          const int64_t last = s + (int64_t)S * ((fill - 1 - s) / S);
           int zero = 0;
-          mbar_wait(&sh->full[s], (uint32_t)((last_fill[s] / S) & 1), &zero);
+          mbar_wait(&sh->full[s], (uint32_t)((last / S) & 1), &zero);
         }
       if (OP == OPK_GA || (OP == OPK_PROJ && p.x_resident)) { int zero = 0; mbar_wait(&sh->xfull, 0, &zero); }
     }
@@ -321,8 +321,13 @@ k_tc_stream(const __grid_constant__ CUtensorMap mapC, const __grid_constant__ CU
         const uint32_t use = (uint32_t)(it >> 1);
         if (!mbar_wait(&sh->dfull[buf], use & 1, abortp)) { tc_abort(sh, p.status); break; }
         tc_fence_after();
-        float v[64];
-        for (int c0 = 0; c0 < p.npad; c0 += 16) tmem_ld16(tmem + lane_addr + (uint32_t)(buf * 64 + c0), v + c0);
+        // this lane's 64 accumulator columns of the tile (npad <= 64)
+        uint32_t r[64];
+        const uint32_t ta = tmem + lane_addr + (uint32_t)(buf * 64);
+        tmem_ld16<0>(ta, r);
+        if (p.npad > 16) tmem_ld16<16>(ta + 16, r);
+        if (p.npad > 32) tmem_ld16<32>(ta + 32, r);
+        if (p.npad > 48) tmem_ld16<48>(ta + 48, r);
         tmem_wait_ld();
         tc_fence_before();
         __syncwarp();
@@ -331,13 +336,27 @@ k_tc_stream(const __grid_constant__ CUtensorMap mapC, const __grid_constant__ CU
         const int64_t col = tile * 128 + lrow;
         if (OP == OPK_PROJ) {
           if (col < p.n) {
-            for (int c = 0; c < p.b; ++c) {
-              float x = v[c];
-              if (p.split_hi_lo) x += v[c + p.lo_off];
-              if (p.out_bf16)
-                reinterpret_cast<__nv_bfloat16*>(p.out)[(int64_t)c * p.ld_out + col] = __float2bfloat16_rn(x);
-              else
-                reinterpret_cast<float*>(p.out)[(int64_t)c * p.ld_out + col] = x;
+            if (p.split_hi_lo) {
+              // S[c] = hi part (column c) + lo part (column c + 32), c < b <= 32
+#pragma unroll
+              for (int c = 0; c < 32; ++c)
+                if (c < p.b) {
+                  const float x = __uint_as_float(r[c]) + __uint_as_float(r[c + 32]);
+                  if (p.out_bf16)
+                    reinterpret_cast<__nv_bfloat16*>(p.out)[(int64_t)c * p.ld_out + col] = __float2bfloat16_rn(x);
+                  else
+                    reinterpret_cast<float*>(p.out)[(int64_t)c * p.ld_out + col] = x;
+                }
+            } else {
+#pragma unroll
+              for (int c = 0; c < 64; ++c)
+                if (c < p.b) {
+                  const float x = __uint_as_float(r[c]);
+                  if (p.out_bf16)
+                    reinterpret_cast<__nv_bfloat16*>(p.out)[(int64_t)c * p.ld_out + col] = __float2bfloat16_rn(x);
+                  else
+                    reinterpret_cast<float*>(p.out)[(int64_t)c * p.ld_out + col] = x;
+                }
             }
           }
         } else {
@@ -345,15 +364,19 @@ k_tc_stream(const __grid_constant__ CUtensorMap mapC, const __grid_constant__ CU
           if (!mbar_wait(&sh->tempty[buf], (use & 1) ^ 1, abortp)) { tc_abort(sh, p.status); break; }
           uint8_t* tb = tbuf + (size_t)buf * p.t_bytes;
           const int kgrp = lrow >> 3, krow = lrow & 7;
-          for (int g = 0; g < p.npad / 8; ++g) {
-            uint32_t w[4];
 #pragma unroll
-            for (int h = 0; h < 4; ++h) {
-              const __nv_bfloat162 pr = __floats2bfloat162_rn(v[8 * g + 2 * h], v[8 * g + 2 * h + 1]);
-              w[h] = *reinterpret_cast<const uint32_t*>(&pr);
+          for (int g = 0; g < 8; ++g)
+            if (g < p.npad / 8) {
+              uint32_t w[4];
+#pragma unroll
+              for (int h = 0; h < 4; ++h) {
+                const __nv_bfloat162 pr =
+                    __floats2bfloat162_rn(__uint_as_float(r[8 * g + 2 * h]), __uint_as_float(r[8 * g + 2 * h + 1]));
+                w[h] = *reinterpret_cast<const uint32_t*>(&pr);
+              }
+              *reinterpret_cast<uint4*>(tb + (size_t)g * 2048 + kgrp * 128 + krow * 16) =
+                  make_uint4(w[0], w[1], w[2], w[3]);
             }
-            *reinterpret_cast<uint4*>(tb + (size_t)g * 2048 + kgrp * 128 + krow * 16) = make_uint4(w[0], w[1], w[2], w[3]);
-          }
           fence_proxy_async_smem();
           __syncwarp();
           if (lane == 0) mbar_arrive(&sh->tfull[buf]);
@@ -361,21 +384,25 @@ k_tc_stream(const __grid_constant__ CUtensorMap mapC, const __grid_constant__ CU
       }
     }
     if (OP != OPK_PROJ) {
-      // final accumulators -> per-CTA partials (rows of this CTA, FP32)
+      // final accumulators -> per-CTA partials (rows of this CTA, FP32),
+      // 16 columns at a time
       if (mbar_wait(&sh->zfull, 0, abortp)) {
         tc_fence_after();
         float* P = reinterpret_cast<float*>(p.out) + (int64_t)blockIdx.x * p.m * p.b;
         const int mbn = (OP == OPK_GRAM) ? 1 : p.mb;
         const uint32_t zoff = (OP == OPK_GA) ? 128u : 0u;
+        const int ncol = (OP == OPK_GRAM) ? (int)p.m : p.b;
         for (int b = 0; b < mbn; ++b) {
-          float v[64];
-          for (int c0 = 0; c0 < p.npad; c0 += 16)
-            tmem_ld16(tmem + lane_addr + zoff + (uint32_t)(b * p.npad + c0), v + c0);
-          tmem_wait_ld();
           const int64_t row = row0 + (int64_t)b * 128 + lrow;
-          if (row < p.m && !*abortp) {
-            const int ncol = (OP == OPK_GRAM) ? (int)p.m : p.b;
-            for (int c = 0; c < ncol; ++c) P[row * ncol + c] = v[c];
+          for (int c0 = 0; c0 < p.npad; c0 += 16) {
+            uint32_t r[16];
+            tmem_ld16<0>(tmem + lane_addr + zoff + (uint32_t)(b * p.npad + c0), r);
+            tmem_wait_ld();
+            if (row < p.m && !*abortp) {
+#pragma unroll
+              for (int i = 0; i < 16; ++i)
+                if (c0 + i < ncol) P[row * ncol + c0 + i] = __uint_as_float(r[i]);
+            }
           }
         }
         tc_fence_before();
@@ -446,9 +473,20 @@ size_t tc_smem_bytes(const TcParams& p) {
 // Rows of a C box: the 16-rounded row count when it is below 128.
 int box_rows_for(int64_t m, int cap) { return (int)imin(cap, (m + 15) / 16 * 16); }
 
-int stages_for(const TcParams& p, int maxst) {
-  const size_t fixed = 1024 + (size_t)p.slack_bytes + p.x_res_bytes + 2 * (size_t)p.t_bytes + sizeof(TcShared) + 64;
-  return (int)imin(maxst, (int64_t)((SMEM_LIMIT - fixed) / p.stage_bytes));
+// Ring depth and residency: two CTAs per SM (each with half the shared
+// memory) whenever a ring of at least three stages fits, since two
+// independent TMA -> MMA -> epilogue pipelines per SM keep more bytes in
+// flight than one deeper ring; else one CTA with the whole shared memory.
+// Sets p.stages; returns the CTAs per SM.
+int choose_residency(TcParams& p, int maxst) {
+  const int64_t fixed = 1024 + (int64_t)p.slack_bytes + p.x_res_bytes + 2 * (int64_t)p.t_bytes + sizeof(TcShared) + 64;
+  const int64_t half = (SMEM_HALF - fixed) / p.stage_bytes;
+  if (half >= 3) {
+    p.stages = (int)imin(maxst, half);
+    return 2;
+  }
+  p.stages = (int)imin(maxst, (SMEM_LIMIT - fixed) / p.stage_bytes);
+  return 1;
 }
 
 template <int OP>
@@ -497,47 +535,51 @@ cudaError_t prep_xt(const float* X, int64_t ldx, int64_t m, int b, int split, in
 // ---------------------------------------------------------------- public launchers
 bool tc_shape_ok(int64_t m, int64_t n) { return n % 8 == 0 && n >= 64 && m >= 1 && n < (int64_t(1) << 31); }
 
-int64_t tc_gram_partials(int64_t m, int64_t n) {
-  const int64_t tiles = ceil_div(n, 128);
-  return imin(tiles, num_sms()) * m * m;
-}
-
-cudaError_t tc_gram(const __nv_bfloat16* C, int64_t m, int64_t n, float* partials, float* out, int* status,
-                    cudaStream_t st) {
-  if (m > 128 || !tc_shape_ok(m, n)) return cudaErrorInvalidValue;
+// Launch shape of a pass: parameters, CTAs per SM, grid size.
+struct TcShape {
   TcParams p{};
+  int per_sm = 1;
+  int ctas = 0;
+};
+
+TcShape gram_shape(int64_t m, int64_t n) {
+  TcShape t;
+  TcParams& p = t.p;
   p.m = m; p.n = n; p.b = (int)m; p.npad = pad16((int)m); p.mb = 1; p.kb = 2;
   p.c_box_rows = box_rows_for(m, 128); p.c_box_bytes = p.c_box_rows * 128;
   p.stage_bytes = 2 * p.c_box_bytes;
   p.slack_bytes = 16384;
   p.tiles = ceil_div(n, 128);
-  p.stages = stages_for(p, 8);
-  p.out = partials; p.status = status; p.row_groups = 1;
+  p.row_groups = 1;
+  t.per_sm = choose_residency(p, 8);
+  t.ctas = (int)imin(p.tiles, (int64_t)num_sms() * t.per_sm);
+  return t;
+}
+
+int64_t tc_gram_partials(int64_t m, int64_t n) { return (int64_t)gram_shape(m, n).ctas * m * m; }
+
+cudaError_t tc_gram(const __nv_bfloat16* C, int64_t m, int64_t n, float* partials, float* out, int* status,
+                    cudaStream_t st) {
+  if (m > 128 || !tc_shape_ok(m, n)) return cudaErrorInvalidValue;
+  TcShape t = gram_shape(m, n);
+  TcParams& p = t.p;
+  p.out = partials; p.status = status;
   CUtensorMap mc;
   cudaError_t e = make_map(&mc, C, m, n, n, p.c_box_rows);
   if (e != cudaSuccess) return e;
-  const int ctas = (int)imin(p.tiles, num_sms());
   {
     ProfScope prof("gram_tc", st, (double)m * n * 2, 2.0 * m * m * n);
     note_launch("gram_tc");
-    e = launch_tc<OPK_GRAM>(mc, mc, p, ctas, st);
+    e = launch_tc<OPK_GRAM>(mc, mc, p, t.ctas, st);
   }
   if (e != cudaSuccess) return e;
-  return launch_reduce_partials(partials, ctas, m, (int)m, out, m, st);
+  return launch_reduce_partials(partials, t.ctas, m, (int)m, out, m, st);
 }
 
 // Y (m x b, ld ldo) = C S^T with S (b x n BF16, row stride lds).
-int64_t tc_cs_partials(int64_t m, int64_t n, int b) {
-  const int64_t groups = ceil_div(m, 512);
-  const int64_t tiles = ceil_div(n, 64);
-  const int64_t per = imax(1, imin(tiles, num_sms() / groups));
-  return groups * per * m * b;
-}
-
-cudaError_t tc_cs(const __nv_bfloat16* C, int64_t m, int64_t n, const __nv_bfloat16* S, int64_t lds, int b,
-                  float* partials, float* out, int64_t ldo, int* status, cudaStream_t st) {
-  if (b > 64 || !tc_shape_ok(m, n) || lds % 8 != 0) return cudaErrorInvalidValue;
-  TcParams p{};
+TcShape cs_shape(int64_t m, int64_t n, int b) {
+  TcShape t;
+  TcParams& p = t.p;
   p.m = m; p.n = n; p.b = b; p.npad = pad16(b); p.kb = 1;
   p.row_groups = ceil_div(m, 512);
   p.mb = (int)imin(4, ceil_div(ceil_div(m, p.row_groups), 128));
@@ -546,25 +588,35 @@ cudaError_t tc_cs(const __nv_bfloat16* C, int64_t m, int64_t n, const __nv_bfloa
   p.stage_bytes = (p.mb * p.c_box_bytes + p.s_box_bytes + 1023) / 1024 * 1024;
   p.slack_bytes = 16384;
   p.tiles = ceil_div(n, 64);
-  p.stages = stages_for(p, 8);
+  t.per_sm = choose_residency(p, 8);
+  const int64_t per = imax(1, imin(p.tiles, (int64_t)num_sms() * t.per_sm / p.row_groups));
+  t.ctas = (int)(per * p.row_groups);
+  return t;
+}
+
+int64_t tc_cs_partials(int64_t m, int64_t n, int b) { return (int64_t)cs_shape(m, n, b).ctas * m * b; }
+
+cudaError_t tc_cs(const __nv_bfloat16* C, int64_t m, int64_t n, const __nv_bfloat16* S, int64_t lds, int b,
+                  float* partials, float* out, int64_t ldo, int* status, cudaStream_t st) {
+  if (b > 64 || !tc_shape_ok(m, n) || lds % 8 != 0) return cudaErrorInvalidValue;
+  TcShape t = cs_shape(m, n, b);
+  TcParams& p = t.p;
   if (p.stages < 2) return cudaErrorInvalidValue;
   p.out = partials; p.status = status;
   CUtensorMap mc, ms;
   cudaError_t e = make_map(&mc, C, m, n, n, p.c_box_rows);
   if (e == cudaSuccess) e = make_map(&ms, S, b, n, lds, p.npad);
   if (e != cudaSuccess) return e;
-  const int64_t per = imax(1, imin(p.tiles, num_sms() / p.row_groups));
-  const int ctas = (int)(per * p.row_groups);
+  const int per = t.ctas / (int)p.row_groups;
   {
     ProfScope prof("cs_tc", st, (double)m * n * 2 + (double)b * n * 2, 2.0 * m * n * b);
     note_launch("cs_tc");
-    e = launch_tc<OPK_CS>(mc, ms, p, ctas, st);
+    e = launch_tc<OPK_CS>(mc, ms, p, t.ctas, st);
   }
   if (e != cudaSuccess) return e;
   // partial slot = CTA index; rows outside a CTA's row group are not written,
   // so each group's partials are reduced over its own CTAs
-  return launch_reduce_partials_grouped(partials, (int)per, (int)p.row_groups, m, b, (int64_t)p.mb * 128, out, ldo,
-                                        st);
+  return launch_reduce_partials_grouped(partials, per, (int)p.row_groups, m, b, (int64_t)p.mb * 128, out, ldo, st);
 }
 
 // S (b x n, row stride lds, BF16 or FP32) = X^T C; X m x b FP32 (ld ldx).
@@ -575,10 +627,9 @@ size_t tc_proj_scratch_bytes(int64_t m, int b, int split) {
   return (size_t)rows * ldt * 2 + 256;
 }
 
-cudaError_t tc_proj(const __nv_bfloat16* C, int64_t m, int64_t n, const float* X, int64_t ldx, int b, int split,
-                    void* S, int s_bf16, int64_t lds, void* scratch, int* status, cudaStream_t st) {
-  if (!tc_shape_ok(m, n) || (split ? b > 32 : b > 64)) return cudaErrorInvalidValue;
-  TcParams p{};
+TcShape proj_shape(int64_t m, int64_t n, int b, int split) {
+  TcShape t;
+  TcParams& p = t.p;
   p.m = m; p.n = n; p.b = b;
   p.split_hi_lo = split;
   p.lo_off = split ? 32 : 0;
@@ -593,7 +644,16 @@ cudaError_t tc_proj(const __nv_bfloat16* C, int64_t m, int64_t n, const float* X
   p.x_res_bytes = p.x_resident ? (p.mpad / 64) * p.x_box_bytes : 0;
   p.stage_bytes = (2 * p.c_box_bytes + (p.x_resident ? 0 : 2 * p.x_box_bytes) + 1023) / 1024 * 1024;
   p.tiles = ceil_div(n, 128);
-  p.stages = stages_for(p, 8);
+  t.per_sm = choose_residency(p, 8);
+  t.ctas = (int)imin(p.tiles, (int64_t)num_sms() * t.per_sm);
+  return t;
+}
+
+cudaError_t tc_proj(const __nv_bfloat16* C, int64_t m, int64_t n, const float* X, int64_t ldx, int b, int split,
+                    void* S, int s_bf16, int64_t lds, void* scratch, int* status, cudaStream_t st) {
+  if (!tc_shape_ok(m, n) || (split ? b > 32 : b > 64)) return cudaErrorInvalidValue;
+  TcShape t = proj_shape(m, n, b, split);
+  TcParams& p = t.p;
   p.out_bf16 = s_bf16; p.ld_out = lds; p.out = S; p.status = status;
   const int rows = p.npad;
   const int64_t ldt = (m + 7) / 8 * 8;
@@ -604,10 +664,9 @@ cudaError_t tc_proj(const __nv_bfloat16* C, int64_t m, int64_t n, const float* X
   e = make_map(&mc, C, m, n, n, p.chunk_rows);
   if (e == cudaSuccess) e = make_map(&mx, Xt, rows, m, ldt, p.npad);
   if (e != cudaSuccess) return e;
-  const int ctas = (int)imin(p.tiles, num_sms());
   ProfScope prof("proj_tc", st, (double)m * n * 2 + (double)b * n * (s_bf16 ? 2 : 4), 2.0 * m * n * p.npad);
   note_launch("proj_tc");
-  return launch_tc<OPK_PROJ>(mc, mx, p, ctas, st);
+  return launch_tc<OPK_PROJ>(mc, mx, p, t.ctas, st);
 }
 
 // Y (m x b, ld ldo) = C (C^T X), m <= 256, b <= 64; X m x b FP32 (ld ldx).
@@ -618,14 +677,9 @@ size_t tc_ga_scratch_bytes(int64_t m, int b) {
   return (size_t)pad16(b) * ldt * 2 + 256;
 }
 
-int64_t tc_ga_partials(int64_t m, int64_t n, int b) {
-  return imin(ceil_div(n, 128), num_sms()) * m * b;
-}
-
-cudaError_t tc_ga(const __nv_bfloat16* C, int64_t m, int64_t n, const float* X, int64_t ldx, int b, float* partials,
-                  float* out, int64_t ldo, void* scratch, int* status, cudaStream_t st) {
-  if (!tc_ga_ok(m, n, b)) return cudaErrorInvalidValue;
-  TcParams p{};
+TcShape ga_shape(int64_t m, int64_t n, int b) {
+  TcShape t;
+  TcParams& p = t.p;
   p.m = m; p.n = n; p.b = b; p.npad = pad16(b);
   p.kb = 2; p.row_groups = 1;
   p.c_box_rows = box_rows_for(m, 256);
@@ -638,7 +692,18 @@ cudaError_t tc_ga(const __nv_bfloat16* C, int64_t m, int64_t n, const float* X, 
   p.stage_bytes = 2 * p.c_box_bytes;
   p.slack_bytes = 16384;
   p.tiles = ceil_div(n, 128);
-  p.stages = stages_for(p, 8);
+  t.per_sm = choose_residency(p, 8);
+  t.ctas = (int)imin(p.tiles, (int64_t)num_sms() * t.per_sm);
+  return t;
+}
+
+int64_t tc_ga_partials(int64_t m, int64_t n, int b) { return (int64_t)ga_shape(m, n, b).ctas * m * b; }
+
+cudaError_t tc_ga(const __nv_bfloat16* C, int64_t m, int64_t n, const float* X, int64_t ldx, int b, float* partials,
+                  float* out, int64_t ldo, void* scratch, int* status, cudaStream_t st) {
+  if (!tc_ga_ok(m, n, b)) return cudaErrorInvalidValue;
+  TcShape t = ga_shape(m, n, b);
+  TcParams& p = t.p;
   if (p.stages < 2) return cudaErrorInvalidValue;
   p.out = partials; p.status = status;
   const int64_t ldt = (m + 7) / 8 * 8;
@@ -649,14 +714,13 @@ cudaError_t tc_ga(const __nv_bfloat16* C, int64_t m, int64_t n, const float* X, 
   e = make_map(&mc, C, m, n, n, p.c_box_rows);
   if (e == cudaSuccess) e = make_map(&mx, Xt, p.npad, m, ldt, p.npad);
   if (e != cudaSuccess) return e;
-  const int ctas = (int)imin(p.tiles, num_sms());
   {
     ProfScope prof("gram_apply_tc", st, (double)m * n * 2, 4.0 * m * n * b);
     note_launch("gram_apply_tc");
-    e = launch_tc<OPK_GA>(mc, mx, p, ctas, st);
+    e = launch_tc<OPK_GA>(mc, mx, p, t.ctas, st);
   }
   if (e != cudaSuccess) return e;
-  return launch_reduce_partials(partials, ctas, m, b, out, ldo, st);
+  return launch_reduce_partials(partials, t.ctas, m, b, out, ldo, st);
 }
 
 }  // namespace ttr
