@@ -1,7 +1,7 @@
 // Top-r eigenpairs of the small symmetric Rayleigh-Ritz matrix (Alg. 3
 // steps 6-8), k <= 160, in two one-CTA kernels.  The first holds H in
-// registers: NW warps, thread (warp w, lane l) owning the entries
-// (w + NW a, l + 32 c), a < 32 KT / NW, c < KT = ceil(k / 32).  The second (16 warps, so
+// registers: 32 warps, thread (warp w, lane l) owning the entries
+// (l + 32 a, w + 32 c), a, c < KT = ceil(k / 32).  The second (16 warps, so
 // that the register-resident Cholesky of step 4 fits) does steps 2-5.
 //
 //  1. Householder tridiagonalisation.  Per column two barriers: the owners
@@ -144,133 +144,126 @@ __host__ __device__ inline size_t er_smem_floats(int KM, int k, int r) {
 }
 
 // Step 1 in one CTA of 32 warps: T = (d, e) and the reflectors (row j of
-// Vg = v_j, tau[j]) to global scratch.
-template <int KT, int NW>
-__global__ void __launch_bounds__(32 * NW, 1) k_eig_tridiag(const float* __restrict__ Hin, int64_t ldh, int k,
-                                                           float* __restrict__ Vg, float* __restrict__ tau_g,
-                                                           float* __restrict__ d_g, float* __restrict__ e_g) {
+// Vg = v_j, tau[j]) to global scratch.  Thread (warp w, lane l) holds the
+// entries (l + 32 a, w + 32 c), a, c < KT, so that column j lives in warp
+// j mod 32 alone.  Per column, four barriers separate: that warp publishes
+// the column; warp 0 forms the reflector v (and tau); every thread forms
+// the partial products of its rows with v over its columns, plus its share
+// of v^T H v; the sums give p = tau H v; every thread applies the rank-2
+// update H -= v w^T + w v^T, w = p - (tau/2)(v^T p) v, to its entries.
+template <int KT>
+__global__ void __launch_bounds__(1024, 1) k_eig_tridiag(const float* __restrict__ Hin, int64_t ldh, int k,
+                                                        float* __restrict__ Vg, float* __restrict__ tau_g,
+                                                        float* __restrict__ d_g, float* __restrict__ e_g) {
   constexpr int KM = 32 * KT;
-  constexpr int NT = 32 * NW;
-  constexpr int RA = KM / NW;
-  __shared__ __align__(16) float xcol[2 * KM];
-  __shared__ __align__(16) float pbuf[2 * KM];
-  float* Vs = Vg;
-  float* tau = tau_g;
-  float* d = d_g;
-  float* e = e_g;
-  const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 5;
+  __shared__ __align__(16) float xcol[KM];
+  __shared__ __align__(16) float vs[KM];
+  __shared__ __align__(16) float ps[KM];
+  __shared__ float pp[32][KM + 1];
+  __shared__ float wsum[32];
+  __shared__ float scal[2];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
 
-  // ---------------------------------------------------------------- 1
-  float A[RA][KT];
-  sfor<RA>([&](auto a) {
+  float A[KT][KT];   // A[a][c] = H[lane + 32 a][w + 32 c]
+  sfor<KT>([&](auto a) {
     sfor<KT>([&](auto c) {
-      const int i = ty + NW * a, j = lane + 32 * c;
+      const int i = lane + 32 * a, j = w + 32 * c;
       A[a][c] = (i < k && j < k) ? 0.5f * (Hin[(int64_t)i * ldh + j] + Hin[(int64_t)j * ldh + i]) : 0.f;
     });
   });
-  for (int x = tid; x < k * k; x += NT) Vs[x] = 0.f;
+  for (int x = tid; x < k * k; x += 1024) Vg[x] = 0.f;
   __syncthreads();
   for (int j = 0; j + 2 < k; ++j) {
-    float* xc = xcol + (j & 1) * KM;
-    float* pb = pbuf + (j & 1) * KM;
-    if (lane == (j & 31)) {
-      sfor<RA>([&](auto a) {
+    // 1. column j (rows > j) from its warp
+    if (w == (j & 31)) {
+      sfor<KT>([&](auto a) {
         float val = 0.f;
         sfor<KT>([&](auto c) {
           if (c == (j >> 5)) val = A[a][c];
         });
-        const int i = ty + NW * a;
-        xc[i] = (i > j && i < k) ? val : 0.f;
-        if (i == j) d[j] = val;
+        const int i = lane + 32 * a;
+        xcol[i] = (i > j && i < k) ? val : 0.f;
+        if (i == j) d_g[j] = val;
       });
     }
     __syncthreads();
-    float part = 0.f;
-#pragma unroll
-    for (int c = 0; c < KT; ++c) {
-      const int i = lane + 32 * c;
-      if (i >= j + 2) {
-        const float x = xc[i];
-        part = fmaf(x, x, part);
-      }
-    }
-    const float sigma = warp_sum(part);
-    const float x0 = xc[j + 1];
-    float t = 0.f, iv = 0.f, beta = x0;
-    if (sigma > 0.f) {
-      const float mu = sqrtf(fmaf(x0, x0, sigma));
-      const float v0 = (x0 <= 0.f) ? x0 - mu : __fdividef(-sigma, x0 + mu);
-      t = __fdividef(2.f * v0 * v0, fmaf(v0, v0, sigma));
-      beta = mu;
-      iv = __fdividef(1.f, v0);
-    }
-    if (tid == 0) {
-      tau[j] = t;
-      e[j] = beta;
-    }
-    if (t == 0.f) continue;              // same decision in every thread
-    float vc[KT];
-#pragma unroll
-    for (int c = 0; c < KT; ++c) {
-      const int i = lane + 32 * c;
-      vc[c] = (i == j + 1) ? 1.f : ((i > j + 1) ? xc[i] * iv : 0.f);
-    }
-    {
-      float s[RA];
-      sfor<RA>([&](auto a) {
-        float acc = 0.f;
-        sfor<KT>([&](auto c) { acc = fmaf(A[a][c], vc[c], acc); });
-        s[a] = acc;
-      });
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int a = 0; a < RA; ++a) s[a] += __shfl_xor_sync(0xffffffffu, s[a], o);
-      if (lane == 0) {
-#pragma unroll
-        for (int a = 0; a < RA; ++a) {
-          const int i = ty + NW * a;
-          pb[i] = (i > j && i < k) ? t * s[a] : 0.f;
-        }
-      }
-    }
-    if (ty == 0) {
-#pragma unroll
-      for (int c = 0; c < KT; ++c) {
+    // 2. the reflector, once
+    if (w == 0) {
+      float part = 0.f;
+      sfor<KT>([&](auto c) {
         const int i = lane + 32 * c;
-        if (i < k) Vs[(size_t)j * k + i] = vc[c];
+        if (i >= j + 2) part = fmaf(xcol[i], xcol[i], part);
+      });
+      const float sigma = warp_sum(part);
+      const float x0 = xcol[j + 1];
+      float t = 0.f, iv = 0.f, beta = x0;
+      if (sigma > 0.f) {
+        const float mu = sqrtf(fmaf(x0, x0, sigma));
+        const float v0 = (x0 <= 0.f) ? x0 - mu : __fdividef(-sigma, x0 + mu);
+        t = __fdividef(2.f * v0 * v0, fmaf(v0, v0, sigma));
+        beta = mu;
+        iv = __fdividef(1.f, v0);
+      }
+      sfor<KT>([&](auto c) {
+        const int i = lane + 32 * c;
+        const float v = (i == j + 1) ? 1.f : ((i > j + 1) ? xcol[i] * iv : 0.f);
+        vs[i] = v;
+        if (i < k) Vg[(size_t)j * k + i] = (t != 0.f) ? v : 0.f;
+      });
+      if (lane == 0) {
+        scal[0] = t;
+        tau_g[j] = t;
+        e_g[j] = beta;
       }
     }
     __syncthreads();
-    float kp = 0.f;
-#pragma unroll
-    for (int c = 0; c < KT; ++c) kp = fmaf(vc[c], pb[lane + 32 * c], kp);
-    const float K = 0.5f * t * warp_sum(kp);
-    float wc[KT];
-#pragma unroll
-    for (int c = 0; c < KT; ++c) wc[c] = fmaf(-K, vc[c], pb[lane + 32 * c]);
-    // rank-2 update, one row of the tile at a time (v_i, w_i from shared)
-    sfor<RA>([&](auto a) {
-      const int i = ty + NW * a;
-      const float vi = (i == j + 1) ? 1.f : ((i > j + 1) ? xc[i] * iv : 0.f);
-      const float wi = fmaf(-K, vi, pb[i]);
-      sfor<KT>([&](auto c) { A[a][c] -= fmaf(vi, wc[c], wi * vc[c]); });
+    const float t = scal[0];
+    if (t == 0.f) continue;                 // the same decision in every thread
+    // 3. partial H v over this thread's columns, and its share of v^T H v
+    float vr[KT], vc[KT];
+    sfor<KT>([&](auto a) { vr[a] = vs[lane + 32 * a]; });
+    sfor<KT>([&](auto c) { vc[c] = vs[w + 32 * c]; });
+    float share = 0.f;
+    sfor<KT>([&](auto a) {
+      float acc = 0.f;
+      sfor<KT>([&](auto c) { acc = fmaf(A[a][c], vc[c], acc); });
+      pp[w][lane + 32 * a] = acc;
+      share = fmaf(vr[a], acc, share);
+    });
+    share = warp_sum(share);
+    if (lane == 0) wsum[w] = share;
+    __syncthreads();
+    // 4. p = tau H v (rows > j)
+    for (int i = tid; i < KM; i += 1024) {
+      float sum = 0.f;
+#pragma unroll 8
+      for (int q = 0; q < 32; ++q) sum += pp[q][i];
+      ps[i] = (i > j && i < k) ? t * sum : 0.f;
+    }
+    const float vhv = warp_sum(wsum[lane]);
+    const float K = 0.5f * t * t * vhv;     // (tau / 2) v^T p
+    __syncthreads();
+    // 5. rank-2 update
+    float wr[KT], wc[KT];
+    sfor<KT>([&](auto a) { wr[a] = fmaf(-K, vr[a], ps[lane + 32 * a]); });
+    sfor<KT>([&](auto c) { wc[c] = fmaf(-K, vc[c], ps[w + 32 * c]); });
+    sfor<KT>([&](auto a) {
+      sfor<KT>([&](auto c) { A[a][c] -= fmaf(vr[a], wc[c], wr[a] * vc[c]); });
     });
   }
   // trailing 2 x 2 (or 1 x 1) block, written by the owners of its entries
-  // (static tile indices keep the tile in registers)
-  sfor<RA>([&](auto a) {
+  sfor<KT>([&](auto a) {
     sfor<KT>([&](auto c) {
-      const int i = ty + NW * a, jj = lane + 32 * c;
-      if (k >= 2 && i == k - 2 && jj == k - 2) d[k - 2] = A[a][c];
-      if (k >= 2 && i == k - 1 && jj == k - 2) e[k - 2] = A[a][c];
-      if (i == k - 1 && jj == k - 1) d[k - 1] = A[a][c];
+      const int i = lane + 32 * a, jj = w + 32 * c;
+      if (k >= 2 && i == k - 2 && jj == k - 2) d_g[k - 2] = A[a][c];
+      if (k >= 2 && i == k - 1 && jj == k - 2) e_g[k - 2] = A[a][c];
+      if (i == k - 1 && jj == k - 1) d_g[k - 1] = A[a][c];
     });
   });
   if (tid == 0) {
-    if (k >= 2) tau[k - 2] = 0.f;
-    e[k - 1] = 0.f;
-    tau[k - 1] = 0.f;
+    if (k >= 2) tau_g[k - 2] = 0.f;
+    e_g[k - 1] = 0.f;
+    tau_g[k - 1] = 0.f;
   }
   __syncthreads();
 }
@@ -397,8 +390,10 @@ __global__ void __launch_bounds__(512, 1) k_eig_vectors(const float* __restrict_
     __syncthreads();
 
   // ---------------------------------------------------------------- 4
+    // one Cholesky QR pass keeps the vectors apart before the second solve;
+    // two make the final ones orthonormal to working accuracy
     if (tid == 0) *sflag = 0;
-    for (int pass = 0; pass < 2; ++pass) {
+    for (int pass = 0; pass < (round == 0 ? 1 : 2); ++pass) {
       for (int x = tid; x < r * r; x += NT) {
         const int a = x / r, b = x % r;
         if (b >= a) {
@@ -509,7 +504,7 @@ static cudaError_t launch_kt(const float* H, int64_t ldh, int k, int r, float* V
   float* tau = Vg + (size_t)k * k;
   float* d = tau + k;
   float* e = d + k;
-  k_eig_tridiag<KT, 32><<<1, 1024, 0, st>>>(H, ldh, k, Vg, tau, d, e);
+  k_eig_tridiag<KT><<<1, 1024, 0, st>>>(H, ldh, k, Vg, tau, d, e);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   const size_t smem = er_smem_floats(32 * KT, k, r) * 4;
