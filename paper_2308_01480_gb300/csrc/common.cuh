@@ -46,6 +46,16 @@ __device__ __forceinline__ float block_sum(float v, float* red) {
   return warp_sum(t);
 }
 
+// Raises a kernel's dynamic shared-memory limit, once per kernel, to the
+// largest the device allows next to the kernel's static shared memory.  One
+// fixed limit (rather than one per launch) keeps every launch captured in a
+// CUDA graph valid however the launches of other sizes that follow set it.
+cudaError_t raise_smem_limit_ptr(const void* kernel);
+template <typename Kernel>
+inline cudaError_t raise_smem_limit(Kernel kernel) {
+  return raise_smem_limit_ptr(reinterpret_cast<const void*>(kernel));
+}
+
 __host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 __host__ __device__ inline int64_t imin(int64_t a, int64_t b) { return a < b ? a : b; }
 __host__ __device__ inline int64_t imax(int64_t a, int64_t b) { return a > b ? a : b; }

@@ -451,7 +451,7 @@ cudaError_t launch_eig_top(const float* H, int64_t ldh, int k, int r, float* V, 
   size_t smem = eig_smem(k, r);
   const int work_in_smem = (smem + eig_work_bytes(k, r) + 16 <= 226 * 1024) ? 1 : 0;
   if (work_in_smem) smem += eig_work_bytes(k, r) + 16;
-  cudaFuncSetAttribute(k_eig_top, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  raise_smem_limit(k_eig_top);
   ProfScope prof("eig_top", st, 0, 0);
   note_launch("eig_top");
   k_eig_top<<<1, EIG_THREADS, smem, st>>>(H, ldh, k, r, V, scratch, evals, work_in_smem);
@@ -474,7 +474,7 @@ cudaError_t launch_tn(const float* A, int64_t lda, int ka, const float* B, int64
   int64_t rpc;
   const int ctas = rows_split(m, &rpc);
   const size_t smem = sizeof(float) * 16 * (size_t)(ka + kb);
-  cudaFuncSetAttribute(k_tn_partials, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  raise_smem_limit(k_tn_partials);
   {
     ProfScope prof("tn_small", st, 0, 2.0 * m * ka * kb);
     note_launch("tn_small");
@@ -491,7 +491,7 @@ cudaError_t launch_apply_basis(const float* Q, int64_t ldq, int64_t m, int k, co
   int64_t rpc = 8;
   const int ctas = (int)ceil_div(m, rpc);
   const size_t smem = sizeof(float) * (size_t)k * r;
-  cudaFuncSetAttribute(k_apply_basis, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  raise_smem_limit(k_apply_basis);
   ProfScope prof("apply_basis", st, 0, 2.0 * m * k * r);
   note_launch("apply_basis");
   k_apply_basis<<<ctas, 256, smem, st>>>(Q, ldq, m, k, V, r, U, core, rpc);

@@ -508,7 +508,7 @@ static cudaError_t launch_kt(const float* H, int64_t ldh, int k, int r, float* V
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   const size_t smem = er_smem_floats(32 * KT, k, r) * 4;
-  err = cudaFuncSetAttribute(k_eig_vectors<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  err = raise_smem_limit(k_eig_vectors<KT>);
   if (err != cudaSuccess) return err;
   k_eig_vectors<KT><<<1, 512, smem, st>>>(Vg, tau, d, e, k, r, V, ldv, evals);
   return cudaGetLastError();

@@ -224,7 +224,7 @@ cudaError_t launch_orth_fast(const float* W, int64_t ldw, int64_t m, int b, floa
   const size_t smem_main = sizeof(float) * ((size_t)a.rows * (kq + b) + (size_t)kq * b + (size_t)b * b);
   const size_t smem_fin = sizeof(float) * ((size_t)b * (b + 1) + 128 + 2 * (size_t)b * b);
   const size_t smem = smem_main > smem_fin ? smem_main : smem_fin;
-  cudaFuncSetAttribute(k_orth_phase, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  raise_smem_limit(k_orth_phase);
   cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
   ProfScope prof("orth_fast", st, 0, 0);

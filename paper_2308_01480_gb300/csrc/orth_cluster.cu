@@ -256,6 +256,8 @@ __global__ void __launch_bounds__(OC_THREADS) k_orth_cluster(ClusterOrthArgs a) 
 }
 
 // ------------------------------------------------------------ launcher
+constexpr int kOcSmemMax = 200 * 1024;
+
 static int oc_cluster_size(int64_t m) {
   if (m <= 64) return 1;
   if (m <= 256) return 4;
@@ -265,7 +267,7 @@ static int oc_cluster_size(int64_t m) {
 bool orth_cluster_ok(int64_t m, int kq, int b) {
   if (b > 64 || kq > 256) return false;
   const int64_t rows = ceil_div(m, oc_cluster_size(m));
-  return oc_smem_floats(kq, b, rows) * 4 <= 200 * 1024;
+  return oc_smem_floats(kq, b, rows) * 4 <= kOcSmemMax;
 }
 
 cudaError_t launch_orth_cluster(const float* W, int64_t ldw, int64_t m, int b, int c, float* Q, int64_t ldq, int kq,
@@ -278,7 +280,7 @@ cudaError_t launch_orth_cluster(const float* W, int64_t ldw, int64_t m, int b, i
   const size_t smem = oc_smem_floats(kq, b, a.rows) * 4;
   cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_orth_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = raise_smem_limit(k_orth_cluster);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(nc);

@@ -55,6 +55,25 @@ ProfScope::~ProfScope() {
   g_recs.push_back({fam_, a_, b_});
 }
 
+cudaError_t raise_smem_limit_ptr(const void* kernel) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, cudaError_t> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = done.find({dev, kernel});
+  if (it != done.end()) return it->second;
+  cudaFuncAttributes fa;
+  int optin = 0;
+  e = cudaFuncGetAttributes(&fa, kernel);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+  done[{dev, kernel}] = e;
+  return e;
+}
+
 }  // namespace ttr
 
 extern "C" {

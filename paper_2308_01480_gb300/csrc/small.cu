@@ -355,7 +355,7 @@ cudaError_t launch_orth_block(const float* Z, int64_t ldz, int64_t m, int zc, fl
   if (zc > 64 || c > zc) return cudaErrorInvalidValue;
   size_t smem = sizeof(float) * ((size_t)kq + c + 32 + 64 + 4 * 32 + 64 + m + zc + 8 + 2 * (size_t)zc * (zc + 1));
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
-  cudaFuncSetAttribute(k_orth_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  raise_smem_limit(k_orth_block);
   ProfScope prof("orth_block", st, 0, 0);
   note_launch("orth_block");
   k_orth_block<<<1, SMALL_THREADS, smem, st>>>(Z, ldz, m, zc, Q, ldq, kq, c, scratch, seed, status, only_if);
@@ -371,7 +371,7 @@ cudaError_t launch_rayleigh_ritz(const float* Q, const float* W, int64_t ld, int
   int use_global = (base + mats > 220 * 1024) ? 1 : 0;
   if (k > 256) return cudaErrorInvalidValue;   // cs scratch holds 128 pairs
   size_t smem = base + (use_global ? 0 : mats);
-  cudaFuncSetAttribute(k_rayleigh_ritz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  raise_smem_limit(k_rayleigh_ritz);
   ProfScope prof("rayleigh_ritz", st, 0, 0);
   note_launch("rayleigh_ritz");
   k_rayleigh_ritz<<<1, SMALL_THREADS, smem, st>>>(Q, W, ld, m, k, r, identity_q, scratch,

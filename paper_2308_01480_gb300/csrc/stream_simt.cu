@@ -425,7 +425,7 @@ static void ga_launch(const TIn* C, int64_t m, int64_t n, const float* X, int ld
                       int64_t tpc, int ctas, cudaStream_t st) {
   size_t smem = sizeof(float) * ((16 * MA) * 33 + (16 * MA) * (16 * VB + 1) + 32 * (16 * VB + 1));
   auto kern = k_ga_fused<TIn, MA, VB>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  raise_smem_limit(kern);
   kern<<<ctas, 256, smem, st>>>(C, m, n, X, ldx, b, P, tpc);
 }
 

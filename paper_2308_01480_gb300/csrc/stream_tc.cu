@@ -493,7 +493,7 @@ template <int OP>
 cudaError_t launch_tc(const CUtensorMap& mc, const CUtensorMap& mb, const TcParams& p, int ctas, cudaStream_t st) {
   const size_t smem = tc_smem_bytes(p);
   if (smem > (size_t)SMEM_LIMIT) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(k_tc_stream<OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = raise_smem_limit(k_tc_stream<OP>);
   if (e != cudaSuccess) return e;
   k_tc_stream<OP><<<ctas, TC_THREADS, smem, st>>>(mc, mb, p);
   return cudaGetLastError();
