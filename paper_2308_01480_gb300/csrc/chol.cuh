@@ -51,89 +51,93 @@ __device__ inline void chol_inv_cta(float* G, int ldg, int b, const float* diag0
 }
 
 
-// Same contract as chol_inv_cta for b <= 32, computed by warp 0 alone:
-// lane l holds column l of the upper triangle of G in registers while it is
-// factored (rows of R travel between lanes by shuffles), R goes to shared
-// memory, then lane l forms column l of T = R^{-1} by back substitution
-// with R read back as broadcasts.  Pivot square roots and reciprocals use
-// the hardware reciprocal square root (a few ulp), which the following
-// Cholesky QR passes absorb.  The CTA synchronises before (G complete) and
-// after (R, T written).
-__device__ __forceinline__ void chol_inv_warp32(const float* G, int ldg, int b, const float* diag0, float* R, int ldr,
-                                       float* T, int ldt, int* flag, bool report) {
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    const unsigned full = 0xffffffffu;
-    const int l = threadIdx.x;
-    float rinv = 1.f;                       // 1 / R[l][l]
-    {
-      float a[32];
+// Cholesky factorisation and triangular inverse of a b x b Gram, b <= 32,
+// by one warp (the calling warp, all 32 lanes): lane l holds column l of the
+// upper triangle of G in registers while it is factored (rows of R travel
+// between lanes by shuffles), R goes to shared memory, then lane l forms
+// column l of T = R^{-1} by back substitution with R read back as
+// broadcasts.  Pivot square roots and reciprocals use the hardware
+// reciprocal square root (a few ulp), which the following Cholesky QR
+// passes absorb.  A pivot below 1e-6 of diag0 (or non-positive) raises
+// *flag when report and is replaced by 1.  Callers use the out-of-line copy
+// below: inlined into a larger kernel the unrolled arrays tend to land in
+// local memory.
+__device__ __forceinline__ void chol_inv_warp(const float* G, int ldg, int b, const float* diag0, float* R,
+                                                   int ldr, float* T, int ldt, int* flag, bool report) {
+  const unsigned full = 0xffffffffu;
+  const int l = threadIdx.x & 31;
+  float rinv = 1.f;                       // 1 / R[l][l]
+  {
+    float a[32];
 #pragma unroll
-      for (int i = 0; i < 32; ++i) a[i] = (i <= l && l < b) ? G[i * ldg + l] : 0.f;
-      const float d0 = (l < b) ? diag0[l] : 1.f;
-      bool bad = false;
+    for (int i = 0; i < 32; ++i) a[i] = (i <= l && l < b) ? G[i * ldg + l] : 0.f;
+    const float d0 = (l < b) ? diag0[l] : 1.f;
+    bool bad = false;
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        if (j < b) {
-          float djj = __shfl_sync(full, a[j], j);
-          const float dref = __shfl_sync(full, d0, j);
-          if (!(djj > 1e-6f * dref)) {
-            bad = true;
-            djj = 1.f;
-          }
-          const float inv = rsqrtf(djj);
-          if (l == j) rinv = inv;
-          const float rjl = (l == j) ? djj * inv : ((l > j) ? a[j] * inv : 0.f);   // R[j][l]
-          a[j] = rjl;
+    for (int j = 0; j < 32; ++j) {
+      if (j < b) {
+        float djj = __shfl_sync(full, a[j], j);
+        const float dref = __shfl_sync(full, d0, j);
+        if (!(djj > 1e-6f * dref)) {
+          bad = true;
+          djj = 1.f;
+        }
+        const float inv = rsqrtf(djj);
+        if (l == j) rinv = inv;
+        const float rjl = (l == j) ? djj * inv : ((l > j) ? a[j] * inv : 0.f);   // R[j][l]
+        a[j] = rjl;
 #pragma unroll
-          for (int i = j + 1; i < 32; ++i) {
-            const float rji = __shfl_sync(full, rjl, i);                  // R[j][i]
-            a[i] = fmaf(-rji, rjl, a[i]);
-          }
+        for (int i = j + 1; i < 32; ++i) {
+          const float rji = __shfl_sync(full, rjl, i);                  // R[j][i]
+          a[i] = fmaf(-rji, rjl, a[i]);
         }
       }
-      if (report && bad && l == 0) atomicExch(flag, 1);
-      if (l < b) {
-#pragma unroll
-        for (int i = 0; i < 32; ++i)
-          if (i < b) R[i * ldr + l] = (i <= l) ? a[i] : 0.f;
-      }
     }
-    __syncwarp();
-    // column l of T = R^{-1}; the reciprocal pivots come from their lanes
-    float t[32];
-#pragma unroll
-    for (int i = 31; i >= 0; --i) {
-      const float ri = __shfl_sync(full, rinv, i);
-      if (i < b) {
-        float s0 = (i == l) ? 1.f : 0.f, s1 = 0.f;
-#pragma unroll
-        for (int k = i + 1; k < 32; ++k)
-          if (k < b) {
-            if ((k - i) & 1) s0 = fmaf(-R[i * ldr + k], t[k], s0);
-            else s1 = fmaf(-R[i * ldr + k], t[k], s1);
-          }
-        t[i] = (i <= l && l < b) ? (s0 + s1) * ri : 0.f;
-      } else {
-        t[i] = 0.f;
-      }
-    }
+    if (report && bad && l == 0) atomicExch(flag, 1);
     if (l < b) {
 #pragma unroll
       for (int i = 0; i < 32; ++i)
-        if (i < b) T[i * ldt + l] = t[i];
+        if (i < b) R[i * ldr + l] = (i <= l) ? a[i] : 0.f;
     }
   }
-  __syncthreads();
+  __syncwarp();
+  float t[32];
+#pragma unroll
+  for (int i = 31; i >= 0; --i) {
+    const float ri = __shfl_sync(full, rinv, i);
+    if (i < b) {
+      float s0 = (i == l) ? 1.f : 0.f, s1 = 0.f;
+#pragma unroll
+      for (int k = i + 1; k < 32; ++k)
+        if (k < b) {
+          if ((k - i) & 1) s0 = fmaf(-R[i * ldr + k], t[k], s0);
+          else s1 = fmaf(-R[i * ldr + k], t[k], s1);
+        }
+      t[i] = (i <= l && l < b) ? (s0 + s1) * ri : 0.f;
+    } else {
+      t[i] = 0.f;
+    }
+  }
+  if (l < b) {
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+      if (i < b) T[i * ldt + l] = t[i];
+  }
 }
 
-// Out-of-line copy: one instance of the unrolled factorisation per kernel
-// however many call sites it has (keeps register budgets and instruction
-// footprints small).
-static __device__ __noinline__ void chol_inv_warp32_call(const float* G, int ldg, int b, const float* diag0,
-                                                         float* R, int ldr, float* T, int ldt, int* flag,
-                                                         bool report) {
-  chol_inv_warp32(G, ldg, b, diag0, R, ldr, T, ldt, flag, report);
+// Out-of-line copy (one per kernel, its own register allocation).
+static __device__ __noinline__ void chol_inv_warp_ool(const float* G, int ldg, int b, const float* diag0, float* R,
+                                                       int ldr, float* T, int ldt, int* flag, bool report) {
+  chol_inv_warp(G, ldg, b, diag0, R, ldr, T, ldt, flag, report);
+}
+
+// chol_inv_cta's contract for b <= 32: the CTA synchronises, warp 0 alone
+// factors (the other warps do not enter the call), the CTA synchronises.
+__device__ __forceinline__ void chol_inv_warp32_call(const float* G, int ldg, int b, const float* diag0, float* R,
+                                                     int ldr, float* T, int ldt, int* flag, bool report) {
+  __syncthreads();
+  if (threadIdx.x < 32) chol_inv_warp_ool(G, ldg, b, diag0, R, ldr, T, ldt, flag, report);
+  __syncthreads();
 }
 
 // Pivoted variant for a block that keeps only c <= b columns (the Krylov

@@ -11,7 +11,7 @@
 //   A: Z = W;                 P1 = Q^T Z
 //   B: Z -= Q P1;             P2 = Q^T Z                 (block Gram-Schmidt twice)
 //   C: Z -= Q P2;             R1 = chol(Z^T Z + s I)     (shifted CholeskyQR)
-//   D: Z = Z R1^-1;           P3 = Q^T Z, R2 = chol(Z^T Z - P3^T P3)
+//   D: Z = Z R1^-1;           P3 = Q^T Z, R2 = chol(Z^T Z)
 //   E: Z = (Z - Q P3) R2^-1;  R3 = chol(Z^T Z)
 //   F: X = Z R3^-1 -> Q[:, kq:kq+b]
 // (C, D, E, F without Q terms for the first block).  The Krylov power
@@ -113,7 +113,7 @@ __device__ void nn_tile(const float* X, int ldx, int kk, const float* M, int ldm
   }
 }
 
-__global__ void __launch_bounds__(OC_THREADS) k_orth_cluster(ClusterOrthArgs a) {
+__global__ void __launch_bounds__(OC_THREADS, 1) k_orth_cluster(ClusterOrthArgs a) {
   extern __shared__ __align__(16) float sm[];
   cg::cluster_group cl = cg::this_cluster();
   const int kq = a.kq, b = a.b, tid = threadIdx.x;
@@ -204,17 +204,6 @@ __global__ void __launch_bounds__(OC_THREADS) k_orth_cluster(ClusterOrthArgs a) 
       a.Q[(r0 + i) * a.ldq + kq + j] = Zc[i * bp + j];
     }
   };
-  // G <- G - P^T P over the first cols columns (Pythagorean update after a
-  // projection that has not been applied yet)
-  auto sub_ptp = [&](int cols) {
-    if (kq == 0) return;
-    for (int e = tid; e < cols * cols; e += blockDim.x) {
-      const int i = e / cols, j = e % cols;
-      float s = 0.f;
-      for (int t = 0; t < kq; ++t) s = fmaf(P[t * bp + i], P[t * bp + j], s);
-      G[i * (b + 1) + j] -= s;
-    }
-  };
 
   if (kq > 0) {
     reduce(true, false);                       // A
@@ -222,12 +211,13 @@ __global__ void __launch_bounds__(OC_THREADS) k_orth_cluster(ClusterOrthArgs a) 
     reduce(true, false);                       // B
     sub_q();
   }
-  reduce(false, true);                         // C
-  set_diag0();
-  {
-    // shifted Cholesky QR, then two Cholesky QR passes (the first with the
-    // re-projection)
-    {
+  // C, D, E: three Cholesky QR passes
+  for (int pass = 0; pass < 3; ++pass) {
+    reduce(pass == 1 && kq > 0, true);
+    set_diag0();
+    if (pass == 0) {
+      // shifted Cholesky QR first: Krylov power blocks lean towards the
+      // dominant directions, so their Gram is far from the identity
       float tr = 0.f;
       for (int i = tid; i < b; i += blockDim.x) tr += G[i * (b + 1) + i];
       tr = block_sum(tr, red);
@@ -235,23 +225,17 @@ __global__ void __launch_bounds__(OC_THREADS) k_orth_cluster(ClusterOrthArgs a) 
       __syncthreads();
       for (int i = tid; i < b; i += blockDim.x) G[i * (b + 1) + i] += shift;
     }
-    if (c < b)
+    // pass 1: Z^T Z stands in for the Gram of Z - Q P3 (after the block
+    // Gram-Schmidt passes P3 = Q^T Z is at rounding level relative to Z, so
+    // P3^T P3 is second order, and pass 2 restores orthonormality anyway)
+    if (pass == 0 && c < b)
       pchol_select_cta(G, b + 1, b, c, diag0, R, b, T, bp, bp, perm, dsw, a.flag, report);
     else
-      factor(b, a.flag, report);
+      factor(pass == 0 ? b : c, a.flag, report);
+    if (pass == 1 && kq > 0) sub_q();
     mul_t();
-    reduce(kq > 0, true);                      // D
-    set_diag0();
-    sub_ptp(c);
-    factor(c, a.flag, report);
-    if (kq > 0) sub_q();
-    mul_t();
-    reduce(false, true);                       // E
-    set_diag0();
-    factor(c, a.flag, report);
-    mul_t();                                   // F
-    write_q(c);
   }
+  write_q(c);
   cl.sync();   // no CTA leaves while others may still read its shares
 }
 
