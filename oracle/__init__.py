@@ -9,7 +9,8 @@ it.  It shares no code, tables, constants or helpers with the CUDA library in
 Modules
 -------
 tt_oracle   TT-SVD (Alg. 1), TT-rBKI (Alg. 3, left block Krylov reading with
-            Rayleigh-Ritz truncation), Krylov-basis helper, tail energies
+            Rayleigh-Ritz truncation; q = 0 is TT-rSVD, Alg. 2), TT-rSI
+            (Alg. 4, subspace iteration), Krylov-basis helper, tail energies
             (Def. 3), TT contraction and the relative error of Sec. 4.
 philox      Philox4x32-10 counter-based generator (Salmon et al., SC'11) and the
             Box-Muller transform that expand an Omega seed into the Gaussian
@@ -27,6 +28,9 @@ from .tt_oracle import (  # noqa: F401
     krylov_basis,
     rbki_mode,
     tt_rbki,
+    subspace_basis,
+    rsi_mode,
+    tt_rsi,
     tt_svd,
     tt_full,
     tt_error,

@@ -1,4 +1,5 @@
-"""Plain float64 restatement of TT-SVD (Alg. 1) and TT-rBKI (Alg. 3).
+"""Plain float64 restatement of TT-SVD (Alg. 1), TT-rBKI (Alg. 3) and
+TT-rSI (Alg. 4); TT-rSVD (Alg. 2) is TT-rBKI with q = 0.
 
 TEST INFRASTRUCTURE ONLY: used by tests/, __graft_entry__.smoke() and the
 CPU-baseline leg of bench.py.  Never imported by the CUDA library.
@@ -114,17 +115,9 @@ def rbki_mode(C, r, Omega, q):
     return U, R, sigma
 
 
-def tt_rbki(A, ranks, oversample, q, omegas=None, seed=None):
-    """TT-rBKI (Alg. 3) in float64.
-
-    A        : ndarray of order d >= 2 (converted to float64).
-    ranks    : target TT ranks r_1..r_{d-1}; clamped as in clamp_ranks.
-    oversample, q : the paper's p and q.
-    omegas   : optional list of d-1 Gaussian matrices, omegas[k] of shape
-               (I_{k+1}...I_d, r_k' + p); otherwise drawn from ``seed`` with
-               omega_from_seed(seed, k, n, b).
-    Returns the list of d cores, core k of shape (r_{k-1}', I_k, r_k').
-    """
+def _tt_randomized(A, ranks, oversample, q, omegas, seed, mode_fn):
+    """The mode loop shared by Alg. 3 and Alg. 4: unfold, draw Omega, run
+    mode_fn(C, r, Omega, q) -> (U, R, sigma), store U as the core, carry R."""
     A = np.asarray(A, dtype=np.float64)
     dims = A.shape
     d = len(dims)
@@ -144,10 +137,63 @@ def tt_rbki(A, ranks, oversample, q, omegas=None, seed=None):
             Omega = omega_from_seed(seed, k, n, b)
         if Omega.shape != (n, b):
             raise ValueError(f"omega {k} has shape {Omega.shape}, want {(n, b)}")
-        U, R, _ = rbki_mode(C, rr[k + 1], Omega, q)
+        U, R, _ = mode_fn(C, rr[k + 1], Omega, q)
         cores.append(U.reshape(rr[k], dims[k], rr[k + 1]))
     cores.append(np.reshape(R, (rr[d - 1], dims[d - 1], 1)))
     return cores
+
+
+def tt_rbki(A, ranks, oversample, q, omegas=None, seed=None):
+    """TT-rBKI (Alg. 3) in float64.
+
+    A        : ndarray of order d >= 2 (converted to float64).
+    ranks    : target TT ranks r_1..r_{d-1}; clamped as in clamp_ranks.
+    oversample, q : the paper's p and q.
+    omegas   : optional list of d-1 Gaussian matrices, omegas[k] of shape
+               (I_{k+1}...I_d, r_k' + p); otherwise drawn from ``seed`` with
+               omega_from_seed(seed, k, n, b).
+    Returns the list of d cores, core k of shape (r_{k-1}', I_k, r_k').
+    With q = 0 this is TT-rSVD (Alg. 2) under the Rayleigh-Ritz reading.
+    """
+    return _tt_randomized(A, ranks, oversample, q, omegas, seed, rbki_mode)
+
+
+def subspace_basis(C, Omega, q):
+    """Orthonormal basis of the subspace iteration of Alg. 4 (steps 4-11):
+    Y = C W, Q_0 = qr(Y); then q times Yhat = C^T Q, Qhat = qr(Yhat),
+    Y = C Qhat, Q = qr(Y).  Its span is that of (C C^T)^q C W.  Under the
+    Krylov dimension cap the left factors keep min(b, D) columns (the top
+    singular directions), D = min(m, n); once Q spans D columns further
+    steps cannot change its span and are skipped.
+    """
+    m, n = C.shape
+    b = Omega.shape[1]
+    D = min(m, n)
+    c = min(b, D)
+    Q = orth_top(C @ Omega, c)              # steps 4-5
+    for _ in range(q):
+        if c >= D:
+            break
+        Qh, _ = np.linalg.qr(C.T @ Q)       # steps 7-8
+        Q = orth_top(C @ Qh, c)             # steps 9-10
+    return Q
+
+
+def rsi_mode(C, r, Omega, q):
+    """One mode of TT-rSI (Alg. 4) on the unfolding C: the subspace basis,
+    then the top-r left singular vectors of Q^T C (Rayleigh-Ritz, the same
+    reading of step 12 as for Alg. 3).  Returns (U, R = U^T C, sigma)."""
+    Q = subspace_basis(C, Omega, q)
+    B = Q.T @ C
+    Ub, sigma, _ = np.linalg.svd(B, full_matrices=False)
+    U = Q @ Ub[:, :r]
+    R = U.T @ C
+    return U, R, sigma
+
+
+def tt_rsi(A, ranks, oversample, q, omegas=None, seed=None):
+    """TT-rSI (Alg. 4) in float64; arguments and result as tt_rbki."""
+    return _tt_randomized(A, ranks, oversample, q, omegas, seed, rsi_mode)
 
 
 def tt_svd(A, ranks=None, eps=None):
