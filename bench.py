@@ -264,10 +264,28 @@ def run_ours(args):
     fp32_steps = max(1, min(args.steps, 10))
     ms32 = time_steps(graph_32.launch, fp32_steps, 2, barrier_sync)
 
-    # ---- accuracy of both forms against the float64 tensor
+    # ---- the paper's comparison methods on the same BF16 tensor (Alg. 4
+    # TT-rSI with the same q, and TT-rSVD = q = 0), graph-launched like the
+    # headline
+    methods = {}
+    cores_m = {}
+    for name, method, qm in (("tt_rsi", tt.TT_METHOD_RSI, q), ("tt_rsvd", tt.TT_METHOD_RBKI, 0)):
+        pm = tt.Problem(Abf, ranks, p, qm, seed)
+        gm = tt.BatchGraph([pm], tt.options(storage=tt.TT_BF16, remainder=tt.TT_BF16, method=method))
+        msm = time_steps(gm.launch, fp32_steps, 2, barrier_sync)
+        if gm.device_status() != [0]:
+            raise RuntimeError(f"device status not OK after {name}")
+        gm.close()
+        methods[name] = {"ms_per_step": msm / fp32_steps, "q": qm}
+        cores_m[name] = pm.cores
+
+    # ---- accuracy against the float64 tensor
     A64 = torch.from_numpy(A).to(dev)
     eps_bf = rel_error_dev(A64, cores_bf)
     eps_32 = rel_error_dev(A64, cores_32)
+    for name in methods:
+        methods[name]["tt_error"] = rel_error_dev(A64, cores_m[name])
+    methods["tt_rbki"] = {"ms_per_step": ms_max / args.steps, "q": q, "tt_error": eps_bf}
     del A64
 
     # ---- end to end through the public API with host buffers: the input
@@ -316,6 +334,7 @@ def run_ours(args):
         "data": "synthetic (seeded; paper's datasets unavailable)",
         "config": workload_config(w, world),
         "tt_error": {"bf16": eps_bf, "fp32": eps_32},
+        "methods_bf16": methods,
         "fp32_form": {"ms_per_step": ms32 / fp32_steps, "decompositions_per_s": fp32_steps / (ms32 * 1e-3),
                       "tt_error": eps_32, "speedup_bf16_over_fp32": (ms32 / fp32_steps) / (ms_max / args.steps)},
         "e2e": {"value": e2e_steps / (ms_e2e * 1e-3), "unit": "decompositions/s",

@@ -90,8 +90,16 @@ typedef struct {
   int32_t batch_streams;/* batched entry points: number of concurrent worker
                            streams the problems are spread over (1..64);
                            0 (default) = 16.  Ignored by single problems.    */
-  int32_t reserved[4];  /* must be zero                                       */
+  int32_t method;       /* TT_METHOD_RBKI (default): Alg. 3, block Krylov
+                           basis [C W, ..., (C C^T)^q C W].  TT_METHOD_RSI:
+                           Alg. 4, subspace iteration, basis of
+                           (C C^T)^q C W only (b columns), re-orthonormalised
+                           after every power.  Either with q = 0 is TT-rSVD
+                           (Alg. 2).  Both truncate by Rayleigh-Ritz.         */
+  int32_t reserved[3];  /* must be zero                                       */
 } tt_options;
+
+enum { TT_METHOD_RBKI = 0, TT_METHOD_RSI = 1 };
 
 /* Fills *opts with the defaults described above. */
 TT_API tt_status tt_rbki_default_options(tt_options* opts);

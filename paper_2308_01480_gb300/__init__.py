@@ -8,8 +8,8 @@ library's CUDA kernels.  There is no CPU path.
 import ctypes
 
 from . import _native as N
-from ._native import (TT_BF16, TT_F32, TT_PASS_GRAM, TT_PASS_GRAMAPPLY,  # noqa: F401
-                      TT_PASS_PROJECT, TT_PASS_SKETCH, TTError)
+from ._native import (TT_BF16, TT_F32, TT_METHOD_RBKI, TT_METHOD_RSI, TT_PASS_GRAM,  # noqa: F401
+                      TT_PASS_GRAMAPPLY, TT_PASS_PROJECT, TT_PASS_SKETCH, TTError)
 
 __all__ = ["decompose", "workspace_size", "core_sizes", "omega_generate", "permute_convert",
            "tt_pass", "device_status", "options", "profile_begin", "profile_end", "TTError", "TT_F32",
@@ -37,14 +37,17 @@ def _stream_handle(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def options(storage=N.TT_F32, remainder=None, exhaust_gram=True, batch_streams=0):
-    """tt_options with the given fields (remainder None = same as storage)."""
+def options(storage=N.TT_F32, remainder=None, exhaust_gram=True, batch_streams=0, method=N.TT_METHOD_RBKI):
+    """tt_options with the given fields (remainder None = same as storage;
+    method TT_METHOD_RBKI (Alg. 3) or TT_METHOD_RSI (Alg. 4); q = 0 with
+    either is TT-rSVD, Alg. 2)."""
     o = N.TTOptions()
     N.check(N.lib().tt_rbki_default_options(ctypes.byref(o)))
     o.storage = int(storage)
     o.remainder = -1 if remainder is None else int(remainder)
     o.exhaust_gram = 1 if exhaust_gram else 0
     o.batch_streams = int(batch_streams)
+    o.method = int(method)
     return o
 
 

@@ -13,6 +13,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libtt_rbki.so")
 TT_OK, TT_EINVAL, TT_ENOMEM, TT_ECUDA, TT_EBREAKDOWN, TT_ENONFINITE, TT_EUNSUPPORTED, TT_ETIMEOUT = range(8)
 TT_F32, TT_BF16 = 0, 1
 TT_PASS_SKETCH, TT_PASS_GRAMAPPLY, TT_PASS_PROJECT, TT_PASS_GRAM = range(4)
+TT_METHOD_RBKI, TT_METHOD_RSI = range(2)
 
 STATUS_NAMES = {0: "TT_OK", 1: "TT_EINVAL", 2: "TT_ENOMEM", 3: "TT_ECUDA", 4: "TT_EBREAKDOWN",
                 5: "TT_ENONFINITE", 6: "TT_EUNSUPPORTED", 7: "TT_ETIMEOUT"}
@@ -21,7 +22,7 @@ STATUS_NAMES = {0: "TT_OK", 1: "TT_EINVAL", 2: "TT_ENOMEM", 3: "TT_ECUDA", 4: "T
 class TTOptions(ctypes.Structure):
     _fields_ = [("storage", ctypes.c_int32), ("remainder", ctypes.c_int32),
                 ("exhaust_gram", ctypes.c_int32), ("batch_streams", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("method", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class TTProblem(ctypes.Structure):

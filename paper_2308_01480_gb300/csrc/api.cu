@@ -36,6 +36,7 @@ struct ModePlan {
   int64_t m = 0, n = 0, D = 0;
   int r_in = 1, r_out = 1, b = 0, kq = 0;
   std::vector<int> blocks;   // columns of X_0, X_1, ... (Krylov dimension cap applied)
+  int iters = 0;             // subspace iteration: powers applied to the single block
   bool gram_route = false;   // exhaustion with D == m: one Gram pass
   bool fused_ga = false;     // Gram-apply fused in one pass over C
 };
@@ -57,7 +58,9 @@ tt_status resolve_options(const tt_options* in, tt_options* out) {
   if (out->storage != TT_F32 && out->storage != TT_BF16) return fail(TT_EINVAL, "options.storage must be TT_F32 or TT_BF16");
   if (out->remainder < 0) out->remainder = out->storage;
   if (out->remainder != TT_F32 && out->remainder != TT_BF16) return fail(TT_EINVAL, "options.remainder must be TT_F32 or TT_BF16");
-  for (int i = 0; i < 4; ++i)
+  if (out->method != TT_METHOD_RBKI && out->method != TT_METHOD_RSI)
+    return fail(TT_EINVAL, "options.method must be TT_METHOD_RBKI or TT_METHOD_RSI");
+  for (int i = 0; i < 3; ++i)
     if (out->reserved[i] != 0) return fail(TT_EINVAL, "options.reserved must be zero");
   return TT_OK;
 }
@@ -117,11 +120,16 @@ tt_status build_plan(const int64_t* dims, int d, const int64_t* ranks, int p, in
     M.b = (int)b64;
     int64_t cols = ttr::imin(M.b, M.D);
     M.blocks.assign(1, (int)cols);
-    for (int j = 1; j <= q; ++j) {
-      if (cols >= M.D) break;
-      const int64_t c = ttr::imin(M.b, M.D - cols);
-      M.blocks.push_back((int)c);
-      cols += c;
+    if (P.o.method == TT_METHOD_RSI) {
+      // Alg. 4: one block, q powers (none once it spans all D directions)
+      M.iters = (cols >= M.D) ? 0 : q;
+    } else {
+      for (int j = 1; j <= q; ++j) {
+        if (cols >= M.D) break;
+        const int64_t c = ttr::imin(M.b, M.D - cols);
+        M.blocks.push_back((int)c);
+        cols += c;
+      }
     }
     M.kq = (int)cols;
     M.gram_route = P.o.exhaust_gram && cols == M.D && M.D == M.m && M.m <= 128;
@@ -240,14 +248,8 @@ tt_status run_mode(const Plan& P, int k, const TIn* C, char* ws, int* status, co
       }
       return TT_OK;
     };
-    tt_status os = orth(Y, M.b, M.b, 0, M.blocks[0], rseed);
-    if (os != TT_OK) return os;
-    int col = 0;
-    for (size_t j = 0; j < M.blocks.size(); ++j) {
-      const int cj = M.blocks[j];
-      const float* Xj = Q + col;
-      float* Wj = W + col;
-      // one Krylov power: W_j = C C^T X_j (also the Rayleigh-Ritz data)
+    // one power: Wj = C C^T Xj (cj columns; row stride kq for both)
+    auto power = [&](const float* Xj, float* Wj, int cj) -> tt_status {
       if (use_tc) {
         if (ttr::tc_ga_ok(M.m, M.n, cj)) {
           TTR_CUDA(ttr::tc_ga(Cb, M.m, M.n, Xj, kq, cj, part, Wj, kq, xs, status, st));
@@ -262,11 +264,35 @@ tt_status run_mode(const Plan& P, int k, const TIn* C, char* ws, int* status, co
         TTR_CUDA((ttr::simt_proj<TIn, float>(C, M.m, M.n, Xj, kq, cj, T, M.n, st, part)));
         TTR_CUDA(ttr::simt_cs<TIn>(C, M.m, M.n, T, M.n, cj, part, Wj, kq, st));
       }
-      if (j + 1 < M.blocks.size()) {
-        os = orth(Wj, kq, cj, col + cj, M.blocks[j + 1], rseed + 7919ull * (j + 1));
+      return TT_OK;
+    };
+    tt_status os = orth(Y, M.b, M.b, 0, M.blocks[0], rseed);
+    if (os != TT_OK) return os;
+    if (P.o.method == TT_METHOD_RSI) {
+      // Alg. 4 steps 6-11: Q <- orth(C C^T Q), q times; then one more power
+      // gives the Rayleigh-Ritz data W = C C^T Q
+      const int c0 = M.blocks[0];
+      for (int it = 0; it <= M.iters; ++it) {
+        os = power(Q, W, c0);
         if (os != TT_OK) return os;
+        if (it < M.iters) {
+          os = orth(W, kq, c0, 0, c0, rseed + 7919ull * (it + 1));
+          if (os != TT_OK) return os;
+        }
       }
-      col += cj;
+    } else {
+      int col = 0;
+      for (size_t j = 0; j < M.blocks.size(); ++j) {
+        const int cj = M.blocks[j];
+        // one Krylov power: W_j = C C^T X_j (also the Rayleigh-Ritz data)
+        os = power(Q + col, W + col, cj);
+        if (os != TT_OK) return os;
+        if (j + 1 < M.blocks.size()) {
+          os = orth(W + col, kq, cj, col + cj, M.blocks[j + 1], rseed + 7919ull * (j + 1));
+          if (os != TT_OK) return os;
+        }
+        col += cj;
+      }
     }
     if (ttr::eig_top_ok(kq))
       TTR_CUDA(ttr::launch_rr_fast(Q, W, kq, M.m, kq, r, 0, small, U, core, st));

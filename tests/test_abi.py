@@ -176,3 +176,19 @@ def test_batched_invalid_arguments(L):
     assert L.tt_rbki_graph_destroy(None) == N.TT_OK
     assert L.tt_rbki_batched_graph_create(3, arr, ctypes.c_void_p(256), 1 << 30, None, per,
                                           ctypes.byref(h)) == N.TT_EINVAL
+
+
+def test_method_option_validated(L):
+    o = N.TTOptions()
+    L.tt_rbki_default_options(ctypes.byref(o))
+    assert o.method == N.TT_METHOD_RBKI
+    nb = ctypes.c_size_t()
+    dims, ranks = N.i64_array([16] * 4), N.i64_array([4] * 3)
+    o.method = N.TT_METHOD_RSI
+    assert L.tt_rbki_workspace_size(dims, 4, ranks, 5, 2, ctypes.byref(o), ctypes.byref(nb)) == N.TT_OK
+    rsi = nb.value
+    o.method = N.TT_METHOD_RBKI
+    assert L.tt_rbki_workspace_size(dims, 4, ranks, 5, 2, ctypes.byref(o), ctypes.byref(nb)) == N.TT_OK
+    assert rsi > 0 and nb.value > 0
+    o.method = 2
+    assert L.tt_rbki_workspace_size(dims, 4, ranks, 5, 2, ctypes.byref(o), ctypes.byref(nb)) == N.TT_EINVAL

@@ -44,7 +44,7 @@ CASES = [
 ]
 
 
-def _run(tt, t, dims, r, p, q, seed, opts, poison):
+def _run(tt, t, dims, r, p, q, seed, opts, poison):  # noqa: D401
     need = tt.workspace_size(dims, r, p, q, opts)
     ws = torch.full((need,), 255 if poison else 0, dtype=torch.uint8, device="cuda")
     rr, _ = tt.core_sizes(dims, r)
@@ -60,12 +60,12 @@ def _run(tt, t, dims, r, p, q, seed, opts, poison):
 
 @pytest.mark.parametrize("case", CASES)
 @pytest.mark.parametrize("storage", ["f32", "bf16"])
-@pytest.mark.parametrize("exhaust", [True, False])
-def test_decompose_ignores_prior_memory_contents(tt, case, storage, exhaust):
+@pytest.mark.parametrize("exhaust,method", [(True, 0), (False, 0), (True, 1)])
+def test_decompose_ignores_prior_memory_contents(tt, case, storage, exhaust, method):
     dims, r, p, q = case
     code = tt.TT_BF16 if storage == "bf16" else tt.TT_F32
     dt = torch.bfloat16 if storage == "bf16" else torch.float32
-    opts = tt.options(storage=code, exhaust_gram=exhaust)
+    opts = tt.options(storage=code, exhaust_gram=exhaust, method=method)
     t = torch.from_numpy(_noisy_tt(dims, r, 31, 0.05).astype(np.float32)).cuda().to(dt)
     clean = _run(tt, t, dims, r, p, q, 5, opts, False)
     dirty = _run(tt, t, dims, r, p, q, 5, opts, True)
