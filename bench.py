@@ -25,6 +25,9 @@ import time
 import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
+# more hardware work queues for the batched form's concurrent worker streams
+# (a per-process setting read when the CUDA context is created)
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 sys.path.insert(0, ROOT)
 
 from paper_2308_01480_gb300 import workloads as W  # noqa: E402
@@ -377,7 +380,7 @@ def batched_measure(tt, torch, dev, sync_all, launches=5):
         probs.append(tt.Problem(tt.permute_convert(t, dst_dtype=torch.bfloat16), wl.ranks, wl.oversample, wl.q,
                                 wl.omega_seed))
         del t
-    g = tt.BatchGraph(probs, tt.options(storage=tt.TT_BF16, remainder=tt.TT_BF16))
+    g = tt.BatchGraph(probs, tt.options(storage=tt.TT_BF16, remainder=tt.TT_BF16, batch_streams=32))
     ms = time_steps(g.launch, launches, 2, sync_all)
     ok = g.device_status() == [0] * len(probs)
     g.close()
@@ -386,7 +389,8 @@ def batched_measure(tt, torch, dev, sync_all, launches=5):
             "input_bytes": nbytes, "ms_per_batch": ms / launches,
             "problems_per_s": len(probs) * launches / (ms * 1e-3),
             "input_GBps": nbytes * launches / (ms * 1e-3) / 1e9, "statuses_ok": ok,
-            "launch": "one CUDA graph per batch, 16 worker streams"}
+            "launch": "one CUDA graph per batch, 32 worker streams, CUDA_DEVICE_MAX_CONNECTIONS=" +
+                      os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS", "default")}
 
 
 def oracle_step(A, w):
