@@ -37,12 +37,7 @@ CONFIG_ID = 3
 # ncu DRAM traffic (read + write bytes per launch) of the dominant kernel, by
 # kernel family, with the profile summary it comes from; None when the
 # kernel changed after the capture.
-NCU_TRAFFIC = {
-    # 13 launches of one decomposition: 900.5 MB of dram__bytes_read.sum +
-    # dram__bytes_write.sum (ncu, -k regex:k_tc_stream -c 26 on this bench
-    # with --steps 1 --warmup 0)
-    "proj_tc": 69.27e6,
-}
+NCU_TRAFFIC = {}
 
 
 def parse():

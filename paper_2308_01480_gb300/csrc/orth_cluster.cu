@@ -13,7 +13,8 @@
 //   C: Z -= Q P2;             R1 = chol(Z^T Z + s I)     (shifted CholeskyQR)
 //   D: Z = Z R1^-1;           P3 = Q^T Z, R2 = chol(Z^T Z)
 //   E: Z = (Z - Q P3) R2^-1;  R3 = chol(Z^T Z)
-//   F: X = Z R3^-1 -> Q[:, kq:kq+b]
+//   F: X = Z R3^-1 -> Q[:, kq:kq+b]  (X = Z (1.5 I - 0.5 Z^T Z) when Z^T Z
+//      is within 1e-4 of the identity in every entry)
 // (C, D, E, F without Q terms for the first block).  The Krylov power
 // blocks are typically far from orthogonal (their columns lean towards the
 // dominant directions), so the shift is always applied.  A pivot below 1e-6 of
@@ -51,6 +52,12 @@ struct ClusterOrthArgs {
 };
 
 __host__ __device__ inline int pad4(int x) { return (x + 3) & ~3; }
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
 
 // Shared-memory layout (floats), kp = pad4(kq), bp = pad4(b), rp = pad4(rows):
 //   share[2][(kp + bp) * bp] | P[kp * bp] | G[b * (b + 1)] | T[bp * bp] | R[b * b] (sizes padded to 4)
@@ -228,9 +235,33 @@ __global__ void __launch_bounds__(OC_THREADS, 1) k_orth_cluster(ClusterOrthArgs 
     // pass 1: Z^T Z stands in for the Gram of Z - Q P3 (after the block
     // Gram-Schmidt passes P3 = Q^T Z is at rounding level relative to Z, so
     // P3^T P3 is second order, and pass 2 restores orthonormality anyway)
+    bool polar = false;
+    if (pass == 2) {
+      // the last pass usually finds the Gram within rounding of the
+      // identity: then Z (1.5 I - 0.5 G) (first-order polar correction,
+      // orthogonality error O(|G - I|^2), same span) replaces the Cholesky
+      float e = 0.f;
+      for (int x = tid; x < c * c; x += blockDim.x) {
+        const int i = x / c, j = x % c;
+        e = fmaxf(e, fabsf(G[i * (b + 1) + j] - (i == j ? 1.f : 0.f)));
+      }
+      e = warp_max(e);
+      __syncthreads();
+      if ((tid & 31) == 0) red[tid >> 5] = e;
+      __syncthreads();
+      e = warp_max((tid & 31) < (int)(blockDim.x >> 5) ? red[tid & 31] : 0.f);
+      polar = e < 1e-4f;                     // the same in every thread
+      if (polar) {
+        for (int x = tid; x < bp * bp; x += blockDim.x) {
+          const int i = x / bp, j = x % bp;
+          T[x] = (i < c && j < c) ? (i == j ? 1.5f : 0.f) - 0.5f * G[i * (b + 1) + j] : 0.f;
+        }
+        __syncthreads();
+      }
+    }
     if (pass == 0 && c < b)
       pchol_select_cta(G, b + 1, b, c, diag0, R, b, T, bp, bp, perm, dsw, a.flag, report);
-    else
+    else if (!polar)
       factor(pass == 0 ? b : c, a.flag, report);
     if (pass == 1 && kq > 0) sub_q();
     mul_t();

@@ -635,7 +635,9 @@ TcShape proj_shape(int64_t m, int64_t n, int b, int split) {
   p.lo_off = split ? 32 : 0;
   p.npad = split ? 64 : pad16(b);
   p.kb = 2; p.mb = 1; p.row_groups = 1;
-  p.chunk_rows = box_rows_for(m, 128);
+  // unfoldings taller than one chunk stream 64-row chunks: the smaller ring
+  // stages let two CTAs share an SM
+  p.chunk_rows = box_rows_for(m, m > 128 ? 64 : 128);
   p.nchunks = (int)ceil_div(m, p.chunk_rows);
   p.x_resident = p.nchunks == 1 ? 1 : 0;
   p.mpad = (int)ceil_div(p.chunk_rows, 64) * 64;
