@@ -4,22 +4,22 @@
 // (l + 32 a, w + 32 c), a, c < KT = ceil(k / 32).  The second (16 warps, so
 // that the register-resident Cholesky of step 4 fits) does steps 2-5.
 //
-//  1. Householder tridiagonalisation.  Per column two barriers: the owners
-//     of column j publish it; every warp forms the same reflector v; each
-//     warp reduces its rows of p = tau H v across its lanes; then every
+//  1. Householder tridiagonalisation.  Per column two barriers: the warp
+//     owning column j forms the reflector v from its registers; each warp
+//     forms p = tau H v for its own columns by a lane reduction; then every
 //     thread applies H -= v w^T + w v^T to its entries, w = p - (tau/2)
-//     (v^T p) v.  The reflectors are kept in shared memory.
-//  2. Bisection by Sturm counts: one round with a count at each of 1024
-//     points over the Gershgorin interval, then a warp per wanted
-//     eigenvalue refines its bracket by 33-point multisection.
+//     (v^T p) v.  The reflectors go to global scratch.
+//  2. Bisection by Sturm counts: one round with a count at each of 512
+//     points over the Gershgorin interval, then each warp refines the
+//     brackets of two wanted eigenvalues at once by 33-point multisection.
 //  3. Inverse iteration on the tridiagonal T (pivoted LU), one thread per
 //     wanted eigenvalue, two rounds of one solve each, and
 //  4. after each round an orthonormalisation of the r vectors by Cholesky
 //     QR twice (columns in descending eigenvalue order, so the result is
 //     the Gram-Schmidt basis), or Gram-Schmidt twice when a Cholesky pivot
 //     is too small.
-//  5. Back-transformation by the stored reflectors, a warp per vector with
-//     the vector in registers.
+//  5. Back-transformation by the stored reflectors, a warp per two vectors
+//     held in registers.
 #include <float.h>
 
 #include <utility>
@@ -79,6 +79,27 @@ __device__ __forceinline__ int sturm(const float* d, const float* e2, int k, flo
     c += q < 0.f;
   }
   return c;
+}
+
+// Two Sturm counts (at x0 and x1) in one pass, so that the two dependent
+// chains overlap.
+__device__ __forceinline__ void sturm2(const float* d, const float* e2, int k, float x0, float x1, float pivmin,
+                                       int& c0, int& c1) {
+  float q0 = d[0] - x0, q1 = d[0] - x1;
+  if (fabsf(q0) < pivmin) q0 = -pivmin;
+  if (fabsf(q1) < pivmin) q1 = -pivmin;
+  c0 = q0 < 0.f;
+  c1 = q1 < 0.f;
+#pragma unroll 4
+  for (int i = 1; i < k; ++i) {
+    const float di = d[i], ei = e2[i - 1];
+    q0 = (di - x0) - __fdividef(ei, q0);
+    q1 = (di - x1) - __fdividef(ei, q1);
+    if (fabsf(q0) < pivmin) q0 = -pivmin;
+    if (fabsf(q1) < pivmin) q1 = -pivmin;
+    c0 += q0 < 0.f;
+    c1 += q1 < 0.f;
+  }
 }
 
 // Pivoted LU of T - lam I into w[0..5k) (reciprocal pivots, two upper
@@ -146,20 +167,24 @@ __host__ __device__ inline size_t er_smem_floats(int KM, int k, int r) {
 // Step 1 in one CTA of 32 warps: T = (d, e) and the reflectors (row j of
 // Vg = v_j, tau[j]) to global scratch.  Thread (warp w, lane l) holds the
 // entries (l + 32 a, w + 32 c), a, c < KT, so that column j lives in warp
-// j mod 32 alone.  Per column, four barriers separate: that warp publishes
-// the column; warp 0 forms the reflector v (and tau); every thread forms
-// the partial products of its rows with v over its columns, plus its share
-// of v^T H v; the sums give p = tau H v; every thread applies the rank-2
-// update H -= v w^T + w v^T, w = p - (tau/2)(v^T p) v, to its entries.
+// j mod 32 alone, and so does the dot product of any column with a vector
+// spread over the rows.  Per column two barriers:
+//   R  the warp owning column j forms the reflector v (and tau) from its
+//      registers and publishes it;
+//   M  every warp forms (H v)_c for its columns c by a lane reduction
+//      (H is symmetric, so the column dot is the row product), scaled by
+//      tau, and its share of v^T H v;
+//   U  every thread applies H -= v w^T + w v^T, w = p - (tau/2)(v^T p) v,
+//      to its entries of the trailing block; the owner of column j + 1
+//      then goes straight on to its reflector.
+// Tiles lying wholly in finished rows or columns are skipped.
 template <int KT>
 __global__ void __launch_bounds__(1024, 1) k_eig_tridiag(const float* __restrict__ Hin, int64_t ldh, int k,
                                                         float* __restrict__ Vg, float* __restrict__ tau_g,
                                                         float* __restrict__ d_g, float* __restrict__ e_g) {
   constexpr int KM = 32 * KT;
-  __shared__ __align__(16) float xcol[KM];
   __shared__ __align__(16) float vs[KM];
   __shared__ __align__(16) float ps[KM];
-  __shared__ float pp[32][KM + 1];
   __shared__ float wsum[32];
   __shared__ float scal[2];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -171,31 +196,29 @@ __global__ void __launch_bounds__(1024, 1) k_eig_tridiag(const float* __restrict
       A[a][c] = (i < k && j < k) ? 0.5f * (Hin[(int64_t)i * ldh + j] + Hin[(int64_t)j * ldh + i]) : 0.f;
     });
   });
-  for (int x = tid; x < k * k; x += 1024) Vg[x] = 0.f;
-  __syncthreads();
+  // rows k - 2 and k - 1 of Vg carry no reflector
+  const int z0 = (k >= 2) ? (k - 2) * k : 0;
+  for (int x = z0 + tid; x < k * k; x += 1024) Vg[x] = 0.f;
   for (int j = 0; j + 2 < k; ++j) {
-    // 1. column j (rows > j) from its warp
+    // R: the reflector of column j, in the warp that owns the column
     if (w == (j & 31)) {
+      const int cj = j >> 5, a1 = (j + 1) >> 5;
+      float col[KT];
       sfor<KT>([&](auto a) {
-        float val = 0.f;
+        col[a] = 0.f;
         sfor<KT>([&](auto c) {
-          if (c == (j >> 5)) val = A[a][c];
+          if (c == cj) col[a] = A[a][c];
         });
-        const int i = lane + 32 * a;
-        xcol[i] = (i > j && i < k) ? val : 0.f;
-        if (i == j) d_g[j] = val;
       });
-    }
-    __syncthreads();
-    // 2. the reflector, once
-    if (w == 0) {
-      float part = 0.f;
-      sfor<KT>([&](auto c) {
-        const int i = lane + 32 * c;
-        if (i >= j + 2) part = fmaf(xcol[i], xcol[i], part);
+      float part = 0.f, sel = 0.f;
+      sfor<KT>([&](auto a) {
+        const int i = lane + 32 * a;
+        if (i >= j + 2 && i < k) part = fmaf(col[a], col[a], part);
+        if (a == a1) sel = col[a];
+        if (i == j) d_g[j] = col[a];
       });
       const float sigma = warp_sum(part);
-      const float x0 = xcol[j + 1];
+      const float x0 = __shfl_sync(0xffffffffu, sel, (j + 1) & 31);
       float t = 0.f, iv = 0.f, beta = x0;
       if (sigma > 0.f) {
         const float mu = sqrtf(fmaf(x0, x0, sigma));
@@ -204,51 +227,54 @@ __global__ void __launch_bounds__(1024, 1) k_eig_tridiag(const float* __restrict
         beta = mu;
         iv = __fdividef(1.f, v0);
       }
-      sfor<KT>([&](auto c) {
-        const int i = lane + 32 * c;
-        const float v = (i == j + 1) ? 1.f : ((i > j + 1) ? xcol[i] * iv : 0.f);
+      sfor<KT>([&](auto a) {
+        const int i = lane + 32 * a;
+        const float v = (i == j + 1) ? 1.f : ((i > j + 1 && i < k) ? col[a] * iv : 0.f);
         vs[i] = v;
         if (i < k) Vg[(size_t)j * k + i] = (t != 0.f) ? v : 0.f;
       });
       if (lane == 0) {
-        scal[0] = t;
+        scal[j & 1] = t;
         tau_g[j] = t;
         e_g[j] = beta;
       }
     }
     __syncthreads();
-    const float t = scal[0];
+    const float t = scal[j & 1];
     if (t == 0.f) continue;                 // the same decision in every thread
-    // 3. partial H v over this thread's columns, and its share of v^T H v
+    // M: p_c = tau (H v)_c for this warp's columns c > j, share of v^T H v
     float vr[KT], vc[KT];
     sfor<KT>([&](auto a) { vr[a] = vs[lane + 32 * a]; });
     sfor<KT>([&](auto c) { vc[c] = vs[w + 32 * c]; });
     float share = 0.f;
-    sfor<KT>([&](auto a) {
-      float acc = 0.f;
-      sfor<KT>([&](auto c) { acc = fmaf(A[a][c], vc[c], acc); });
-      pp[w][lane + 32 * a] = acc;
-      share = fmaf(vr[a], acc, share);
+    sfor<KT>([&](auto c) {
+      if (32 * c + 31 > j) {
+        float acc = 0.f;
+        sfor<KT>([&](auto a) {
+          if (32 * a + 31 > j) acc = fmaf(A[a][c], vr[a], acc);
+        });
+        acc = warp_sum(acc);
+        share = fmaf(vc[c], acc, share);
+        const int col = w + 32 * c;
+        if (lane == c) ps[col] = (col > j && col < k) ? t * acc : 0.f;
+      } else if (lane == c) {
+        ps[w + 32 * c] = 0.f;
+      }
     });
-    share = warp_sum(share);
     if (lane == 0) wsum[w] = share;
     __syncthreads();
-    // 4. p = tau H v (rows > j)
-    for (int i = tid; i < KM; i += 1024) {
-      float sum = 0.f;
-#pragma unroll 8
-      for (int q = 0; q < 32; ++q) sum += pp[q][i];
-      ps[i] = (i > j && i < k) ? t * sum : 0.f;
-    }
+    // U: rank-2 update of the trailing block
     const float vhv = warp_sum(wsum[lane]);
     const float K = 0.5f * t * t * vhv;     // (tau / 2) v^T p
-    __syncthreads();
-    // 5. rank-2 update
     float wr[KT], wc[KT];
     sfor<KT>([&](auto a) { wr[a] = fmaf(-K, vr[a], ps[lane + 32 * a]); });
     sfor<KT>([&](auto c) { wc[c] = fmaf(-K, vc[c], ps[w + 32 * c]); });
     sfor<KT>([&](auto a) {
-      sfor<KT>([&](auto c) { A[a][c] -= fmaf(vr[a], wc[c], wr[a] * vc[c]); });
+      if (32 * a + 31 > j) {
+        sfor<KT>([&](auto c) {
+          if (32 * c + 31 > j) A[a][c] -= fmaf(vr[a], wc[c], wr[a] * vc[c]);
+        });
+      }
     });
   }
   // trailing 2 x 2 (or 1 x 1) block, written by the owners of its entries
@@ -265,7 +291,6 @@ __global__ void __launch_bounds__(1024, 1) k_eig_tridiag(const float* __restrict
     e_g[k - 1] = 0.f;
     tau_g[k - 1] = 0.f;
   }
-  __syncthreads();
 }
 
 // Steps 2-5 in one CTA of 16 warps, from T and the reflectors in global
@@ -334,22 +359,26 @@ __global__ void __launch_bounds__(512, 1) k_eig_vectors(const float* __restrict_
   const float step = (hi0 - lo0) * (1.f / (float)(NT + 1));
   cnt[tid] = sturm(d, e2, k, fmaf((float)(tid + 1), step, lo0), pivmin);
   __syncthreads();
-  for (int jj = ty; jj < r; jj += NW) {
-    const int want = k - jj;             // count reaching k - j brackets the j-th largest
-    int first = NT;
-    for (int u = 0; u < NW; ++u) {
-      const int tt = lane * NW + u;
-      if (cnt[tt] >= want) {
-        first = tt;
-        break;
+  // a warp refines the brackets of eigenvalues ty and ty + NW together
+  // (two independent Sturm chains in flight)
+  {
+    const int j0 = ty, j1 = ty + NW;
+    const bool has0 = j0 < r, has1 = j1 < r;
+    auto bracket = [&](int jj, float& lo, float& hi) {
+      const int want = k - jj;             // count reaching k - j brackets the j-th largest
+      int first = NT;
+      for (int u = 0; u < NW; ++u) {
+        const int tt = lane * NW + u;
+        if (cnt[tt] >= want) {
+          first = tt;
+          break;
+        }
       }
-    }
-    first = warp_min_i(first);
-    float lo = (first == 0) ? lo0 : fmaf((float)first, step, lo0);
-    float hi = (first == NT) ? hi0 : fmaf((float)(first + 1), step, lo0);
-    for (int it = 0; it < 4; ++it) {
-      const float x = lo + (hi - lo) * (float)(lane + 1) * (1.f / 33.f);
-      const int c = sturm(d, e2, k, x, pivmin);
+      first = warp_min_i(first);
+      lo = (first == 0) ? lo0 : fmaf((float)first, step, lo0);
+      hi = (first == NT) ? hi0 : fmaf((float)(first + 1), step, lo0);
+    };
+    auto narrow = [&](int c, int want, float x, float& lo, float& hi) {
       const unsigned ge = __ballot_sync(0xffffffffu, c >= want);
       const int sidx = ge ? (__ffs(ge) - 1) : 32;
       const float xs = __shfl_sync(0xffffffffu, x, sidx < 32 ? sidx : 31);
@@ -359,8 +388,24 @@ __global__ void __launch_bounds__(512, 1) k_eig_vectors(const float* __restrict_
         hi = xs;
         if (sidx > 0) lo = xp;
       }
+    };
+    float lo_0 = 0.f, hi_0 = 0.f, lo_1 = 0.f, hi_1 = 0.f;
+    if (has0) bracket(j0, lo_0, hi_0);
+    if (has1) bracket(j1, lo_1, hi_1);
+    for (int it = 0; it < 4 && has0; ++it) {
+      const float x0 = lo_0 + (hi_0 - lo_0) * (float)(lane + 1) * (1.f / 33.f);
+      if (has1) {
+        const float x1 = lo_1 + (hi_1 - lo_1) * (float)(lane + 1) * (1.f / 33.f);
+        int c0, c1;
+        sturm2(d, e2, k, x0, x1, pivmin, c0, c1);
+        narrow(c0, k - j0, x0, lo_0, hi_0);
+        narrow(c1, k - j1, x1, lo_1, hi_1);
+      } else {
+        narrow(sturm(d, e2, k, x0, pivmin), k - j0, x0, lo_0, hi_0);
+      }
     }
-    if (lane == 0) lam[jj] = 0.5f * (lo + hi);
+    if (lane == 0 && has0) lam[j0] = 0.5f * (lo_0 + hi_0);
+    if (lane == 0 && has1) lam[j1] = 0.5f * (lo_1 + hi_1);
   }
   __syncthreads();
 
@@ -456,36 +501,59 @@ __global__ void __launch_bounds__(512, 1) k_eig_vectors(const float* __restrict_
   }
 
   // ---------------------------------------------------------------- 5
-  for (int jj = ty; jj < r; jj += NW) {
-    float xv[KT];
-    const float* src = cur + (size_t)jj * ldx;
-#pragma unroll
-    for (int c = 0; c < KT; ++c) {
-      const int i = lane + 32 * c;
-      xv[c] = (i < k) ? src[i] : 0.f;
-    }
-    for (int h = k - 3; h >= 0; --h) {
-      const float th = tau[h];
-      if (th == 0.f) continue;
-      const float* vh = Vs + (size_t)h * k;
-      float vv[KT];
-      float dp = 0.f;
+  // a warp back-transforms vectors ty and ty + NW together: each reflector
+  // is read once for both and the two lane reductions overlap
+  {
+    const int j0 = ty, j1 = ty + NW;
+    const bool has1 = j1 < r;
+    if (j0 < r) {
+      float x0[KT], x1[KT];
+      const float* s0 = cur + (size_t)j0 * ldx;
+      const float* s1 = cur + (size_t)(has1 ? j1 : j0) * ldx;
 #pragma unroll
       for (int c = 0; c < KT; ++c) {
         const int i = lane + 32 * c;
-        vv[c] = (i < k) ? vh[i] : 0.f;
-        dp = fmaf(vv[c], xv[c], dp);
+        x0[c] = (i < k) ? s0[i] : 0.f;
+        x1[c] = (i < k) ? s1[i] : 0.f;
       }
-      const float sc = th * warp_sum(dp);
+      for (int h = k - 3; h >= 0; --h) {
+        const float th = tau[h];
+        if (th == 0.f) continue;
+        const float* vh = Vs + (size_t)h * k;
+        float vv[KT];
+        float dp0 = 0.f, dp1 = 0.f;
 #pragma unroll
-      for (int c = 0; c < KT; ++c) xv[c] = fmaf(-sc, vv[c], xv[c]);
-    }
+        for (int c = 0; c < KT; ++c) {
+          const int i = lane + 32 * c;
+          vv[c] = (i < k) ? vh[i] : 0.f;
+          dp0 = fmaf(vv[c], x0[c], dp0);
+          dp1 = fmaf(vv[c], x1[c], dp1);
+        }
 #pragma unroll
-    for (int c = 0; c < KT; ++c) {
-      const int i = lane + 32 * c;
-      if (i < k) V[(size_t)i * ldv + jj] = xv[c];
+        for (int o = 16; o > 0; o >>= 1) {
+          dp0 += __shfl_xor_sync(0xffffffffu, dp0, o);
+          dp1 += __shfl_xor_sync(0xffffffffu, dp1, o);
+        }
+        const float sc0 = th * dp0, sc1 = th * dp1;
+#pragma unroll
+        for (int c = 0; c < KT; ++c) {
+          x0[c] = fmaf(-sc0, vv[c], x0[c]);
+          x1[c] = fmaf(-sc1, vv[c], x1[c]);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < KT; ++c) {
+        const int i = lane + 32 * c;
+        if (i < k) {
+          V[(size_t)i * ldv + j0] = x0[c];
+          if (has1) V[(size_t)i * ldv + j1] = x1[c];
+        }
+      }
+      if (evals && lane == 0) {
+        evals[j0] = lam[j0];
+        if (has1) evals[j1] = lam[j1];
+      }
     }
-    if (evals && lane == 0) evals[jj] = lam[jj];
   }
 }
 

@@ -120,6 +120,34 @@ __device__ void nn_tile(const float* X, int ldx, int kk, const float* M, int ldm
   }
 }
 
+// Sums element e of the NC CTAs' shares (rank order, the same in every CTA)
+// for e0 <= e < e1 and hands each sum to put(e, s); four elements per
+// thread at a time, so that 4 NC remote loads are in flight together.
+template <int NC, typename Put>
+__device__ __forceinline__ void sum_ranks(cg::cluster_group& cl, float* mine, int e0, int e1, Put& put) {
+  const float* src[NC];
+#pragma unroll
+  for (int r = 0; r < NC; ++r) src[r] = cl.map_shared_rank(mine, r);
+  const int stride = blockDim.x;
+  for (int base = e0 + threadIdx.x; base < e1; base += 4 * stride) {
+    float x[4][NC];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = base + u * stride;
+#pragma unroll
+      for (int r = 0; r < NC; ++r) x[u][r] = (e < e1) ? src[r][e] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = base + u * stride;
+      float s = 0.f;
+#pragma unroll
+      for (int r = 0; r < NC; ++r) s += x[u][r];
+      if (e < e1) put(e, s);
+    }
+  }
+}
+
 __global__ void __launch_bounds__(OC_THREADS, 1) k_orth_cluster(ClusterOrthArgs a) {
   extern __shared__ __align__(16) float sm[];
   cg::cluster_group cl = cg::this_cluster();
@@ -166,15 +194,16 @@ __global__ void __launch_bounds__(OC_THREADS, 1) k_orth_cluster(ClusterOrthArgs 
     if (qz) tn_tile(Qc, kp, kp, Zc, bp, bp, rp, mine, bp);
     if (zz) tn_tile(Zc, bp, bp, Zc, bp, bp, rp, mine + kp * bp, bp);
     cl.sync();
-    const unsigned nc = cl.num_blocks();
     const int e0 = qz ? 0 : kp * bp, e1 = zz ? E : kp * bp;
-    for (int e = e0 + tid; e < e1; e += blockDim.x) {
-      float s = 0.f;
-#pragma unroll 8
-      for (unsigned r = 0; r < nc; ++r) s += cl.map_shared_rank(mine, r)[e];
+    auto put = [&](int e, float s) {
       const int row = e / bp, j = e % bp;
       if (row < kp) P[e] = s;
       else if (row - kp < b && j < b) G[(row - kp) * (b + 1) + j] = s;
+    };
+    switch (cl.num_blocks()) {
+      case 8: sum_ranks<8>(cl, mine, e0, e1, put); break;
+      case 4: sum_ranks<4>(cl, mine, e0, e1, put); break;
+      default: sum_ranks<1>(cl, mine, e0, e1, put); break;
     }
     __syncthreads();
     ++phase;

@@ -6,8 +6,10 @@
 //   proj : S = X^T C (b x n)          (projection U^T C of Alg. 3 step 10,
 //                                       with U split in BF16 hi + lo parts;
 //                                       first half of a power for tall C)
-//   ga   : Y = C (C^T X)              (one Krylov power for m <= 256, each
-//                                       column tile read from HBM once)
+//   ga   : Y = C (C^T X)              (one Krylov power, each column tile
+//                                       read from HBM once; for m > 256 the
+//                                       tile's 128-row chunks stream twice,
+//                                       the second time from L2)
 // Column tiles of C arrive by TMA (128-byte swizzle) into a ring of shared
 // memory stages.  Warp 0 issues TMA, warp 1 issues tcgen05.mma from one
 // thread and owns the TMEM allocation, warps 2-5 read TMEM (each warp the
@@ -41,7 +43,7 @@ struct TcParams {
   int stages;
   int64_t tiles;    // column tiles of width 64*kb
   int64_t row_groups;
-  int nchunks;      // proj: 128-row chunks of C per tile
+  int nchunks;      // proj, ga: row chunks of C per tile (ga: > 1 for tall C)
   int split_hi_lo;  // proj: out = D[:, c] + D[:, c + lo_off]
   int lo_off;
   int out_bf16;     // proj: output dtype
@@ -101,8 +103,11 @@ k_tc_stream(const __grid_constant__ CUtensorMap mapC, const __grid_constant__ CU
   // tiles handled by this CTA: cta_in_group, + ctas_in_group, ...
   const int64_t my_tiles =
       (p.tiles > cta_in_group) ? (p.tiles - cta_in_group + ctas_in_group - 1) / ctas_in_group : 0;
-  const uint32_t tmem_cols = (OP == OPK_PROJ) ? 128u : (OP == OPK_GA ? 256u : (p.mb * p.npad <= 32 ? 32u :
-                              p.mb * p.npad <= 64 ? 64u : p.mb * p.npad <= 128 ? 128u : 256u));
+  const uint32_t tmem_cols = (OP == OPK_PROJ) ? 128u
+                            : (OP == OPK_GA ? (128 + p.mb * p.npad <= 256 ? 256u : 512u)
+                                            : (p.mb * p.npad <= 32 ? 32u : p.mb * p.npad <= 64 ? 64u
+                                               : p.mb * p.npad <= 128 ? 128u : 256u));
+  const bool ga_tall = (OP == OPK_GA) && p.nchunks > 1;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) { mbar_init(&sh->full[s], 1); mbar_init(&sh->empty[s], 1); }
@@ -137,8 +142,28 @@ k_tc_stream(const __grid_constant__ CUtensorMap mapC, const __grid_constant__ CU
         for (int i = 0; i < nbox; ++i) tma_load_2d(xres + (size_t)i * p.x_box_bytes, &mapB, &sh->xfull, i * 64, 0);
       }
       int64_t fill = 0;
+      // tall Gram-apply: the chunks of tile t for C^T X, then those of tile
+      // t - 1 again for C T (by then its T is in shared memory)
+      auto load_tile = [&](int64_t it) {
+        const int64_t tile = cta_in_group + it * ctas_in_group;
+        for (int r = 0; r < p.nchunks && ok; ++r, ++fill) {
+          const int s = (int)(fill % S);
+          if (!mbar_wait(&sh->empty[s], (uint32_t)(((fill / S) & 1) ^ 1), abortp)) { tc_abort(sh, p.status); ok = false; break; }
+          uint8_t* st = ring + (size_t)s * p.stage_bytes;
+          mbar_arrive_expect_tx(&sh->full[s], (uint32_t)(2 * p.c_box_bytes));
+          for (int kb = 0; kb < 2; ++kb)
+            tma_load_2d(st + (size_t)kb * p.c_box_bytes, &mapC, &sh->full[s], (int)(tile * 128 + 64 * kb), r * 128);
+        }
+      };
+      if (ga_tall) {
+        for (int64_t it = 0; it < my_tiles && ok; ++it) {
+          load_tile(it);
+          if (it > 0) load_tile(it - 1);
+        }
+        if (my_tiles > 0) load_tile(my_tiles - 1);
+      }
       const int per_tile = (OP == OPK_PROJ) ? p.nchunks : 1;
-      for (int64_t it = 0; it < my_tiles && ok; ++it) {
+      for (int64_t it = 0; it < my_tiles && ok && !ga_tall; ++it) {
         const int64_t tile = cta_in_group + it * ctas_in_group;
         for (int ch = 0; ch < per_tile && ok; ++ch, ++fill) {
           const int s = (int)(fill % S);
@@ -244,6 +269,72 @@ k_tc_stream(const __grid_constant__ CUtensorMap mapC, const __grid_constant__ CU
           }
           if (ok) mma_commit(&sh->dfull[buf]);
         }
+      } else if (ga_tall) {
+        const uint32_t idesc1 = idesc_bf16(128, p.npad, 1, 0);   // T = C_tile^T X
+        const uint32_t idesc2 = idesc_bf16(128, p.npad, 0, 1);   // Z_r += C_chunk T
+        const uint32_t dz = tmem + 128;                           // Z_r at column 128 + r npad
+        if (!mbar_wait(&sh->xfull, 0, abortp)) { tc_abort(sh, p.status); ok = false; }
+        tc_fence_after();
+        const uint32_t xbase = smem_u32(xres);
+        auto next_stage = [&](uint32_t& base) -> bool {
+          const int s = (int)(fill % S);
+          if (!mbar_wait(&sh->full[s], (uint32_t)((fill / S) & 1), abortp)) { tc_abort(sh, p.status); return false; }
+          tc_fence_after();
+          base = smem_u32(ring + (size_t)s * p.stage_bytes);
+          return true;
+        };
+        auto release_stage = [&]() {
+          mma_commit(&sh->empty[(int)(fill % S)]);
+          ++fill;
+        };
+        // T(it) = sum_r C_r^T X_r over the 128-row chunks r
+        auto phase1 = [&](int64_t it) -> bool {
+          const int buf = (int)(it & 1);
+          const uint32_t use = (uint32_t)(it >> 1);
+          if (!mbar_wait(&sh->dempty[buf], (use & 1) ^ 1, abortp)) { tc_abort(sh, p.status); return false; }
+          tc_fence_after();
+          const uint32_t d = tmem + (uint32_t)(buf * 64);
+          for (int r = 0; r < p.nchunks; ++r) {
+            uint32_t base;
+            if (!next_stage(base)) return false;
+            for (int ks = 0; ks < 8; ++ks) {
+              // A: rows 16 ks .. 16 ks + 15 of the chunk, MN-major; B: X^T box 2 r + ks / 4
+              const uint64_t da = smem_desc(base + ks * 2048, p.c_box_bytes, 1024, SW_128B);
+              const uint64_t db =
+                  smem_desc(xbase + (2 * r + (ks >> 2)) * p.x_box_bytes + (ks & 3) * 32, 16, 1024, SW_128B);
+              mma_bf16(d, da, db, idesc1, (r > 0 || ks > 0) ? 1u : 0u);
+            }
+            release_stage();
+          }
+          mma_commit(&sh->dfull[buf]);
+          return true;
+        };
+        // Z_r += C_r T(it), T(it) in BF16 from the epilogue
+        auto phase2 = [&](int64_t it) -> bool {
+          const int buf = (int)(it & 1);
+          const uint32_t use = (uint32_t)(it >> 1);
+          if (!mbar_wait(&sh->tfull[buf], use & 1, abortp)) { tc_abort(sh, p.status); return false; }
+          tc_fence_after();
+          const uint32_t tb = smem_u32(tbuf + (size_t)buf * p.t_bytes);
+          for (int r = 0; r < p.nchunks; ++r) {
+            uint32_t base;
+            if (!next_stage(base)) return false;
+            for (int ks = 0; ks < 8; ++ks) {
+              const uint64_t da = smem_desc(base + (ks >> 2) * p.c_box_bytes + (ks & 3) * 32, 16, 1024, SW_128B);
+              const uint64_t db = smem_desc(tb + ks * 256, 128, 2048, SW_NONE);
+              mma_bf16(dz + (uint32_t)(r * p.npad), da, db, idesc2, (it > 0 || ks > 0) ? 1u : 0u);
+            }
+            release_stage();
+          }
+          mma_commit(&sh->tempty[buf]);
+          return true;
+        };
+        for (int64_t it = 0; it < my_tiles && ok; ++it) {
+          ok = phase1(it);
+          if (ok && it > 0) ok = phase2(it - 1);
+        }
+        if (ok && my_tiles > 0) ok = phase2(my_tiles - 1);
+        mma_commit(&sh->zfull);
       } else {  // OPK_GA
         const uint32_t idesc1 = idesc_bf16(128, p.npad, 1, 0);   // T = C_tile^T X
         const uint32_t idesc2 = idesc_bf16(128, p.npad, 0, 1);   // Z += C_tile T (T MN-major)
@@ -478,10 +569,10 @@ int box_rows_for(int64_t m, int cap) { return (int)imin(cap, (m + 15) / 16 * 16)
 // independent TMA -> MMA -> epilogue pipelines per SM keep more bytes in
 // flight than one deeper ring; else one CTA with the whole shared memory.
 // Sets p.stages; returns the CTAs per SM.
-int choose_residency(TcParams& p, int maxst) {
+int choose_residency(TcParams& p, int maxst, bool allow_two = true) {
   const int64_t fixed = 1024 + (int64_t)p.slack_bytes + p.x_res_bytes + 2 * (int64_t)p.t_bytes + sizeof(TcShared) + 64;
   const int64_t half = (SMEM_HALF - fixed) / p.stage_bytes;
-  if (half >= 3) {
+  if (allow_two && half >= 3) {
     p.stages = (int)imin(maxst, half);
     return 2;
   }
@@ -671,32 +762,50 @@ cudaError_t tc_proj(const __nv_bfloat16* C, int64_t m, int64_t n, const float* X
   return launch_tc<OPK_PROJ>(mc, mx, p, t.ctas, st);
 }
 
-// Y (m x b, ld ldo) = C (C^T X), m <= 256, b <= 64; X m x b FP32 (ld ldx).
-bool tc_ga_ok(int64_t m, int64_t n, int b) { return m <= 256 && b <= 64 && tc_shape_ok(m, n); }
-
-size_t tc_ga_scratch_bytes(int64_t m, int b) {
-  const int64_t ldt = (m + 7) / 8 * 8;
-  return (size_t)pad16(b) * ldt * 2 + 256;
-}
-
+// Y (m x b, ld ldo) = C (C^T X), b <= 64; X m x b FP32 (ld ldx).  For
+// m <= 256 a stage holds the whole height of a 128-column tile; taller C
+// streams each tile as 128-row chunks twice (C^T X, then C T), so T and the
+// m x b accumulators stay on chip: 128 + ceil(m / 128) pad16(b) TMEM columns
+// must fit in 512.
 TcShape ga_shape(int64_t m, int64_t n, int b) {
   TcShape t;
   TcParams& p = t.p;
   p.m = m; p.n = n; p.b = b; p.npad = pad16(b);
   p.kb = 2; p.row_groups = 1;
-  p.c_box_rows = box_rows_for(m, 256);
-  p.mpad = (int)ceil_div(p.c_box_rows, 64) * 64;
   p.mb = (int)ceil_div(m, 128);
-  p.c_box_bytes = p.c_box_rows * 128;
   p.x_box_bytes = p.npad * 128;
-  p.x_res_bytes = (p.mpad / 64) * p.x_box_bytes;
   p.t_bytes = p.npad / 8 * 2048;
-  p.stage_bytes = 2 * p.c_box_bytes;
-  p.slack_bytes = 16384;
   p.tiles = ceil_div(n, 128);
-  t.per_sm = choose_residency(p, 8);
+  if (m <= 256) {
+    p.nchunks = 1;
+    p.c_box_rows = box_rows_for(m, 256);
+    p.mpad = (int)ceil_div(p.c_box_rows, 64) * 64;
+    p.slack_bytes = 16384;               // C T reads 128 rows of a shorter box
+  } else {
+    p.nchunks = p.mb;
+    p.c_box_rows = 128;
+    p.mpad = 128 * p.nchunks;            // X^T boxes past m are zero-filled
+    p.slack_bytes = 0;
+  }
+  p.c_box_bytes = p.c_box_rows * 128;
+  p.x_res_bytes = (p.mpad / 64) * p.x_box_bytes;
+  p.stage_bytes = 2 * p.c_box_bytes;
+  // 512 TMEM columns (128 + mb npad > 256) leave room for one CTA per SM
+  t.per_sm = choose_residency(p, 8, 128 + p.mb * p.npad <= 256);
   t.ctas = (int)imin(p.tiles, (int64_t)num_sms() * t.per_sm);
   return t;
+}
+
+bool tc_ga_ok(int64_t m, int64_t n, int b) {
+  if (b > 64 || b < 1 || !tc_shape_ok(m, n)) return false;
+  if (m <= 256) return true;
+  if (128 + ceil_div(m, 128) * pad16(b) > 512) return false;
+  return ga_shape(m, n, b).p.stages >= 2;
+}
+
+size_t tc_ga_scratch_bytes(int64_t m, int b) {
+  const int64_t ldt = (m + 7) / 8 * 8;
+  return (size_t)pad16(b) * ldt * 2 + 256;
 }
 
 int64_t tc_ga_partials(int64_t m, int64_t n, int b) { return (int64_t)ga_shape(m, n, b).ctas * m * b; }

@@ -88,7 +88,10 @@ def _tc_path(n, bf16):
 SHAPES = [(1, 1, 1), (7, 31, 9), (40, 4097, 30), (129, 31, 1), (256, 2050, 40), (33, 1000, 15),
           (300, 777, 20), (7, 4097, 40),
           (40, 4104, 30), (256, 2048, 40), (300, 1024, 20), (7, 4104, 40), (129, 1000, 1),
-          (800, 2056, 30), (64, 1032, 64), (128, 4096, 16), (1, 64, 8), (200, 72, 33)]
+          (800, 2056, 30), (64, 1032, 64), (128, 4096, 16), (1, 64, 8), (200, 72, 33),
+          # tall Gram-apply: 128-row chunks, up to the 512-column TMEM limit
+          # (1536 x 32 fills it; 1537 x 32 does not fit and falls back)
+          (1536, 1024, 32), (897, 2048, 16), (640, 1032, 64), (1537, 1024, 32), (520, 8200, 48)]
 
 
 @pytest.mark.parametrize("m,n,b", SHAPES)

@@ -74,7 +74,8 @@ def test_decompose_ignores_prior_memory_contents(tt, case, storage, exhaust, met
         assert torch.equal(a, b)
 
 
-PASS_SHAPES = [(7, 31, 9), (40, 4104, 30), (300, 1024, 20), (129, 1000, 1), (200, 72, 33), (64, 1032, 64)]
+PASS_SHAPES = [(7, 31, 9), (40, 4104, 30), (300, 1024, 20), (129, 1000, 1), (200, 72, 33), (64, 1032, 64),
+               (800, 2056, 30), (1536, 1024, 32)]
 
 
 @pytest.mark.parametrize("m,n,b", PASS_SHAPES)
