@@ -206,17 +206,28 @@ k_tc_stream(const __grid_constant__ CUtensorMap mapC, const __grid_constant__ CU
     if (lane == 0) {
       bool ok = true;
       int64_t fill = 0;
+      // descriptors relative to the ring base (offsets of xres and tbuf too):
+      // K-major 128-byte-swizzled operands, the MN-major C tile (its two
+      // 64-column atoms one box apart), and T (8 x 8 core matrices)
+      const uint32_t ring_s = smem_u32(ring);
+      const DescGen gK(ring_s, 16, 1024, SW_128B);
+      const DescGen gM(ring_s, (uint32_t)p.c_box_bytes, 1024, SW_128B);
+      const DescGen gT(ring_s, 128, 2048, SW_NONE);
+      const uint32_t xres_off = (uint32_t)(xres - ring), tbuf_off = (uint32_t)(tbuf - ring);
       if (OP == OPK_GRAM) {
         const uint32_t idesc = idesc_bf16(128, p.npad, 0, 0);
         for (int64_t it = 0; it < my_tiles && ok; ++it, ++fill) {
           const int s = (int)(fill % S);
           if (!mbar_wait(&sh->full[s], (uint32_t)((fill / S) & 1), abortp)) { tc_abort(sh, p.status); ok = false; break; }
           tc_fence_after();
-          const uint32_t base = smem_u32(ring + (size_t)s * p.stage_bytes);
-          for (int ks = 0; ks < 4 * p.kb; ++ks) {
-            const uint32_t a = base + (ks >> 2) * p.c_box_bytes + (ks & 3) * 32;
-            const uint64_t da = smem_desc(a, 16, 1024, SW_128B);
-            mma_bf16(tmem, da, da, idesc, (it > 0 || ks > 0) ? 1u : 0u);
+          const uint32_t soff = (uint32_t)s * (uint32_t)p.stage_bytes;
+          for (int kb = 0; kb < p.kb; ++kb) {
+            const uint32_t boff = soff + (uint32_t)(kb * p.c_box_bytes);
+#pragma unroll
+            for (int k4 = 0; k4 < 4; ++k4) {
+              const uint64_t da = gK.at(boff + k4 * 32);
+              mma_bf16(tmem, da, da, idesc, (it > 0 || kb > 0 || k4 > 0) ? 1u : 0u);
+            }
           }
           mma_commit(&sh->empty[s]);
         }
@@ -227,14 +238,15 @@ k_tc_stream(const __grid_constant__ CUtensorMap mapC, const __grid_constant__ CU
           const int s = (int)(fill % S);
           if (!mbar_wait(&sh->full[s], (uint32_t)((fill / S) & 1), abortp)) { tc_abort(sh, p.status); ok = false; break; }
           tc_fence_after();
-          const uint32_t base = smem_u32(ring + (size_t)s * p.stage_bytes);
-          const uint32_t sb = base + p.mb * p.c_box_bytes;
-          for (int b = 0; b < p.mb; ++b)
-            for (int ks = 0; ks < 4; ++ks) {
-              const uint64_t da = smem_desc(base + b * p.c_box_bytes + ks * 32, 16, 1024, SW_128B);
-              const uint64_t db = smem_desc(sb + ks * 32, 16, 1024, SW_128B);
-              mma_bf16(tmem + (uint32_t)(b * p.npad), da, db, idesc, (it > 0 || ks > 0) ? 1u : 0u);
-            }
+          const uint32_t soff = (uint32_t)s * (uint32_t)p.stage_bytes;
+          const uint32_t sboff = soff + (uint32_t)(p.mb * p.c_box_bytes);
+          for (int b = 0; b < p.mb; ++b) {
+            const uint32_t aoff = soff + (uint32_t)(b * p.c_box_bytes);
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks)
+              mma_bf16(tmem + (uint32_t)(b * p.npad), gK.at(aoff + ks * 32), gK.at(sboff + ks * 32), idesc,
+                       (it > 0 || ks > 0) ? 1u : 0u);
+          }
           mma_commit(&sh->empty[s]);
         }
         mma_commit(&sh->zfull);
@@ -256,13 +268,13 @@ k_tc_stream(const __grid_constant__ CUtensorMap mapC, const __grid_constant__ CU
             const int s = (int)(fill % S);
             if (!mbar_wait(&sh->full[s], (uint32_t)((fill / S) & 1), abortp)) { tc_abort(sh, p.status); ok = false; break; }
             tc_fence_after();
-            const uint32_t base = smem_u32(ring + (size_t)s * p.stage_bytes);
-            const uint32_t xb = p.x_resident ? smem_u32(xres) : base + 2 * p.c_box_bytes;
+            const uint32_t soff = (uint32_t)s * (uint32_t)p.stage_bytes;
+            const uint32_t xoff = p.x_resident ? xres_off : soff + 2 * (uint32_t)p.c_box_bytes;
             for (int ks = 0; ks < ksteps; ++ks) {
               // A: rows 16 ks .. 16 ks + 15 of the chunk; two 64-column atoms p.c_box_bytes apart
-              const uint64_t da = smem_desc(base + ks * 2048, p.c_box_bytes, 1024, SW_128B);
+              const uint64_t da = gM.at(soff + ks * 2048);
               // B: X^T box (npad rows x 64 of m), K offset within the 64-wide atom
-              const uint64_t db = smem_desc(xb + (ks >> 2) * p.x_box_bytes + (ks & 3) * 32, 16, 1024, SW_128B);
+              const uint64_t db = gK.at(xoff + (ks >> 2) * p.x_box_bytes + (ks & 3) * 32);
               mma_bf16(d, da, db, idesc, (ch > 0 || ks > 0) ? 1u : 0u);
             }
             mma_commit(&sh->empty[s]);
@@ -275,12 +287,11 @@ k_tc_stream(const __grid_constant__ CUtensorMap mapC, const __grid_constant__ CU
         const uint32_t dz = tmem + 128;                           // Z_r at column 128 + r npad
         if (!mbar_wait(&sh->xfull, 0, abortp)) { tc_abort(sh, p.status); ok = false; }
         tc_fence_after();
-        const uint32_t xbase = smem_u32(xres);
-        auto next_stage = [&](uint32_t& base) -> bool {
+        auto next_stage = [&](uint32_t& soff) -> bool {
           const int s = (int)(fill % S);
           if (!mbar_wait(&sh->full[s], (uint32_t)((fill / S) & 1), abortp)) { tc_abort(sh, p.status); return false; }
           tc_fence_after();
-          base = smem_u32(ring + (size_t)s * p.stage_bytes);
+          soff = (uint32_t)s * (uint32_t)p.stage_bytes;
           return true;
         };
         auto release_stage = [&]() {
@@ -295,13 +306,14 @@ k_tc_stream(const __grid_constant__ CUtensorMap mapC, const __grid_constant__ CU
           tc_fence_after();
           const uint32_t d = tmem + (uint32_t)(buf * 64);
           for (int r = 0; r < p.nchunks; ++r) {
-            uint32_t base;
-            if (!next_stage(base)) return false;
+            uint32_t soff;
+            if (!next_stage(soff)) return false;
+            const uint32_t xoff = xres_off + (uint32_t)(2 * r * p.x_box_bytes);
+#pragma unroll
             for (int ks = 0; ks < 8; ++ks) {
               // A: rows 16 ks .. 16 ks + 15 of the chunk, MN-major; B: X^T box 2 r + ks / 4
-              const uint64_t da = smem_desc(base + ks * 2048, p.c_box_bytes, 1024, SW_128B);
-              const uint64_t db =
-                  smem_desc(xbase + (2 * r + (ks >> 2)) * p.x_box_bytes + (ks & 3) * 32, 16, 1024, SW_128B);
+              const uint64_t da = gM.at(soff + ks * 2048);
+              const uint64_t db = gK.at(xoff + (ks >> 2) * p.x_box_bytes + (ks & 3) * 32);
               mma_bf16(d, da, db, idesc1, (r > 0 || ks > 0) ? 1u : 0u);
             }
             release_stage();
@@ -315,13 +327,14 @@ k_tc_stream(const __grid_constant__ CUtensorMap mapC, const __grid_constant__ CU
           const uint32_t use = (uint32_t)(it >> 1);
           if (!mbar_wait(&sh->tfull[buf], use & 1, abortp)) { tc_abort(sh, p.status); return false; }
           tc_fence_after();
-          const uint32_t tb = smem_u32(tbuf + (size_t)buf * p.t_bytes);
+          const uint32_t toff = tbuf_off + (uint32_t)(buf * p.t_bytes);
           for (int r = 0; r < p.nchunks; ++r) {
-            uint32_t base;
-            if (!next_stage(base)) return false;
+            uint32_t soff;
+            if (!next_stage(soff)) return false;
+#pragma unroll
             for (int ks = 0; ks < 8; ++ks) {
-              const uint64_t da = smem_desc(base + (ks >> 2) * p.c_box_bytes + (ks & 3) * 32, 16, 1024, SW_128B);
-              const uint64_t db = smem_desc(tb + ks * 256, 128, 2048, SW_NONE);
+              const uint64_t da = gK.at(soff + (ks >> 2) * p.c_box_bytes + (ks & 3) * 32);
+              const uint64_t db = gT.at(toff + ks * 256);
               mma_bf16(dz + (uint32_t)(r * p.npad), da, db, idesc2, (it > 0 || ks > 0) ? 1u : 0u);
             }
             release_stage();
@@ -341,29 +354,28 @@ k_tc_stream(const __grid_constant__ CUtensorMap mapC, const __grid_constant__ CU
         const uint32_t dz = tmem + 128;                           // Z accumulators (mb x npad)
         if (!mbar_wait(&sh->xfull, 0, abortp)) { tc_abort(sh, p.status); ok = false; }
         tc_fence_after();
-        const uint32_t xbase = smem_u32(xres);
         auto gemm1 = [&](int64_t it, int s) {
           const int buf = (int)(it & 1);
           const uint32_t d = tmem + (uint32_t)(buf * 64);
-          const uint32_t base = smem_u32(ring + (size_t)s * p.stage_bytes);
+          const uint32_t soff = (uint32_t)s * (uint32_t)p.stage_bytes;
           for (int ks = 0; ks < p.c_box_rows / 16; ++ks) {
-            const uint64_t da = smem_desc(base + ks * 2048, p.c_box_bytes, 1024, SW_128B);
-            const uint64_t db = smem_desc(xbase + (ks >> 2) * p.x_box_bytes + (ks & 3) * 32, 16, 1024, SW_128B);
+            const uint64_t da = gM.at(soff + ks * 2048);
+            const uint64_t db = gK.at(xres_off + (ks >> 2) * p.x_box_bytes + (ks & 3) * 32);
             mma_bf16(d, da, db, idesc1, ks > 0 ? 1u : 0u);
           }
           mma_commit(&sh->dfull[buf]);
         };
         auto gemm2 = [&](int64_t it, int s) {
           const int buf = (int)(it & 1);
-          const uint32_t base = smem_u32(ring + (size_t)s * p.stage_bytes);
-          const uint32_t tb = smem_u32(tbuf + (size_t)buf * p.t_bytes);
+          const uint32_t soff = (uint32_t)s * (uint32_t)p.stage_bytes;
+          const uint32_t toff = tbuf_off + (uint32_t)(buf * p.t_bytes);
           for (int b = 0; b < p.mb; ++b)
+#pragma unroll
             for (int ks = 0; ks < 8; ++ks) {
-              const uint64_t da = smem_desc(base + (ks >> 2) * p.c_box_bytes + b * 16384 + (ks & 3) * 32, 16, 1024,
-                                            SW_128B);
+              const uint64_t da = gK.at(soff + (ks >> 2) * p.c_box_bytes + b * 16384 + (ks & 3) * 32);
               // T_j: MN-major, no swizzle: 8x8 core matrices; K groups 128 B apart,
               // MN groups (8 columns of T) 2048 B apart
-              const uint64_t db = smem_desc(tb + ks * 256, 128, 2048, SW_NONE);
+              const uint64_t db = gT.at(toff + ks * 256);
               mma_bf16(dz + (uint32_t)(b * p.npad), da, db, idesc2, (it > 0 || ks > 0) ? 1u : 0u);
             }
           mma_commit(&sh->tempty[buf]);

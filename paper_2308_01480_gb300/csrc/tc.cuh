@@ -47,6 +47,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 // Waits for the phase of `bar` with the given parity.  Gives up after
 // about two seconds or when *abort becomes nonzero; returns false then.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+  if (mbar_try_wait(bar, parity)) return true;   // the common case reads no timer
   const uint64_t t0 = globaltimer();
   for (uint32_t it = 0; it < (1u << 26); ++it) {
     if (mbar_try_wait(bar, parity)) return true;
@@ -145,6 +146,23 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo_bytes
   d |= (uint64_t)(swizzle & 7u) << 61;
   return d;
 }
+
+// A descriptor split into its layout fields (everything but the start
+// address) and a shared-memory base: at(off) is the descriptor of base + off
+// (off a multiple of 16) for one 32-bit add, so that an MMA issue loop does
+// not rebuild descriptors.  Shared-memory addresses stay below 2^18, so the
+// 14-bit address field never carries into the layout fields.
+struct DescGen {
+  uint32_t lo, hi;
+  __device__ __forceinline__ DescGen(uint32_t saddr, uint32_t lbo_bytes, uint32_t sbo_bytes, uint32_t swizzle) {
+    const uint64_t d = smem_desc(saddr, lbo_bytes, sbo_bytes, swizzle);
+    lo = (uint32_t)d;
+    hi = (uint32_t)(d >> 32);
+  }
+  __device__ __forceinline__ uint64_t at(uint32_t off_bytes) const {
+    return ((uint64_t)hi << 32) | (uint64_t)(lo + (off_bytes >> 4));
+  }
+};
 
 }  // namespace tc
 }  // namespace ttr
