@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(1024, 1) k_eig_tridiag(const float* __restrict
   constexpr int KM = 32 * KT;
   __shared__ __align__(16) float vs[KM];
   __shared__ __align__(16) float ps[KM];
-  __shared__ float wsum[32];
+  __shared__ __align__(16) float wsum[32];
   __shared__ float scal[2];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
 
@@ -242,29 +242,62 @@ __global__ void __launch_bounds__(1024, 1) k_eig_tridiag(const float* __restrict
     __syncthreads();
     const float t = scal[j & 1];
     if (t == 0.f) continue;                 // the same decision in every thread
-    // M: p_c = tau (H v)_c for this warp's columns c > j, share of v^T H v
+    // M: p_c = tau (H v)_c for this warp's columns c > j, share of v^T H v.
+    // The KT column sums and the share (slot 7) are reduced over the lanes
+    // together: each butterfly level keeps half of the values and sends the
+    // other half, 9 shuffles in all, after which lanes 4i .. 4i + 3 hold sum i.
     float vr[KT], vc[KT];
     sfor<KT>([&](auto a) { vr[a] = vs[lane + 32 * a]; });
     sfor<KT>([&](auto c) { vc[c] = vs[w + 32 * c]; });
-    float share = 0.f;
+    float x8[8];
+    sfor<8>([&](auto c) { x8[c] = 0.f; });
     sfor<KT>([&](auto c) {
       if (32 * c + 31 > j) {
         float acc = 0.f;
         sfor<KT>([&](auto a) {
           if (32 * a + 31 > j) acc = fmaf(A[a][c], vr[a], acc);
         });
-        acc = warp_sum(acc);
-        share = fmaf(vc[c], acc, share);
-        const int col = w + 32 * c;
-        if (lane == c) ps[col] = (col > j && col < k) ? t * acc : 0.f;
-      } else if (lane == c) {
-        ps[w + 32 * c] = 0.f;
+        x8[c] = acc;
+        x8[7] = fmaf(vc[c], acc, x8[7]);
       }
     });
-    if (lane == 0) wsum[w] = share;
+    {
+      const unsigned full = 0xffffffffu;
+      const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4;
+      float x4[4], x2[2];
+      sfor<4>([&](auto q) {
+        const float send = h4 ? x8[q] : x8[q + 4], keep = h4 ? x8[q + 4] : x8[q];
+        x4[q] = keep + __shfl_xor_sync(full, send, 16);
+      });
+      sfor<2>([&](auto q) {
+        const float send = h3 ? x4[q] : x4[q + 2], keep = h3 ? x4[q + 2] : x4[q];
+        x2[q] = keep + __shfl_xor_sync(full, send, 8);
+      });
+      float x1 = (h2 ? x2[1] : x2[0]) + __shfl_xor_sync(full, h2 ? x2[0] : x2[1], 4);
+      x1 += __shfl_xor_sync(full, x1, 2);
+      x1 += __shfl_xor_sync(full, x1, 1);
+      const int slot = (lane >> 2) & 7;
+      if ((lane & 3) == 0) {
+        if (slot < KT) {
+          const int col = w + 32 * slot;
+          ps[col] = (col > j && col < k) ? t * x1 : 0.f;
+        } else if (slot == 7) {
+          wsum[w] = x1;
+        }
+      }
+    }
     __syncthreads();
-    // U: rank-2 update of the trailing block
-    const float vhv = warp_sum(wsum[lane]);
+    // U: rank-2 update of the trailing block; v^T H v from the 32 shares
+    float vhv;
+    {
+      float q0 = 0.f, q1 = 0.f, q2 = 0.f, q3 = 0.f;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float4 s4 = reinterpret_cast<const float4*>(wsum)[q];
+        q0 += s4.x; q1 += s4.y; q2 += s4.z; q3 += s4.w;
+      }
+      vhv = (q0 + q1) + (q2 + q3);
+    }
     const float K = 0.5f * t * t * vhv;     // (tau / 2) v^T p
     float wr[KT], wc[KT];
     sfor<KT>([&](auto a) { wr[a] = fmaf(-K, vr[a], ps[lane + 32 * a]); });
