@@ -38,6 +38,7 @@ constexpr int ER_KTMAX = 5;
 // register-tile indices are constants however large the unrolled body.
 template <int I>
 struct CIdx {
+  static constexpr int value = I;
   __host__ __device__ constexpr operator int() const { return I; }
 };
 template <typename F, int... I>
@@ -177,7 +178,8 @@ __host__ __device__ inline size_t er_smem_floats(int KM, int k, int r) {
 //   U  every thread applies H -= v w^T + w v^T, w = p - (tau/2)(v^T p) v,
 //      to its entries of the trailing block; the owner of column j + 1
 //      then goes straight on to its reflector.
-// Tiles lying wholly in finished rows or columns are skipped.
+// Tiles lying wholly in finished rows or columns are skipped (at compile
+// time: the column loop is split into 32-column segments).
 template <int KT>
 __global__ void __launch_bounds__(1024, 1) k_eig_tridiag(const float* __restrict__ Hin, int64_t ldh, int k,
                                                         float* __restrict__ Vg, float* __restrict__ tau_g,
@@ -199,117 +201,113 @@ __global__ void __launch_bounds__(1024, 1) k_eig_tridiag(const float* __restrict
   // rows k - 2 and k - 1 of Vg carry no reflector
   const int z0 = (k >= 2) ? (k - 2) * k : 0;
   for (int x = z0 + tid; x < k * k; x += 1024) Vg[x] = 0.f;
-  for (int j = 0; j + 2 < k; ++j) {
-    // R: the reflector of column j, in the warp that owns the column
-    if (w == (j & 31)) {
-      const int cj = j >> 5, a1 = (j + 1) >> 5;
-      float col[KT];
-      sfor<KT>([&](auto a) {
-        col[a] = 0.f;
-        sfor<KT>([&](auto c) {
-          if (c == cj) col[a] = A[a][c];
-        });
-      });
-      float part = 0.f, sel = 0.f;
-      sfor<KT>([&](auto a) {
-        const int i = lane + 32 * a;
-        if (i >= j + 2 && i < k) part = fmaf(col[a], col[a], part);
-        if (a == a1) sel = col[a];
-        if (i == j) d_g[j] = col[a];
-      });
-      const float sigma = warp_sum(part);
-      const float x0 = __shfl_sync(0xffffffffu, sel, (j + 1) & 31);
-      float t = 0.f, iv = 0.f, beta = x0;
-      if (sigma > 0.f) {
-        const float mu = sqrtf(fmaf(x0, x0, sigma));
-        const float v0 = (x0 <= 0.f) ? x0 - mu : __fdividef(-sigma, x0 + mu);
-        t = __fdividef(2.f * v0 * v0, fmaf(v0, v0, sigma));
-        beta = mu;
-        iv = __fdividef(1.f, v0);
-      }
-      sfor<KT>([&](auto a) {
-        const int i = lane + 32 * a;
-        const float v = (i == j + 1) ? 1.f : ((i > j + 1 && i < k) ? col[a] * iv : 0.f);
-        vs[i] = v;
-        if (i < k) Vg[(size_t)j * k + i] = (t != 0.f) ? v : 0.f;
-      });
-      if (lane == 0) {
-        scal[j & 1] = t;
-        tau_g[j] = t;
-        e_g[j] = beta;
-      }
-    }
-    __syncthreads();
-    const float t = scal[j & 1];
-    if (t == 0.f) continue;                 // the same decision in every thread
-    // M: p_c = tau (H v)_c for this warp's columns c > j, share of v^T H v.
-    // The KT column sums and the share (slot 7) are reduced over the lanes
-    // together: each butterfly level keeps half of the values and sends the
-    // other half, 9 shuffles in all, after which lanes 4i .. 4i + 3 hold sum i.
-    float vr[KT], vc[KT];
-    sfor<KT>([&](auto a) { vr[a] = vs[lane + 32 * a]; });
-    sfor<KT>([&](auto c) { vc[c] = vs[w + 32 * c]; });
-    float x8[8];
-    sfor<8>([&](auto c) { x8[c] = 0.f; });
-    sfor<KT>([&](auto c) {
-      if (32 * c + 31 > j) {
-        float acc = 0.f;
+  // Columns 32 s .. 32 s + 31 form segment s: there the tiles a < s and
+  // c < s are finished (compile-time), so each segment is its own loop with
+  // only its live tiles.  (At the segment's last column tile s is finished
+  // too; it only adds exact zeros.)
+  sfor<KT>([&](auto seg) {
+    constexpr int S = decltype(seg)::value;
+    const int jend = min(32 * S + 32, k - 2);
+    for (int j = 32 * S; j < jend; ++j) {
+      // R: the reflector of column j, in the warp that owns the column
+      if (w == (j & 31)) {
+        float part = 0.f, sel = 0.f;
+        const bool next_seg = (j + 1) >> 5 != S;
         sfor<KT>([&](auto a) {
-          if (32 * a + 31 > j) acc = fmaf(A[a][c], vr[a], acc);
+          if (a >= S) {
+            const float x = A[a][S];
+            const int i = lane + 32 * a;
+            if (i >= j + 2 && i < k) part = fmaf(x, x, part);
+            if (a == S && !next_seg) sel = x;
+            if (a == S + 1 && next_seg) sel = x;
+            if (i == j) d_g[j] = x;
+          }
         });
-        x8[c] = acc;
-        x8[7] = fmaf(vc[c], acc, x8[7]);
-      }
-    });
-    {
-      const unsigned full = 0xffffffffu;
-      const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4;
-      float x4[4], x2[2];
-      sfor<4>([&](auto q) {
-        const float send = h4 ? x8[q] : x8[q + 4], keep = h4 ? x8[q + 4] : x8[q];
-        x4[q] = keep + __shfl_xor_sync(full, send, 16);
-      });
-      sfor<2>([&](auto q) {
-        const float send = h3 ? x4[q] : x4[q + 2], keep = h3 ? x4[q + 2] : x4[q];
-        x2[q] = keep + __shfl_xor_sync(full, send, 8);
-      });
-      float x1 = (h2 ? x2[1] : x2[0]) + __shfl_xor_sync(full, h2 ? x2[0] : x2[1], 4);
-      x1 += __shfl_xor_sync(full, x1, 2);
-      x1 += __shfl_xor_sync(full, x1, 1);
-      const int slot = (lane >> 2) & 7;
-      if ((lane & 3) == 0) {
-        if (slot < KT) {
-          const int col = w + 32 * slot;
-          ps[col] = (col > j && col < k) ? t * x1 : 0.f;
-        } else if (slot == 7) {
-          wsum[w] = x1;
+        const float sigma = warp_sum(part);
+        const float x0 = __shfl_sync(0xffffffffu, sel, (j + 1) & 31);
+        float t = 0.f, iv = 0.f, beta = x0;
+        if (sigma > 0.f) {
+          const float mu = sqrtf(fmaf(x0, x0, sigma));
+          const float v0 = (x0 <= 0.f) ? x0 - mu : __fdividef(-sigma, x0 + mu);
+          t = __fdividef(2.f * v0 * v0, fmaf(v0, v0, sigma));
+          beta = mu;
+          iv = __fdividef(1.f, v0);
+        }
+        sfor<KT>([&](auto a) {
+          const int i = lane + 32 * a;
+          const float v = (a < S) ? 0.f : ((i == j + 1) ? 1.f : ((i > j + 1 && i < k) ? A[a][S] * iv : 0.f));
+          vs[i] = v;
+          if (i < k) Vg[(size_t)j * k + i] = (t != 0.f) ? v : 0.f;
+        });
+        if (lane == 0) {
+          scal[j & 1] = t;
+          tau_g[j] = t;
+          e_g[j] = beta;
         }
       }
-    }
-    __syncthreads();
-    // U: rank-2 update of the trailing block; v^T H v from the 32 shares
-    float vhv;
-    {
-      float q0 = 0.f, q1 = 0.f, q2 = 0.f, q3 = 0.f;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const float4 s4 = reinterpret_cast<const float4*>(wsum)[q];
-        q0 += s4.x; q1 += s4.y; q2 += s4.z; q3 += s4.w;
-      }
-      vhv = (q0 + q1) + (q2 + q3);
-    }
-    const float K = 0.5f * t * t * vhv;     // (tau / 2) v^T p
-    float wr[KT], wc[KT];
-    sfor<KT>([&](auto a) { wr[a] = fmaf(-K, vr[a], ps[lane + 32 * a]); });
-    sfor<KT>([&](auto c) { wc[c] = fmaf(-K, vc[c], ps[w + 32 * c]); });
-    sfor<KT>([&](auto a) {
-      if (32 * a + 31 > j) {
-        sfor<KT>([&](auto c) {
-          if (32 * c + 31 > j) A[a][c] -= fmaf(vr[a], wc[c], wr[a] * vc[c]);
+      __syncthreads();
+      const float t = scal[j & 1];
+      if (t == 0.f) continue;               // the same decision in every thread
+      // M: p_c = tau (H v)_c for this warp's live columns, share of v^T H v.
+      // The KT column sums and the share (slot 7) are reduced over the lanes
+      // together: each butterfly level keeps half of the values and sends the
+      // other half, 9 shuffles in all, after which lanes 4i .. 4i + 3 hold sum i.
+      float vr[KT], vc[KT];
+      sfor<KT>([&](auto a) { vr[a] = (a >= S) ? vs[lane + 32 * a] : 0.f; });
+      sfor<KT>([&](auto c) { vc[c] = (c >= S) ? vs[w + 32 * c] : 0.f; });
+      float x8[8];
+      sfor<8>([&](auto c) { x8[c] = 0.f; });
+      sfor<KT>([&](auto c) {
+        if (c >= S) {
+          float acc = 0.f;
+          sfor<KT>([&](auto a) {
+            if (a >= S) acc = fmaf(A[a][c], vr[a], acc);
+          });
+          x8[c] = acc;
+          x8[7] = fmaf(vc[c], acc, x8[7]);
+        }
+      });
+      {
+        const unsigned full = 0xffffffffu;
+        const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4;
+        float x4[4], x2[2];
+        sfor<4>([&](auto q) {
+          const float send = h4 ? x8[q] : x8[q + 4], keep = h4 ? x8[q + 4] : x8[q];
+          x4[q] = keep + __shfl_xor_sync(full, send, 16);
         });
+        sfor<2>([&](auto q) {
+          const float send = h3 ? x4[q] : x4[q + 2], keep = h3 ? x4[q + 2] : x4[q];
+          x2[q] = keep + __shfl_xor_sync(full, send, 8);
+        });
+        float x1 = (h2 ? x2[1] : x2[0]) + __shfl_xor_sync(full, h2 ? x2[0] : x2[1], 4);
+        x1 += __shfl_xor_sync(full, x1, 2);
+        x1 += __shfl_xor_sync(full, x1, 1);
+        const int slot = (lane >> 2) & 7;
+        if ((lane & 3) == 0) {
+          if (slot < KT) {
+            const int col = w + 32 * slot;
+            ps[col] = (col > j && col < k) ? t * x1 : 0.f;
+          } else if (slot == 7) {
+            wsum[w] = x1;
+          }
+        }
       }
-    });
-  }
+      __syncthreads();
+      // U: rank-2 update of the live tiles; v^T H v from the 32 shares
+      const float vhv = warp_sum(wsum[lane]);
+      const float K = 0.5f * t * t * vhv;   // (tau / 2) v^T p
+      float wr[KT], wc[KT];
+      sfor<KT>([&](auto a) { wr[a] = (a >= S) ? fmaf(-K, vr[a], ps[lane + 32 * a]) : 0.f; });
+      sfor<KT>([&](auto c) { wc[c] = (c >= S) ? fmaf(-K, vc[c], ps[w + 32 * c]) : 0.f; });
+      sfor<KT>([&](auto a) {
+        if (a >= S) {
+          sfor<KT>([&](auto c) {
+            if (c >= S) A[a][c] -= fmaf(vr[a], wc[c], wr[a] * vc[c]);
+          });
+        }
+      });
+    }
+  });
   // trailing 2 x 2 (or 1 x 1) block, written by the owners of its entries
   sfor<KT>([&](auto a) {
     sfor<KT>([&](auto c) {
