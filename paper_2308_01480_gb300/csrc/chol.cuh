@@ -52,23 +52,35 @@ __device__ inline void chol_inv_cta(float* G, int ldg, int b, const float* diag0
 
 
 // Cholesky factorisation and triangular inverse of a b x b Gram, b <= 32,
-// by one warp (the calling warp, all 32 lanes).  Lane l holds column l of
-// the upper triangle of G in a register window that slides down one row per
-// step: at step j, a[s] = G[j + s][l], so the pivot row is always a[0] and
-// every register index is a compile-time constant while the column loop
-// runs at run time (compact code that stays in the instruction cache; the
-// routine runs once per call).  Row j of R travels between lanes by
-// shuffles and is stored to R; then lane l forms column l of T = R^{-1} by
-// back substitution over a window u[s] = T[i + 1 + s][l] that slides up one
-// row per step, reading rows of R as shared-memory broadcasts.  Pivot square
-// roots and reciprocals use the hardware reciprocal square root (a few
-// ulp), which the following Cholesky QR passes absorb.  A pivot below 1e-6
-// of diag0 (or non-positive) raises *flag when report and is replaced by 1.
-// Callers use the out-of-line copy below.
+// by one warp (the calling warp, all 32 lanes; one warp of a CTA at a time,
+// since the routine keeps its rows of R in a static shared array).  Lane l
+// holds column l of the upper triangle of G in a register window that
+// slides down one row per step: at step j, a[s] = G[j + s][l], so the pivot
+// row is always a[0] and every register index is a compile-time constant
+// while the column loop runs at run time (compact code that stays in the
+// instruction cache; the routine runs once per call).  Row j of R goes to
+// R and, shifted so that it starts at R[j][j + 1], to a 16-byte-aligned
+// shared row Rs[j], which every lane then reads back as vector broadcasts
+// (eight loads instead of 31 shuffles).  Lane l then forms column l of
+// T = R^{-1} by back substitution over a window u[s] = T[i + 1 + s][l] that
+// slides up one row per step, reading Rs[i] the same way.  Entries past
+// row b or column b are exact zeros in Rs and in the windows, so the sums
+// run over full vectors without changing a bit of the result.  Pivot
+// square roots and reciprocals use the hardware reciprocal square root (a
+// few ulp), which the following Cholesky QR passes absorb.  A pivot below
+// 1e-6 of diag0 (or non-positive) raises *flag when report and is replaced
+// by 1.  Callers use the out-of-line copy below.
 __device__ __forceinline__ void chol_inv_warp(const float* G, int ldg, int b, const float* diag0, float* R,
                                                    int ldr, float* T, int ldt, int* flag, bool report) {
+  __shared__ __align__(16) float Rs[32][36];   // Rs[j][s] = R[j][j + 1 + s], zero past column b
   const unsigned full = 0xffffffffu;
   const int l = threadIdx.x & 31;
+#pragma unroll
+  for (int q = 0; q < 32; ++q) Rs[q][l] = 0.f;
+  if (l < 4) {
+#pragma unroll
+    for (int q = 0; q < 32; ++q) Rs[q][32 + l] = 0.f;
+  }
   float rinv = 1.f;                       // 1 / R[l][l]
   {
     float a[32];                          // a[s] = G[j + s][l] at step j (rows <= l)
@@ -76,6 +88,7 @@ __device__ __forceinline__ void chol_inv_warp(const float* G, int ldg, int b, co
     for (int i = 0; i < 32; ++i) a[i] = (i <= l && l < b) ? G[i * ldg + l] : 0.f;
     const float d0 = (l < b) ? diag0[l] : 1.f;
     bool bad = false;
+    __syncwarp();
 #pragma unroll 1
     for (int j = 0; j < b; ++j) {
       float djj = __shfl_sync(full, a[0], j);
@@ -88,10 +101,20 @@ __device__ __forceinline__ void chol_inv_warp(const float* G, int ldg, int b, co
       if (l == j) rinv = inv;
       const float rjl = (l == j) ? djj * inv : ((l > j) ? a[0] * inv : 0.f);   // R[j][l]
       if (l < b) R[j * ldr + l] = rjl;
+      if (l > j) Rs[j][l - j - 1] = rjl;
+      __syncwarp();
       // G[j + s][l] -= R[j][j + s] R[j][l], then slide the window down a row
-      // (lanes j + s >= 32 hold rows past b, which are never used)
+      const float4* rv = reinterpret_cast<const float4*>(Rs[j]);
 #pragma unroll
-      for (int s = 1; s < 32; ++s) a[s - 1] = fmaf(-__shfl_sync(full, rjl, (j + s) & 31), rjl, a[s]);
+      for (int q = 0; q < 8; ++q) {
+        const float4 r4 = rv[q];
+        const float rr[4] = {r4.x, r4.y, r4.z, r4.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int s = 4 * q + e + 1;
+          if (s < 32) a[s - 1] = fmaf(-rr[e], rjl, a[s]);
+        }
+      }
       a[31] = 0.f;
     }
     if (report && bad && l == 0) atomicExch(flag, 1);
@@ -104,15 +127,21 @@ __device__ __forceinline__ void chol_inv_warp(const float* G, int ldg, int b, co
 #pragma unroll 1
   for (int i = b - 1; i >= 0; --i) {
     const float ri = __shfl_sync(full, rinv, i);
-    const float* Ri = R + i * ldr + i + 1;   // R[i][i + 1 + s]
-    const int ns = b - 1 - i;                // terms in the sum
+    const float4* rv = reinterpret_cast<const float4*>(Rs[i]);   // R[i][i + 1 + s]
     float s0 = (i == l) ? 1.f : 0.f, s1 = 0.f;
 #pragma unroll
-    for (int s = 0; s < 31; ++s)
-      if (s < ns) {
-        if (s & 1) s1 = fmaf(-Ri[s], u[s], s1);
-        else s0 = fmaf(-Ri[s], u[s], s0);
+    for (int q = 0; q < 8; ++q) {
+      const float4 r4 = rv[q];
+      const float rr[4] = {r4.x, r4.y, r4.z, r4.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int s = 4 * q + e;
+        if (s < 31) {
+          if (s & 1) s1 = fmaf(-rr[e], u[s], s1);
+          else s0 = fmaf(-rr[e], u[s], s0);
+        }
       }
+    }
     const float ti = (i <= l && l < b) ? (s0 + s1) * ri : 0.f;
 #pragma unroll
     for (int s = 31; s > 0; --s) u[s] = u[s - 1];

@@ -593,7 +593,9 @@ static int er_kt(int k) { return (k + 31) / 32; }
 
 bool eig_reg_ok(int k, int r) {
   if (k < 1 || r < 1 || r > 32 || r > k || k > 32 * ER_KTMAX) return false;
-  return er_smem_floats(32 * er_kt(k), k, r) * 4 <= 227 * 1024;
+  // dynamic shared memory plus the kernel's static arrays (the Cholesky's
+  // 4.5 KB of R rows) within the 227 KB a CTA may use
+  return er_smem_floats(32 * er_kt(k), k, r) * 4 + 6 * 1024 <= 227 * 1024;
 }
 
 template <int KT>

@@ -172,15 +172,25 @@ __global__ void __launch_bounds__(OC_THREADS, 1) k_orth_cluster(ClusterOrthArgs 
   float* Qc = Zn + rp * bp;
   const bool report = rank == 0;
 
-  // zero-padded copies of the CTA's rows of Q and W; zero T and P
-  for (int x = tid; x < rp * kp; x += blockDim.x) {
-    const int i = x / kp, t = x % kp;
-    Qc[x] = (i < rc && t < kq) ? a.Q[(r0 + i) * a.ldq + t] : 0.f;
-  }
-  for (int x = tid; x < rp * bp; x += blockDim.x) {
-    const int i = x / bp, j = x % bp;
-    Zc[x] = (i < rc && j < b) ? a.W[(r0 + i) * a.ldw + j] : 0.f;
-    Zn[x] = 0.f;
+  // zero-padded copies of the CTA's rows of Q and W (a warp per row, lanes
+  // along the row, four rows in flight per warp); zero T and P
+  {
+    const int lane = tid & 31, nw = blockDim.x >> 5;
+    for (int i0 = tid >> 5; i0 < rp; i0 += 4 * nw) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = i0 + u * nw;
+        if (i < rp) {
+          const float* qrow = a.Q + (r0 + i) * a.ldq;
+          const float* wrow = a.W + (r0 + i) * a.ldw;
+          for (int t = lane; t < kp; t += 32) Qc[i * kp + t] = (i < rc && t < kq) ? qrow[t] : 0.f;
+          for (int j = lane; j < bp; j += 32) {
+            Zc[i * bp + j] = (i < rc && j < b) ? wrow[j] : 0.f;
+            Zn[i * bp + j] = 0.f;
+          }
+        }
+      }
+    }
   }
   for (int x = tid; x < bp * bp; x += blockDim.x) T[x] = 0.f;
   for (int x = tid; x < kp * bp; x += blockDim.x) P[x] = 0.f;
