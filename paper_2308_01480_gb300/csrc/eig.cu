@@ -19,52 +19,48 @@ constexpr int EIG_THREADS = 1024;
 constexpr int EIG_KMAX = 224;   // H (k x (k+1) floats) must fit shared memory
 
 // ------------------------------------------------------------ partial A^T B
-// P[cta][s][t] = sum_{i in rows of cta} A[i][s] B[i][t], s < ka, t < kb.
-__global__ void __launch_bounds__(256) k_tn_partials(const float* __restrict__ A, int64_t lda, int ka,
-                                                     const float* __restrict__ B, int64_t ldb, int kb,
-                                                     int64_t m, int64_t rows_per_cta, float* __restrict__ P) {
-  constexpr int RC = 16;
-  extern __shared__ float sm[];
-  float* As = sm;                  // [RC][ka]
-  float* Bs = As + RC * ka;        // [RC][kb]
-  const int64_t r0 = (int64_t)blockIdx.x * rows_per_cta;
-  const int64_t r1 = imin(m, r0 + rows_per_cta);
-  const int E = ka * kb;
-  float* out = P + (int64_t)blockIdx.x * E;
-  // each thread owns outputs e = e0 + tid + 256 u, u < 16
-  for (int e0 = 0; e0 < E; e0 += 256 * 16) {
-    float a[16];
-#pragma unroll
-    for (int u = 0; u < 16; ++u) a[u] = 0.f;
-    for (int64_t i0 = r0; i0 < r1; i0 += RC) {
-      const int rc = (int)imin(RC, r1 - i0);
-      __syncthreads();
-      for (int x = threadIdx.x; x < RC * ka; x += 256) {
-        int r = x / ka, s = x % ka;
-        As[x] = r < rc ? A[(i0 + r) * lda + s] : 0.f;
-      }
-      for (int x = threadIdx.x; x < RC * kb; x += 256) {
-        int r = x / kb, t = x % kb;
-        Bs[x] = r < rc ? B[(i0 + r) * ldb + t] : 0.f;
-      }
-      __syncthreads();
-#pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const int e = e0 + threadIdx.x + 256 * u;
-        if (e < E) {
-          const int s = e / kb, t = e % kb;
-          float v = a[u];
-          for (int r = 0; r < RC; ++r) v = fmaf(As[r * ka + s], Bs[r * kb + t], v);
-          a[u] = v;
-        }
-      }
+// P[y][s][t] = sum_{i in row range y} A[i][s] B[i][t] for the 32 x 32 output
+// tile blockIdx.x (s < ka, t < kb); 64 threads, each with a 4 x 4 register
+// tile fed by two float4 shared-memory broadcasts per row.
+__global__ void __launch_bounds__(64) k_tn_partials(const float* __restrict__ A, int64_t lda, int ka,
+                                                    const float* __restrict__ B, int64_t ldb, int kb, int64_t m,
+                                                    int64_t rows_per_split, float* __restrict__ P) {
+  __shared__ __align__(16) float As[32][32];
+  __shared__ __align__(16) float Bs[32][32];
+  const int tiles_t = (kb + 31) / 32;
+  const int s0 = (int)(blockIdx.x / tiles_t) * 32, t0 = (int)(blockIdx.x % tiles_t) * 32;
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per_split, r1 = imin(m, r0 + rows_per_split);
+  const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
+  float acc[4][4] = {};
+  for (int64_t i0 = r0; i0 < r1; i0 += 32) {
+    __syncthreads();
+#pragma unroll 4
+    for (int x = threadIdx.x; x < 32 * 32; x += 64) {
+      const int r = x >> 5, c = x & 31;
+      const int64_t i = i0 + r;
+      As[r][c] = (i < r1 && s0 + c < ka) ? A[i * lda + s0 + c] : 0.f;
+      Bs[r][c] = (i < r1 && t0 + c < kb) ? B[i * ldb + t0 + c] : 0.f;
     }
+    __syncthreads();
+#pragma unroll 8
+    for (int r = 0; r < 32; ++r) {
+      const float4 a4 = *reinterpret_cast<const float4*>(&As[r][4 * ty]);
+      const float4 b4 = *reinterpret_cast<const float4*>(&Bs[r][4 * tx]);
+      const float av[4] = {a4.x, a4.y, a4.z, a4.w}, bv[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
-    for (int u = 0; u < 16; ++u) {
-      const int e = e0 + threadIdx.x + 256 * u;
-      if (e < E) out[e] = a[u];
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) acc[u][w] = fmaf(av[u], bv[w], acc[u][w]);
     }
   }
+  float* out = P + (int64_t)blockIdx.y * ka * kb;
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      const int sidx = s0 + 4 * ty + u, tidx = t0 + 4 * tx + w;
+      if (sidx < ka && tidx < kb) out[(int64_t)sidx * kb + tidx] = acc[u][w];
+    }
 }
 
 // out[e] = sum_{c < nparts} P[c][e] (fixed order)
@@ -458,10 +454,11 @@ cudaError_t launch_eig_top(const float* H, int64_t ldh, int k, int r, float* V, 
   return cudaGetLastError();
 }
 
-static int rows_split(int64_t m, int64_t* rows_per_cta) {
-  int64_t ctas = imin(ceil_div(m, 16), 128);
-  *rows_per_cta = ceil_div(m, ctas);
-  return (int)ceil_div(m, *rows_per_cta);
+// Row ranges of the partial products: about 96 rows each, at most 16.
+static int rows_split(int64_t m, int64_t* rows_per_split) {
+  const int64_t splits = imax(1, imin(ceil_div(m, 96), 16));
+  *rows_per_split = ceil_div(m, splits);
+  return (int)ceil_div(m, *rows_per_split);
 }
 
 size_t tn_parts_floats(int64_t m, int ka, int kb) {
@@ -471,18 +468,17 @@ size_t tn_parts_floats(int64_t m, int ka, int kb) {
 
 cudaError_t launch_tn(const float* A, int64_t lda, int ka, const float* B, int64_t ldb, int kb, int64_t m,
                       float* parts, float* out, cudaStream_t st) {
-  int64_t rpc;
-  const int ctas = rows_split(m, &rpc);
-  const size_t smem = sizeof(float) * 16 * (size_t)(ka + kb);
-  raise_smem_limit(k_tn_partials);
+  int64_t rps;
+  const int splits = rows_split(m, &rps);
+  const dim3 grid((unsigned)(ceil_div(ka, 32) * ceil_div(kb, 32)), (unsigned)splits);
   {
     ProfScope prof("tn_small", st, 0, 2.0 * m * ka * kb);
     note_launch("tn_small");
-    k_tn_partials<<<ctas, 256, smem, st>>>(A, lda, ka, B, ldb, kb, m, rpc, parts);
+    k_tn_partials<<<grid, 64, 0, st>>>(A, lda, ka, B, ldb, kb, m, rps, parts);
   }
   const int64_t E = (int64_t)ka * kb;
   note_launch("sum_parts");
-  k_sum_parts<<<(int)imin(ceil_div(E, 256), 256), 256, 0, st>>>(parts, ctas, E, out);
+  k_sum_parts<<<(int)imin(ceil_div(E, 256), 256), 256, 0, st>>>(parts, splits, E, out);
   return cudaGetLastError();
 }
 

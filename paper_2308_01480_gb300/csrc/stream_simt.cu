@@ -273,13 +273,25 @@ __global__ void __launch_bounds__(256) k_gram(const TIn* __restrict__ C, int64_t
 
 // ---------------------------------------------------------------- reduce
 // out[r * ldo + c] = sum_{s < S} P[s][r][c] (fixed order), r < rows, c < cols.
+// Sum of n values at p[0], p[stride], ..., in eight interleaved partial
+// sums (eight loads in flight), combined in a fixed order.
+__device__ __forceinline__ float strided_sum(const float* __restrict__ p, int n, int64_t stride) {
+  float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  int k = 0;
+  for (; k + 8 <= n; k += 8) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) a[u] += p[(int64_t)(k + u) * stride];
+  }
+  for (; k < n; ++k) a[0] += p[(int64_t)k * stride];
+  return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+}
+
 __global__ void k_reduce_partials(const float* __restrict__ P, int S, int64_t rows, int cols,
                                   float* __restrict__ out, int64_t ldo) {
   const int64_t E = rows * cols;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
        e += (int64_t)gridDim.x * blockDim.x) {
-    float s = 0.f;
-    for (int k = 0; k < S; ++k) s += P[(int64_t)k * E + e];
+    const float s = strided_sum(P + e, S, E);
     int64_t r = e / cols;
     int c = (int)(e % cols);
     out[r * ldo + c] = s;
@@ -296,8 +308,7 @@ __global__ void k_reduce_grouped(const float* __restrict__ P, int per, int group
     const int64_t r = e / cols;
     const int c = (int)(e % cols);
     const int g = (int)(r / group_rows);
-    float s = 0.f;
-    for (int j = 0; j < per; ++j) s += P[(int64_t)(j * groups + g) * E + e];
+    const float s = strided_sum(P + (int64_t)g * E + e, per, (int64_t)groups * E);
     out[r * ldo + c] = s;
   }
 }
