@@ -38,6 +38,7 @@ struct ModePlan {
   std::vector<int> blocks;   // columns of X_0, X_1, ... (Krylov dimension cap applied)
   int iters = 0;             // subspace iteration: powers applied to the single block
   bool gram_route = false;   // exhaustion with D == m: one Gram pass
+  bool gram_cols = false;    // exhaustion with D == n < m: the n x n Gram C^T C
   bool fused_ga = false;     // Gram-apply fused in one pass over C
 };
 
@@ -133,8 +134,11 @@ tt_status build_plan(const int64_t* dims, int d, const int64_t* ranks, int p, in
     }
     M.kq = (int)cols;
     M.gram_route = P.o.exhaust_gram && cols == M.D && M.D == M.m && M.m <= 128;
+    M.gram_cols = P.o.exhaust_gram && !M.gram_route && cols == M.D && M.D == M.n && M.n < M.m &&
+                  ttr::eig_top_ok((int)M.n);
     M.fused_ga = ttr::simt_ga_fused_ok(M.m, M.b);
-    if (!M.gram_route && M.kq > 256) return fail(TT_EUNSUPPORTED, "Krylov basis larger than 256 columns");
+    if (!M.gram_route && !M.gram_cols && M.kq > 256)
+      return fail(TT_EUNSUPPORTED, "Krylov basis larger than 256 columns");
     // sizes
     maxR = std::max(maxR, (size_t)(M.r_out * M.n) * esize(P.remainder));
     if (M.gram_route) {
@@ -142,6 +146,11 @@ tt_status build_plan(const int64_t* dims, int d, const int64_t* ranks, int p, in
       maxG = std::max(maxG, (size_t)(M.m * M.m));
       maxSmall = std::max(maxSmall, ttr::rr_scratch_floats((int)M.m));
       maxSmall = std::max(maxSmall, ttr::rr_fast_scratch_floats(M.m, (int)M.m, M.r_out));
+    } else if (M.gram_cols) {
+      maxY = std::max(maxY, (size_t)(M.m * M.r_out));
+      maxSmall = std::max(maxSmall, ttr::colgram_scratch_floats(M.m, (int)M.n, M.r_out));
+      maxSmall = std::max(maxSmall, ttr::orth_scratch_floats(M.m, M.r_out, M.r_out));
+      maxSmall = std::max(maxSmall, ttr::orth_fast_scratch_floats(M.m, 0, M.r_out));
     } else {
       maxS = std::max(maxS, (size_t)(M.b * M.n));
       maxPart = std::max(maxPart, (size_t)ttr::simt_cs_partials(M.m, M.n, M.b));
@@ -167,7 +176,7 @@ tt_status build_plan(const int64_t* dims, int d, const int64_t* ranks, int p, in
       maxX = std::max(maxX, ttr::tc_proj_scratch_bytes(M.m, M.b, 0));
       maxX = std::max(maxX, ttr::tc_proj_scratch_bytes(M.m, M.r_out, 1));
       maxX = std::max(maxX, ttr::tc_ga_scratch_bytes(M.m, M.b));
-      if (!M.gram_route) maxT = std::max(maxT, (size_t)(M.b * M.n));
+      if (!M.gram_route && !M.gram_cols) maxT = std::max(maxT, (size_t)(M.b * M.n));
     }
   }
   size_t off = 0;
@@ -211,6 +220,27 @@ tt_status run_mode(const Plan& P, int k, const TIn* C, char* ws, int* status, co
       TTR_CUDA(ttr::launch_rr_fast(nullptr, G, M.m, M.m, (int)M.m, r, 1, small, U, core, st));
     else
       TTR_CUDA(ttr::launch_rayleigh_ritz(nullptr, G, M.m, M.m, (int)M.m, r, 1, small, U, core, st));
+  } else if (M.gram_cols) {
+    // exhaustion with D = n < m: the Krylov basis would span range(C), so
+    // Rayleigh-Ritz would return the exact top-r left singular vectors;
+    // they are orth(C V'), V' the top-r eigenvectors of the n x n Gram
+    // C^T C (orthonormalising C v'_1, C v'_2, ... in order recovers
+    // u_1, u_2, ... since C v'_j = sigma_j u_j)
+    float* Y = (float*)(ws + P.off_Y);
+    int* flag = status + 1;
+    unsigned* ticket = reinterpret_cast<unsigned*>(status + 2);
+    const uint64_t rseed = 0x5EEDull * (uint64_t)(k + 1);
+    TTR_CUDA(ttr::launch_colgram<TIn>(C, M.m, (int)M.n, r, small, Y, st));
+    if (ttr::orth_cluster_ok(M.m, 0, r)) {
+      TTR_CUDA(ttr::launch_orth_cluster(Y, r, M.m, r, r, U, r, 0, flag, st));
+      TTR_CUDA(ttr::launch_orth_block(Y, r, M.m, r, U, r, 0, r, small, rseed, status, flag, st));
+    } else if (ttr::orth_fast_ok(M.m, 0, r)) {
+      TTR_CUDA(ttr::launch_orth_fast(Y, r, M.m, r, U, r, 0, small, ticket, flag, st));
+      TTR_CUDA(ttr::launch_orth_block(Y, r, M.m, r, U, r, 0, r, small, rseed, status, flag, st));
+    } else {
+      TTR_CUDA(ttr::launch_orth_block(Y, r, M.m, r, U, r, 0, r, small, rseed, status, nullptr, st));
+    }
+    TTR_CUDA(cudaMemcpyAsync(core, U, sizeof(float) * (size_t)M.m * r, cudaMemcpyDeviceToDevice, st));
   } else {
     float* S = (float*)(ws + P.off_S);
     float* T = (float*)(ws + P.off_T);
@@ -318,7 +348,8 @@ tt_status check_problem(const Plan& P, const void* tensor, const float* const* o
     if (!cores_out[k]) return fail(TT_EINVAL, "cores_out[k] is NULL");
   if (omegas)
     for (int k = 0; k < P.d - 1; ++k)
-      if (!omegas[k] && !P.modes[k].gram_route) return fail(TT_EINVAL, "omegas[k] is NULL");
+      if (!omegas[k] && !P.modes[k].gram_route && !P.modes[k].gram_cols)
+        return fail(TT_EINVAL, "omegas[k] is NULL");
   return TT_OK;
 }
 
@@ -403,9 +434,10 @@ double plan_cost(const Plan& P) {
   for (int k = 0; k < P.d - 1; ++k) {
     const ModePlan& M = P.modes[k];
     const double e = (double)esize(k == 0 ? P.storage : P.remainder);
-    const double passes = M.gram_route ? 2.0 : 2.0 + 2.0 * (double)M.blocks.size();
+    const bool gram = M.gram_route || M.gram_cols;
+    const double passes = gram ? 2.0 : 2.0 + 2.0 * (double)M.blocks.size();
     us += passes * (double)M.m * (double)M.n * e / 1.0e6;
-    us += M.gram_route ? 60.0 : 50.0 * (double)M.blocks.size() + 30.0 + 0.02 * (double)M.kq * M.kq;
+    us += M.gram_route ? 60.0 : M.gram_cols ? 110.0 : 50.0 * (double)M.blocks.size() + 30.0 + 0.02 * (double)M.kq * M.kq;
   }
   return us + 10.0;
 }

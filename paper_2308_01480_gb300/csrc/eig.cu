@@ -22,8 +22,9 @@ constexpr int EIG_KMAX = 224;   // H (k x (k+1) floats) must fit shared memory
 // P[y][s][t] = sum_{i in row range y} A[i][s] B[i][t] for the 32 x 32 output
 // tile blockIdx.x (s < ka, t < kb); 64 threads, each with a 4 x 4 register
 // tile fed by two float4 shared-memory broadcasts per row.
-__global__ void __launch_bounds__(64) k_tn_partials(const float* __restrict__ A, int64_t lda, int ka,
-                                                    const float* __restrict__ B, int64_t ldb, int kb, int64_t m,
+template <typename TA, typename TB>
+__global__ void __launch_bounds__(64) k_tn_partials(const TA* __restrict__ A, int64_t lda, int ka,
+                                                    const TB* __restrict__ B, int64_t ldb, int kb, int64_t m,
                                                     int64_t rows_per_split, float* __restrict__ P) {
   __shared__ __align__(16) float As[32][32];
   __shared__ __align__(16) float Bs[32][32];
@@ -38,8 +39,8 @@ __global__ void __launch_bounds__(64) k_tn_partials(const float* __restrict__ A,
     for (int x = threadIdx.x; x < 32 * 32; x += 64) {
       const int r = x >> 5, c = x & 31;
       const int64_t i = i0 + r;
-      As[r][c] = (i < r1 && s0 + c < ka) ? A[i * lda + s0 + c] : 0.f;
-      Bs[r][c] = (i < r1 && t0 + c < kb) ? B[i * ldb + t0 + c] : 0.f;
+      As[r][c] = (i < r1 && s0 + c < ka) ? ld_elem(A, i * lda + s0 + c) : 0.f;
+      Bs[r][c] = (i < r1 && t0 + c < kb) ? ld_elem(B, i * ldb + t0 + c) : 0.f;
     }
     __syncthreads();
 #pragma unroll 8
@@ -412,7 +413,8 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eig_top(const float* __restrict
 }
 
 // U (m x r) = Q (m x k, ld ldq) V (k x r); also written to core (same layout).
-__global__ void __launch_bounds__(256) k_apply_basis(const float* __restrict__ Q, int64_t ldq, int64_t m, int k,
+template <typename TQ>
+__global__ void __launch_bounds__(256) k_apply_basis(const TQ* __restrict__ Q, int64_t ldq, int64_t m, int k,
                                                      const float* __restrict__ V, int r, float* __restrict__ U,
                                                      float* __restrict__ core, int64_t rows_per_cta) {
   extern __shared__ float sm[];
@@ -424,9 +426,9 @@ __global__ void __launch_bounds__(256) k_apply_basis(const float* __restrict__ Q
   for (int64_t x = threadIdx.x; x < (r1 - r0) * r; x += blockDim.x) {
     const int64_t i = r0 + x / r;
     const int j = (int)(x % r);
-    const float* qi = Q + i * ldq;
+    const TQ* qi = Q + i * ldq;
     float s = 0.f;
-    for (int t = 0; t < k; ++t) s = fmaf(qi[t], Vs[t * r + j], s);
+    for (int t = 0; t < k; ++t) s = fmaf(ld_elem(qi, t), Vs[t * r + j], s);
     U[i * r + j] = s;
     if (core) core[i * r + j] = s;
   }
@@ -466,15 +468,16 @@ size_t tn_parts_floats(int64_t m, int ka, int kb) {
   return (size_t)rows_split(m, &rpc) * ka * kb;
 }
 
-cudaError_t launch_tn(const float* A, int64_t lda, int ka, const float* B, int64_t ldb, int kb, int64_t m,
-                      float* parts, float* out, cudaStream_t st) {
+template <typename TA, typename TB>
+static cudaError_t launch_tn(const TA* A, int64_t lda, int ka, const TB* B, int64_t ldb, int kb, int64_t m,
+                             float* parts, float* out, cudaStream_t st) {
   int64_t rps;
   const int splits = rows_split(m, &rps);
   const dim3 grid((unsigned)(ceil_div(ka, 32) * ceil_div(kb, 32)), (unsigned)splits);
   {
     ProfScope prof("tn_small", st, 0, 2.0 * m * ka * kb);
     note_launch("tn_small");
-    k_tn_partials<<<grid, 64, 0, st>>>(A, lda, ka, B, ldb, kb, m, rps, parts);
+    k_tn_partials<TA, TB><<<grid, 64, 0, st>>>(A, lda, ka, B, ldb, kb, m, rps, parts);
   }
   const int64_t E = (int64_t)ka * kb;
   note_launch("sum_parts");
@@ -482,16 +485,22 @@ cudaError_t launch_tn(const float* A, int64_t lda, int ka, const float* B, int64
   return cudaGetLastError();
 }
 
-cudaError_t launch_apply_basis(const float* Q, int64_t ldq, int64_t m, int k, const float* V, int r, float* U,
-                               float* core, cudaStream_t st) {
+template <typename TQ>
+static cudaError_t apply_basis_t(const TQ* Q, int64_t ldq, int64_t m, int k, const float* V, int r, float* U,
+                                 float* core, cudaStream_t st) {
   int64_t rpc = 8;
   const int ctas = (int)ceil_div(m, rpc);
   const size_t smem = sizeof(float) * (size_t)k * r;
-  raise_smem_limit(k_apply_basis);
+  raise_smem_limit(k_apply_basis<TQ>);
   ProfScope prof("apply_basis", st, 0, 2.0 * m * k * r);
   note_launch("apply_basis");
-  k_apply_basis<<<ctas, 256, smem, st>>>(Q, ldq, m, k, V, r, U, core, rpc);
+  k_apply_basis<TQ><<<ctas, 256, smem, st>>>(Q, ldq, m, k, V, r, U, core, rpc);
   return cudaGetLastError();
+}
+
+cudaError_t launch_apply_basis(const float* Q, int64_t ldq, int64_t m, int k, const float* V, int r, float* U,
+                               float* core, cudaStream_t st) {
+  return apply_basis_t(Q, ldq, m, k, V, r, U, core, st);
 }
 
 // Rayleigh-Ritz: H = Q^T W (or H = G when Q is the identity), top-r
@@ -529,5 +538,30 @@ cudaError_t launch_rr_fast(const float* Q, const float* W, int64_t ld, int64_t m
   }
   return launch_apply_basis(Q, ld, m, k, V, r, U, core, st);
 }
+
+// Exhaustion with D = n < m (the Krylov basis would span range(C)): the
+// top-r right singular vectors V' of C from its n x n Gram C^T C, and
+// Y = C V' (m x r), whose orthonormalisation (left to the caller) gives
+// the top-r left singular vectors.
+size_t colgram_scratch_floats(int64_t m, int n, int r) {
+  return tn_parts_floats(m, n, n) + (size_t)n * n + (size_t)n * r + eig_scratch_floats(n, r);
+}
+
+template <typename T>
+cudaError_t launch_colgram(const T* C, int64_t m, int n, int r, float* scratch, float* Y, cudaStream_t st) {
+  float* parts = scratch;
+  float* G = parts + tn_parts_floats(m, n, n);
+  float* V = G + (size_t)n * n;
+  float* es = V + (size_t)n * r;
+  cudaError_t e = launch_tn(C, n, n, C, n, n, m, parts, G, st);
+  if (e != cudaSuccess) return e;
+  e = launch_eig_top(G, n, n, r, V, es, nullptr, st);
+  if (e != cudaSuccess) return e;
+  return apply_basis_t(C, n, m, n, V, r, Y, nullptr, st);
+}
+
+template cudaError_t launch_colgram<float>(const float*, int64_t, int, int, float*, float*, cudaStream_t);
+template cudaError_t launch_colgram<__nv_bfloat16>(const __nv_bfloat16*, int64_t, int, int, float*, float*,
+                                                   cudaStream_t);
 
 }  // namespace ttr

@@ -107,6 +107,11 @@ cudaError_t launch_eig_top(const float* H, int64_t ldh, int k, int r, float* V, 
 cudaError_t launch_rr_fast(const float* Q, const float* W, int64_t ld, int64_t m, int k, int r, int identity_q,
                            float* scratch, float* U, float* core, cudaStream_t st);
 size_t rr_scratch_floats(int k);
+// exhaustion with D = n < m: Y = C V' (m x r), V' the top-r eigenvectors of
+// C^T C (n x n, n <= 224); scratch: colgram_scratch_floats(m, n, r)
+size_t colgram_scratch_floats(int64_t m, int n, int r);
+template <typename T>
+cudaError_t launch_colgram(const T* C, int64_t m, int n, int r, float* scratch, float* Y, cudaStream_t st);
 cudaError_t launch_rayleigh_ritz(const float* Q, const float* W, int64_t ld, int64_t m, int k, int r,
                                  int identity_q, float* scratch, float* U, float* core, cudaStream_t st);
 cudaError_t launch_last_core(const void* R, int dtype, int64_t count, float* core, int* status, cudaStream_t st);
