@@ -284,6 +284,20 @@ def run_ours(args):
         methods[name] = {"ms_per_step": msm / fp32_steps, "q": qm}
         cores_m[name] = pm.cores
 
+    # ---- TT-SVD (Alg. 1), the deterministic baseline, at the same ranks
+    # (eps = 0 with the target ranks as caps); host-synchronous per mode
+    svd_ws = {}
+
+    def step_svd():
+        c, _ = tt.tt_svd(Abf, eps=0.0, max_ranks=ranks, workspace=svd_ws.get("ws"))
+        cores_m["tt_svd"] = c
+
+    step_svd()
+    svd_steps = 3
+    mss = time_steps(step_svd, svd_steps, 1, barrier_sync)
+    methods["tt_svd"] = {"ms_per_step": mss / svd_steps, "q": None,
+                         "note": "Gram GEMM + cuSOLVER syevd per mode, ranks capped at the targets"}
+
     # ---- accuracy against the float64 tensor
     A64 = torch.from_numpy(A).to(dev)
     eps_bf = rel_error_dev(A64, cores_bf)

@@ -308,6 +308,44 @@ TT_API tt_status tt_sym_eig_top(const float* H, int64_t ldh, int k, int r, float
                                 void* workspace, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------------
+ * TT-SVD (Alg. 1, Sec. 2.2): the deterministic baseline, sequential
+ * truncated SVDs of the unfoldings with prescribed accuracy.
+ *
+ * delta = eps * ||A||_F / sqrt(d - 1) (Alg. 1 step 1).  At mode k the
+ * unfolding C (m = r_{k-1} I_k rows, n = I_{k+1} ... I_d columns) has the
+ * Gram G = C C^T, whose eigenvalues are the squared singular values of C;
+ * r_k is the smallest rank whose discarded tail sum_{i > r_k} lambda_i is
+ * at most delta^2 (Alg. 1 step 4), capped by max_ranks[k] and min(m, n);
+ * core k is the top r_k eigenvectors of G (the left singular vectors), and
+ * the next remainder is U^T C = S V^T (Alg. 1 step 6).  ||A||_F^2 is the
+ * trace of the first Gram.  eps = 0 with max_ranks gives the fixed-rank
+ * form.
+ *
+ *   tensor    device, row-major (i_1 slowest), dtype storage (TT_F32 or
+ *             TT_BF16); remainders are FP32.
+ *   dims, d   mode sizes, d >= 2.
+ *   eps       >= 0.
+ *   max_ranks host, d - 1 rank caps >= 1, or NULL for none (min(m, n)).
+ *   cores_out d device FP32 buffers, core k sized for the clamped caps
+ *             (tt_svd_workspace_size reports them through core_elems);
+ *             written as [r_{k-1}][I_k][r_k] with the chosen ranks.
+ *   ranks_out host, d + 1 chosen ranks (r_0 = r_d = 1).
+ * Host-synchronous: the call waits on `stream` once per mode to read the
+ * eigenvalues back and returns when the cores are written; it cannot be
+ * captured in a CUDA graph.  The Gram matrices and the projections are
+ * cuBLAS GEMMs (FP32 accumulation; a BF16 tensor's projection applies U as
+ * BF16 hi + lo parts), the eigendecompositions cuSOLVER's syevd in FP32;
+ * one cuBLAS and one cuSOLVER handle per host thread and device are
+ * created on first use.  Errors: TT_EINVAL, TT_EUNSUPPORTED (a Gram larger
+ * than 16384 x 16384), TT_ECUDA.
+ * ---------------------------------------------------------------------- */
+TT_API tt_status tt_svd_workspace_size(const int64_t* dims, int d, const int64_t* max_ranks, int storage,
+                                       int64_t* core_elems, size_t* bytes);
+TT_API tt_status tt_svd_decompose(const void* tensor, int storage, const int64_t* dims, int d, double eps,
+                                  const int64_t* max_ranks, float* const* cores_out, int64_t* ranks_out,
+                                  void* workspace, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------
  * Allocation-free Gram-apply.  The paper has no counterpart: this entry
  * point exists for deployment, not for the method.
  *

@@ -11,7 +11,7 @@ from . import _native as N
 from ._native import (TT_BF16, TT_F32, TT_METHOD_RBKI, TT_METHOD_RSI, TT_PASS_GRAM,  # noqa: F401
                       TT_PASS_GRAMAPPLY, TT_PASS_PROJECT, TT_PASS_SKETCH, TTError)
 
-__all__ = ["decompose", "workspace_size", "core_sizes", "omega_generate", "permute_convert",
+__all__ = ["decompose", "tt_svd", "workspace_size", "core_sizes", "omega_generate", "permute_convert",
            "tt_pass", "device_status", "options", "profile_begin", "profile_end", "TTError", "TT_F32",
            "TT_BF16", "Problem", "batched_workspace_size", "decompose_batched", "batched_device_status",
            "BatchGraph"]
@@ -285,6 +285,34 @@ def _batch_ws(problems, opts, workspace):
         dev = problems[0].tensor.device if problems else torch.device("cuda")
         workspace = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
     return workspace
+
+
+def tt_svd(tensor, eps=0.0, max_ranks=None, workspace=None, stream=None):
+    """TT-SVD (Alg. 1) of a dense row-major CUDA tensor (float32 or
+    bfloat16) with accuracy eps and optional rank caps (tt_svd_decompose).
+    Host-synchronous.  Returns (cores, ranks): float32 CUDA tensors of shape
+    (r_{k-1}, I_k, r_k) with the chosen ranks, and the ranks r_0 .. r_d."""
+    torch = _torch()
+    if not tensor.is_cuda or not tensor.is_contiguous():
+        raise ValueError("tensor must be a contiguous CUDA tensor")
+    dims = list(tensor.shape)
+    d = len(dims)
+    storage = _dtype_code(tensor)
+    caps = N.i64_array(max_ranks) if max_ranks is not None else None
+    elems = (ctypes.c_int64 * d)()
+    nbytes = ctypes.c_size_t()
+    N.check(N.lib().tt_svd_workspace_size(N.i64_array(dims), d, caps, storage, elems, ctypes.byref(nbytes)))
+    if workspace is None or workspace.numel() < nbytes.value:
+        workspace = torch.empty(nbytes.value, dtype=torch.uint8, device=tensor.device)
+    bufs = [torch.empty(int(elems[k]), dtype=torch.float32, device=tensor.device) for k in range(d)]
+    ranks_out = (ctypes.c_int64 * (d + 1))()
+    N.check(N.lib().tt_svd_decompose(ctypes.c_void_p(tensor.data_ptr()), storage, N.i64_array(dims), d,
+                                     float(eps), caps, N.ptr_array([b.data_ptr() for b in bufs]), ranks_out,
+                                     ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
+                                     _stream_handle(stream)))
+    rr = [int(ranks_out[k]) for k in range(d + 1)]
+    cores = [bufs[k][:rr[k] * dims[k] * rr[k + 1]].view(rr[k], dims[k], rr[k + 1]) for k in range(d)]
+    return cores, rr
 
 
 def decompose_batched(problems, opts, workspace=None, stream=None):

@@ -72,6 +72,10 @@ _SIGNATURES = {
     "tt_rbki_graph_launch": ([_vp, _vp], ctypes.c_int),
     "tt_rbki_graph_destroy": ([_vp], ctypes.c_int),
     "tt_rbki_last_error": ([], ctypes.c_char_p),
+    "tt_svd_workspace_size": ([_i64p, ctypes.c_int, _i64p, ctypes.c_int, _i64p, ctypes.POINTER(ctypes.c_size_t)],
+                              ctypes.c_int),
+    "tt_svd_decompose": ([_vp, ctypes.c_int, _i64p, ctypes.c_int, ctypes.c_double, _i64p, _vpp, _i64p, _vp,
+                          ctypes.c_size_t, _vp], ctypes.c_int),
     "tt_permute_convert": ([_vp, ctypes.c_int, _i64p, _i64p, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                             _vp, ctypes.c_int, _vp], ctypes.c_int),
     "tt_omega_generate": ([ctypes.c_uint64, ctypes.c_int, ctypes.c_int64, ctypes.c_int, _vp, ctypes.c_int,

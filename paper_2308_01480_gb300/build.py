@@ -50,7 +50,8 @@ def build(verbose=False, extra=()):
             if log:
                 print(log)
     tmp = LIB + ".tmp"
-    cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs
+    # cuBLAS and cuSOLVER serve only the TT-SVD baseline (tt_svd.cu)
+    cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcublas", "-lcusolver"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
