@@ -322,7 +322,7 @@ TT_API tt_status tt_sym_eig_top(const float* H, int64_t ldh, int k, int r, float
  * form.
  *
  *   tensor    device, row-major (i_1 slowest), dtype storage (TT_F32 or
- *             TT_BF16); remainders are FP32.
+ *             TT_BF16); converted to FP64 once, remainders are FP64.
  *   dims, d   mode sizes, d >= 2.
  *   eps       >= 0.
  *   max_ranks host, d - 1 rank caps >= 1, or NULL for none (min(m, n)).
@@ -333,11 +333,13 @@ TT_API tt_status tt_sym_eig_top(const float* H, int64_t ldh, int k, int r, float
  * Host-synchronous: the call waits on `stream` once per mode to read the
  * eigenvalues back and returns when the cores are written; it cannot be
  * captured in a CUDA graph.  The Gram matrices and the projections are
- * cuBLAS GEMMs (FP32 accumulation; a BF16 tensor's projection applies U as
- * BF16 hi + lo parts), the eigendecompositions cuSOLVER's syevd in FP32;
- * one cuBLAS and one cuSOLVER handle per host thread and device are
- * created on first use.  Errors: TT_EINVAL, TT_EUNSUPPORTED (a Gram larger
- * than 16384 x 16384), TT_ECUDA.
+ * cuBLAS DGEMMs and the eigendecompositions cuSOLVER's Dsyevd, in FP64
+ * (the Gram squares the singular values, which FP32 could not resolve for
+ * fast-decaying spectra); cores are returned in FP32.  The workspace holds
+ * the FP64 copy of the tensor.  One cuBLAS and one cuSOLVER handle per
+ * host thread and device are created on first use.  Errors: TT_EINVAL,
+ * TT_ENOMEM (workspace too small), TT_EUNSUPPORTED (a Gram larger than
+ * 16384 x 16384, more than 2^31 - 1 columns), TT_ECUDA.
  * ---------------------------------------------------------------------- */
 TT_API tt_status tt_svd_workspace_size(const int64_t* dims, int d, const int64_t* max_ranks, int storage,
                                        int64_t* core_elems, size_t* bytes);

@@ -11,7 +11,8 @@ Modules
 tt_oracle   TT-SVD (Alg. 1), TT-rBKI (Alg. 3, left block Krylov reading with
             Rayleigh-Ritz truncation; q = 0 is TT-rSVD, Alg. 2), TT-rSI
             (Alg. 4, subspace iteration), Krylov-basis helper, tail energies
-            (Def. 3), TT contraction and the relative error of Sec. 4.
+            (Def. 3), TT contraction, the relative error and the PSNR of
+            Sec. 4.
 philox      Philox4x32-10 counter-based generator (Salmon et al., SC'11) and the
             Box-Muller transform that expand an Omega seed into the Gaussian
             test matrices of Alg. 3 step 3.
@@ -34,6 +35,7 @@ from .tt_oracle import (  # noqa: F401
     tt_svd,
     tt_full,
     tt_error,
+    psnr,
     tt_distance,
     tail_energy,
     left_orthogonality_defect,

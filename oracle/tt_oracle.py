@@ -296,3 +296,16 @@ def left_orthogonality_defect(core):
     ra, I, rb = core.shape
     U = np.asarray(core, dtype=np.float64).reshape(ra * I, rb)
     return float(np.max(np.abs(U.T @ U - np.eye(rb))))
+
+
+def psnr(A, A_hat):
+    """Peak signal-to-noise ratio of Sec. 4: 10 log10(N ||A_hat||_max^2 /
+    ||A - A_hat||_F^2) with N the number of entries (the paper prints the
+    third-order case I_1 I_2 I_3; the product of all mode sizes is the
+    reading for any order) and ||A_hat||_max the largest absolute entry of
+    the reconstruction, as printed.  Dense float64."""
+    A = np.asarray(A, dtype=np.float64)
+    A_hat = np.asarray(A_hat, dtype=np.float64)
+    err2 = float(np.sum((A - A_hat) ** 2))
+    peak = float(np.max(np.abs(A_hat)))
+    return 10.0 * np.log10(A.size * peak * peak / err2)

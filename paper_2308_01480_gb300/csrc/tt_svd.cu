@@ -1,16 +1,18 @@
 // TT-SVD (Alg. 1): sequential truncated SVDs of the unfoldings with the
 // prescribed accuracy delta = eps ||A||_F / sqrt(d - 1), on the GPU.
 //
-// Per mode the unfolding C (m x n, row-major) gives its Gram G = C C^T by a
-// cuBLAS GEMM; cuSOLVER's syevd returns all eigenpairs of G (ascending);
-// the eigenvalues come back to the host, which picks the smallest rank
-// whose discarded tail sum_{i > r} lambda_i is at most delta^2 (capped);
-// core k is the top r eigenvectors (left singular vectors of C) and the
-// next remainder U^T C = S V^T is a second GEMM.  For a BF16 tensor the
-// projection applies U as BF16 hi + lo parts (two GEMMs into one FP32
-// result), so the remainder is FP32-accurate.  This is the deterministic
-// baseline of the paper, off the randomized hot path: host-synchronous,
-// library GEMMs and eigendecompositions.
+// The tensor is converted to FP64 once; per mode the unfolding C (m x n,
+// row-major) gives its Gram G = C C^T by a cuBLAS DGEMM; cuSOLVER's Dsyevd
+// returns all eigenpairs of G (ascending); the eigenvalues come back to
+// the host, which picks the smallest rank whose discarded tail
+// sum_{i > r} lambda_i is at most delta^2 (capped); core k is the top r
+// eigenvectors (left singular vectors of C, stored as FP32) and the next
+// remainder U^T C = S V^T is a second DGEMM.  FP64 throughout because the
+// Gram squares the singular values: in FP32 the smooth tensors of the
+// paper's experiments (singular values decaying below 1e-4 of the first)
+// would lose the directions that decide their error.  This is the
+// deterministic baseline of the paper, off the randomized hot path:
+// host-synchronous, library GEMMs and eigendecompositions.
 #include <cublas_v2.h>
 #include <cusolverDn.h>
 
@@ -58,8 +60,8 @@ tt_status handles(Handles** out) {
 struct SvdLayout {
   std::vector<int64_t> cap;   // clamped rank caps, cap[0] = cap[d] = 1
   std::vector<int64_t> m, n;  // unfolding sizes at the caps, modes 0 .. d-2
-  size_t off_R0 = 0, off_R1 = 0, off_G = 0, off_W = 0, off_U = 0, off_Uh = 0, off_Ul = 0, off_work = 0,
-         off_info = 0, total = 0;
+  size_t off_A = 0, off_R0 = 0, off_R1 = 0, off_G = 0, off_W = 0, off_U = 0, off_work = 0, off_info = 0,
+         total = 0;
   int lwork = 0;
 };
 
@@ -105,9 +107,9 @@ tt_status svd_layout(const int64_t* dims, int d, const int64_t* max_ranks, int s
   int lwork = 0;
   for (int k = 0; k < d - 1; ++k) {
     int lw = 0;
-    if (cusolverDnSsyevd_bufferSize(h->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, (int)L.m[k], nullptr,
+    if (cusolverDnDsyevd_bufferSize(h->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, (int)L.m[k], nullptr,
                                     (int)L.m[k], nullptr, &lw) != CUSOLVER_STATUS_SUCCESS) {
-      set_last_error("cusolverDnSsyevd_bufferSize failed");
+      set_last_error("cusolverDnDsyevd_bufferSize failed");
       return TT_ECUDA;
     }
     lwork = std::max(lwork, lw);
@@ -115,38 +117,43 @@ tt_status svd_layout(const int64_t* dims, int d, const int64_t* max_ranks, int s
   L.lwork = lwork;
   size_t off = 0;
   auto take = [&](size_t bytes) { const size_t o = off; off = align_up(off + std::max<size_t>(bytes, 1)); return o; };
-  L.off_R0 = take(maxR * 4);
-  L.off_R1 = take(maxR * 4);
-  L.off_G = take(maxG * 4);
-  L.off_W = take(maxW * 4);
-  L.off_U = take(maxU * 4);
-  const size_t uh = storage == TT_BF16 ? (size_t)(L.m[0] * L.cap[1]) * 2 : 0;
-  L.off_Uh = take(uh);
-  L.off_Ul = take(uh);
-  L.off_work = take((size_t)lwork * 4);
+  L.off_A = take((size_t)total * 8);
+  L.off_R0 = take(maxR * 8);
+  L.off_R1 = take(maxR * 8);
+  L.off_G = take(maxG * 8);
+  L.off_W = take(maxW * 8);
+  L.off_U = take(maxU * 8);
+  L.off_work = take((size_t)lwork * 8);
   L.off_info = take(sizeof(int));
   L.total = off;
   return TT_OK;
 }
 
-// U (m x r, row-major) = the eigenvectors of the r largest eigenvalues, in
-// descending order, from syevd's column-major ascending output; also to
-// core, and (when hi != NULL) U split into BF16 hi + lo parts.
-__global__ void k_gather_top(const float* __restrict__ Gv, int m, int r, float* __restrict__ U,
-                             float* __restrict__ core, __nv_bfloat16* __restrict__ hi,
-                             __nv_bfloat16* __restrict__ lo) {
+// U (m x r, row-major, FP64) = the eigenvectors of the r largest
+// eigenvalues, in descending order, from syevd's column-major ascending
+// output; also to core (FP32).
+__global__ void k_gather_top(const double* __restrict__ Gv, int m, int r, double* __restrict__ U,
+                             float* __restrict__ core) {
   const int64_t total = (int64_t)m * r;
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(x / r), c = (int)(x % r);
-    const float v = Gv[(int64_t)(m - 1 - c) * m + i];
+    const double v = Gv[(int64_t)(m - 1 - c) * m + i];
     U[x] = v;
-    core[x] = v;
-    if (hi) {
-      const __nv_bfloat16 h = __float2bfloat16_rn(v);
-      hi[x] = h;
-      lo[x] = __float2bfloat16_rn(v - __bfloat162float(h));
-    }
+    core[x] = (float)v;
   }
+}
+
+// The tensor (FP32 or BF16) to FP64, exactly.
+template <typename T>
+__global__ void k_to_f64(const T* __restrict__ x, int64_t count, double* __restrict__ y) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (double)ld_elem(x, i);
+}
+
+// The last remainder (FP64) to the last core (FP32).
+__global__ void k_to_f32(const double* __restrict__ x, int64_t count, float* __restrict__ y) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
 }
 
 tt_status blas_check(cublasStatus_t s, const char* what) {
@@ -205,49 +212,56 @@ extern "C" tt_status tt_svd_decompose(const void* tensor, int storage, const int
     return TT_ECUDA;
   }
   char* ws = static_cast<char*>(workspace);
-  float* G = (float*)(ws + L.off_G);
-  float* W = (float*)(ws + L.off_W);
-  float* U = (float*)(ws + L.off_U);
-  __nv_bfloat16* Uh = (__nv_bfloat16*)(ws + L.off_Uh);
-  __nv_bfloat16* Ul = (__nv_bfloat16*)(ws + L.off_Ul);
-  float* work = (float*)(ws + L.off_work);
+  double* A64 = (double*)(ws + L.off_A);
+  double* G = (double*)(ws + L.off_G);
+  double* W = (double*)(ws + L.off_W);
+  double* U = (double*)(ws + L.off_U);
+  double* work = (double*)(ws + L.off_work);
   int* info = (int*)(ws + L.off_info);
-  const float one = 1.f, zero = 0.f;
-  std::vector<float> w;
+  const double one = 1.0, zero = 0.0;
+  int64_t total = 1;
+  for (int k = 0; k < d; ++k) total *= dims[k];
+  {
+    const int blocks = (int)imin(ceil_div(total, 256), 4096);
+    note_launch("svd_convert");
+    if (storage == TT_BF16)
+      k_to_f64<__nv_bfloat16><<<blocks, 256, 0, st>>>((const __nv_bfloat16*)tensor, total, A64);
+    else
+      k_to_f64<float><<<blocks, 256, 0, st>>>((const float*)tensor, total, A64);
+    SVD_TRY(cuda_check(cudaGetLastError(), "k_to_f64"));
+  }
+  std::vector<double> w;
   double delta2 = 0.0;
   int64_t r_prev = 1;
-  const void* C = tensor;
-  cudaDataType_t ctype = storage == TT_BF16 ? CUDA_R_16BF : CUDA_R_32F;
+  const double* C = A64;
   ranks_out[0] = 1;
   for (int k = 0; k < d - 1; ++k) {
     const int m = (int)(r_prev * dims[k]);
     const int n = (int)L.n[k];
     // Alg. 1 step 3 (as a Gram): G = C C^T, C row-major m x n is the
     // column-major n x m matrix C', so G = C'^T C'
-    SVD_TRY(blas_check(cublasGemmEx(h->blas, CUBLAS_OP_T, CUBLAS_OP_N, m, m, n, &one, C, ctype, n, C, ctype, n, &zero,
-                                    G, CUDA_R_32F, m, CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT),
-                       "Gram GEMM"));
-    if (cusolverDnSsyevd(h->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, m, G, m, W, work, L.lwork,
+    SVD_TRY(blas_check(cublasDgemm(h->blas, CUBLAS_OP_T, CUBLAS_OP_N, m, m, n, &one, C, n, C, n, &zero, G, m),
+                       "Gram DGEMM"));
+    if (cusolverDnDsyevd(h->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, m, G, m, W, work, L.lwork,
                          info) != CUSOLVER_STATUS_SUCCESS) {
-      set_last_error("cusolverDnSsyevd failed");
+      set_last_error("cusolverDnDsyevd failed");
       return TT_ECUDA;
     }
     w.resize(m);
     int hinfo = 0;
-    SVD_TRY(cuda_check(cudaMemcpyAsync(w.data(), W, sizeof(float) * m, cudaMemcpyDeviceToHost, st), "eigenvalues"));
+    SVD_TRY(cuda_check(cudaMemcpyAsync(w.data(), W, sizeof(double) * m, cudaMemcpyDeviceToHost, st), "eigenvalues"));
     SVD_TRY(cuda_check(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, st), "syevd info"));
     SVD_TRY(cuda_check(cudaStreamSynchronize(st), "cudaStreamSynchronize"));
     if (hinfo != 0) {
-      set_last_error(("cusolverDnSsyevd did not converge (info " + std::to_string(hinfo) + ")").c_str());
+      set_last_error(("cusolverDnDsyevd did not converge (info " + std::to_string(hinfo) + ")").c_str());
       return TT_ECUDA;
     }
     // descending eigenvalues (squared singular values).  The discarded
     // tails are suffix sums of the eigenvalues as computed: the small ones
-    // are rounding noise of either sign (about eps_32 lambda_max each), so
-    // they are summed unclamped and cancel, instead of adding a bias; the
-    // first Gram's trace is ||A||_F^2
+    // are rounding noise of either sign, so they are summed unclamped and
+    // cancel instead of adding a bias; the first Gram's trace is ||A||_F^2
     std::vector<double> lam(m);
-    for (int i = 0; i < m; ++i) lam[i] = (double)w[m - 1 - i];
+    for (int i = 0; i < m; ++i) lam[i] = w[m - 1 - i];
     const int64_t cap = L.cap[k + 1];
     std::vector<double> tail(m + 1, 0.0);
     for (int i = m - 1; i >= 0; --i) tail[i] = tail[i + 1] + lam[i];
@@ -261,38 +275,26 @@ extern "C" tt_status tt_svd_decompose(const void* tensor, int storage, const int
       }
     ranks_out[k + 1] = r;
     // Alg. 1 step 5: core k = the top r left singular vectors
-    const bool split = (k == 0 && storage == TT_BF16);
     const int64_t cnt = (int64_t)m * r;
     note_launch("svd_gather");
-    k_gather_top<<<(int)imin(ceil_div(cnt, 256), 1024), 256, 0, st>>>(G, m, (int)r, U, cores_out[k],
-                                                                      split ? Uh : nullptr, split ? Ul : nullptr);
+    k_gather_top<<<(int)imin(ceil_div(cnt, 256), 1024), 256, 0, st>>>(G, m, (int)r, U, cores_out[k]);
     SVD_TRY(cuda_check(cudaGetLastError(), "k_gather_top"));
     // Alg. 1 step 6: the next remainder U^T C (r x n, row-major) is the
     // column-major n x r matrix C' U
-    float* R = (float*)(ws + ((k % 2 == 0) ? L.off_R0 : L.off_R1));
-    if (split) {
-      SVD_TRY(blas_check(cublasGemmEx(h->blas, CUBLAS_OP_N, CUBLAS_OP_T, n, (int)r, m, &one, C, ctype, n, Uh,
-                                      CUDA_R_16BF, (int)r, &zero, R, CUDA_R_32F, n, CUBLAS_COMPUTE_32F,
-                                      CUBLAS_GEMM_DEFAULT),
-                         "projection GEMM (hi)"));
-      SVD_TRY(blas_check(cublasGemmEx(h->blas, CUBLAS_OP_N, CUBLAS_OP_T, n, (int)r, m, &one, C, ctype, n, Ul,
-                                      CUDA_R_16BF, (int)r, &one, R, CUDA_R_32F, n, CUBLAS_COMPUTE_32F,
-                                      CUBLAS_GEMM_DEFAULT),
-                         "projection GEMM (lo)"));
-    } else {
-      SVD_TRY(blas_check(cublasGemmEx(h->blas, CUBLAS_OP_N, CUBLAS_OP_T, n, (int)r, m, &one, C, ctype, n, U,
-                                      CUDA_R_32F, (int)r, &zero, R, CUDA_R_32F, n, CUBLAS_COMPUTE_32F,
-                                      CUBLAS_GEMM_DEFAULT),
-                         "projection GEMM"));
-    }
+    double* R = (double*)(ws + ((k % 2 == 0) ? L.off_R0 : L.off_R1));
+    SVD_TRY(blas_check(cublasDgemm(h->blas, CUBLAS_OP_N, CUBLAS_OP_T, n, (int)r, m, &one, C, n, U, (int)r, &zero, R,
+                                   n),
+                       "projection DGEMM"));
     C = R;
-    ctype = CUDA_R_32F;
     r_prev = r;
   }
   // Alg. 1 step 8: the last core is the last remainder
-  SVD_TRY(cuda_check(cudaMemcpyAsync(cores_out[d - 1], C, sizeof(float) * (size_t)(r_prev * dims[d - 1]),
-                                     cudaMemcpyDeviceToDevice, st),
-                     "last core"));
+  {
+    const int64_t cnt = r_prev * dims[d - 1];
+    note_launch("svd_convert");
+    k_to_f32<<<(int)imin(ceil_div(cnt, 256), 1024), 256, 0, st>>>(C, cnt, cores_out[d - 1]);
+    SVD_TRY(cuda_check(cudaGetLastError(), "k_to_f32"));
+  }
   ranks_out[d] = 1;
   return cuda_check(cudaStreamSynchronize(st), "cudaStreamSynchronize");
 }

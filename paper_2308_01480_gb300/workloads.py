@@ -98,6 +98,36 @@ def power_tensor(dims):
     return 1.0 / (s + 1.0)
 
 
+def power_tensor_h(dims, h):
+    """The power function of Sec. 4.1, Eq. (5): x = (i_1^h + ... + i_d^h)^(-1/h)
+    with 1-based indices i_k = 1 .. I_k, as printed."""
+    s = np.zeros(dims, dtype=np.float64)
+    for k, n in enumerate(dims):
+        shape = [1] * len(dims)
+        shape[k] = n
+        s = s + (np.arange(1, n + 1, dtype=np.float64) ** h).reshape(shape)
+    return s ** (-1.0 / h)
+
+
+def decaying_diag_tensor(n, T, D, dtype=np.float64):
+    """The spectrum-decaying tensor of Sec. 4.1: frontal slice j (1-based)
+    is diag(1 x min(T, j), 10^-D, 10^-2D, ..., 10^-(n - min(T, j)) D),
+    n x n; entries below the dtype's range are zero."""
+    X = np.zeros((n, n, n), dtype=dtype)
+    idx = np.arange(n)
+    for j in range(1, n + 1):
+        t = min(T, j)
+        diag = np.ones(n, dtype=np.float64)
+        diag[t:] = 10.0 ** (-D * np.arange(1, n - t + 1, dtype=np.float64))
+        X[idx, idx, j - 1] = diag.astype(dtype)
+    return X
+
+
+def add_noise_snr(X, snr_db, rng):
+    """Gaussian white noise at a measured SNR: ||E|| / ||X|| = 10^(-SNR/20)."""
+    return add_noise(X, 10.0 ** (-snr_db / 20.0), rng)
+
+
 def make_tensor(w: Workload):
     """Dense float64 tensor of workload w (deterministic in w.tensor_seed)."""
     rng = np.random.default_rng(w.tensor_seed)
@@ -105,6 +135,10 @@ def make_tensor(w: Workload):
         X = dense_from_cores(random_tt_cores(w.dims, w.tt_ranks, rng, w.slice_decay))
     elif w.family == "power":
         X = power_tensor(w.dims)
+    elif w.family == "power_h5":
+        X = power_tensor_h(w.dims, 5.0)
+    elif w.family == "decay_diag":
+        X = decaying_diag_tensor(w.dims[0], 50, 1.0)
     else:
         raise ValueError(w.family)
     return add_noise(X, w.noise, rng, w.noise_kind)
@@ -166,3 +200,27 @@ def batch_workloads(count=256, seed=TENSOR_SEED_BASE + 5, omega_seed=OMEGA_SEED_
         out.append(Workload(f"batch{i}", dims, ranks, 5, 2, "bf16", seed * 1000 + i, omega_seed * 1000 + i,
                             "tt", ranks, noise=0.05))
     return out
+
+
+# The paper's synthetic accuracy experiments (Sec. 4.1, 4.2), parameterised
+# by the target rank r (all bonds r) and, for the noisy one, the SNR in dB.
+# q is not stated for them; q = 2 is taken (the TT-rBKI depth of the
+# paper's other experiments is small).
+STUDY_SEED_BASE = 20230900
+
+
+def study_workload(name, r, snr_db=5.0, q=2):
+    if name == "e1":          # 500^3 decaying spectrum, T = 50, D = 1, p = 2
+        return Workload(f"e1_decay500_r{r}", (500, 500, 500), (r, r), 2, q, "f32",
+                        STUDY_SEED_BASE + 1, OMEGA_SEED_BASE + 100 + r, "decay_diag",
+                        notes="500^3 diagonal slices, T=50, D=1")
+    if name == "e2":          # 45^5 power function, h = 5, p = 2
+        return Workload(f"e2_power45_r{r}", (45,) * 5, (r,) * 4, 2, q, "f32",
+                        STUDY_SEED_BASE + 2, OMEGA_SEED_BASE + 200 + r, "power_h5",
+                        notes="45^5 power function, h=5")
+    if name == "e6":          # E2 plus white noise at snr_db (measured)
+        return Workload(f"e6_power45_r{r}_snr{snr_db:g}", (45,) * 5, (r,) * 4, 2, q, "f32",
+                        STUDY_SEED_BASE + 6, OMEGA_SEED_BASE + 600 + r, "power_h5",
+                        noise=10.0 ** (-snr_db / 20.0),
+                        notes=f"45^5 power function, h=5, white noise at {snr_db:g} dB")
+    raise ValueError(name)
