@@ -296,7 +296,7 @@ def run_ours(args):
     svd_steps = 3
     mss = time_steps(step_svd, svd_steps, 1, barrier_sync)
     methods["tt_svd"] = {"ms_per_step": mss / svd_steps, "q": None,
-                         "note": "Gram GEMM + cuSOLVER syevd per mode, ranks capped at the targets"}
+                         "note": "FP64 Gram DGEMM + cuSOLVER Dsyevd per mode, ranks capped at the targets"}
 
     # ---- accuracy against the float64 tensor
     A64 = torch.from_numpy(A).to(dev)
