@@ -39,6 +39,7 @@ struct ModePlan {
   int iters = 0;             // subspace iteration: powers applied to the single block
   bool gram_route = false;   // exhaustion with D == m: one Gram pass
   bool gram_cols = false;    // exhaustion with D == n < m: the n x n Gram C^T C
+  bool gram_power = false;   // short unfolding: G = C C^T formed once, each power W = G X
   bool fused_ga = false;     // Gram-apply fused in one pass over C
 };
 
@@ -50,7 +51,7 @@ struct Plan {
   std::vector<ModePlan> modes;
   // workspace offsets in bytes
   size_t off_status = 0, off_R0 = 0, off_R1 = 0, off_S = 0, off_T = 0, off_part = 0, off_Y = 0,
-         off_Q = 0, off_W = 0, off_U = 0, off_G = 0, off_small = 0, off_X = 0, total = 0;
+         off_Q = 0, off_W = 0, off_U = 0, off_G = 0, off_small = 0, off_X = 0, off_blas = 0, total = 0;
 };
 
 tt_status resolve_options(const tt_options* in, tt_options* out) {
@@ -108,6 +109,7 @@ tt_status build_plan(const int64_t* dims, int d, const int64_t* ranks, int p, in
   int64_t n = total;
   size_t maxR = 0, maxS = 0, maxT = 0, maxPart = 0, maxY = 0, maxQ = 0, maxU = 0, maxG = 0, maxSmall = 0,
          maxX = 0;
+  bool need_blas = false;
   for (int k = 0; k < d - 1; ++k) {
     ModePlan& M = P.modes[k];
     n /= dims[k];
@@ -137,6 +139,14 @@ tt_status build_plan(const int64_t* dims, int d, const int64_t* ranks, int p, in
     M.gram_cols = P.o.exhaust_gram && !M.gram_route && cols == M.D && M.D == M.n && M.n < M.m &&
                   ttr::eig_top_ok((int)M.n);
     M.fused_ga = ttr::simt_ga_fused_ok(M.m, M.b);
+    // Krylov powers over a short unfolding (n <= 8192) are latency-bound
+    // passes over few column tiles; when there are at least two, one Gram
+    // G = C C^T (m^2 n flops, a plain GEMM) and small GEMMs W = G X replace
+    // them.  G stays below 16 MB.
+    {
+      const size_t powers = (P.o.method == TT_METHOD_RSI) ? (size_t)M.iters + 1 : M.blocks.size();
+      M.gram_power = !M.gram_route && !M.gram_cols && powers >= 2 && M.m <= 2048 && M.n <= 8192;
+    }
     if (!M.gram_route && !M.gram_cols && M.kq > 256)
       return fail(TT_EUNSUPPORTED, "Krylov basis larger than 256 columns");
     // sizes
@@ -178,6 +188,10 @@ tt_status build_plan(const int64_t* dims, int d, const int64_t* ranks, int p, in
       maxX = std::max(maxX, ttr::tc_ga_scratch_bytes(M.m, M.b));
       if (!M.gram_route && !M.gram_cols) maxT = std::max(maxT, (size_t)(M.b * M.n));
     }
+    if (M.gram_power) {
+      maxG = std::max(maxG, (size_t)(M.m * M.m));
+      need_blas = true;
+    }
   }
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + std::max<size_t>(bytes, 1)); return o; };
@@ -194,6 +208,7 @@ tt_status build_plan(const int64_t* dims, int d, const int64_t* ranks, int p, in
   P.off_G = take(maxG * 4);
   P.off_small = take(maxSmall * 4);
   P.off_X = take(maxX);
+  P.off_blas = take(need_blas ? ttr::kBlasWorkspace : 0);
   P.total = off;
   return TT_OK;
 }
@@ -278,9 +293,15 @@ tt_status run_mode(const Plan& P, int k, const TIn* C, char* ws, int* status, co
       }
       return TT_OK;
     };
+    float* Gp = (float*)(ws + P.off_G);
+    void* blas_ws = ws + P.off_blas;
+    if (M.gram_power)
+      TTR_CUDA(ttr::blas_gram(C, kBf16 ? 1 : 0, M.m, M.n, Gp, blas_ws, ttr::kBlasWorkspace, st));
     // one power: Wj = C C^T Xj (cj columns; row stride kq for both)
     auto power = [&](const float* Xj, float* Wj, int cj) -> tt_status {
-      if (use_tc) {
+      if (M.gram_power) {
+        TTR_CUDA(ttr::blas_gram_apply(Gp, M.m, Xj, kq, cj, Wj, kq, blas_ws, ttr::kBlasWorkspace, st));
+      } else if (use_tc) {
         if (ttr::tc_ga_ok(M.m, M.n, cj)) {
           TTR_CUDA(ttr::tc_ga(Cb, M.m, M.n, Xj, kq, cj, part, Wj, kq, xs, status, st));
         } else {
@@ -356,9 +377,21 @@ tt_status check_problem(const Plan& P, const void* tensor, const float* const* o
 // Enqueues the whole mode loop of Alg. 3 for one problem on `st`.  `ws`
 // holds P.total bytes (its own status area unused); `status` points to the
 // problem's 256-byte status area, cleared by the caller.
+// The cuBLAS handle of the Gram-power route, created before any work is
+// enqueued (and before a capture begins), never while capturing.
+tt_status ensure_blas(const Plan& P) {
+  for (const ModePlan& M : P.modes)
+    if (M.gram_power) {
+      if (ttr::blas_init() != cudaSuccess) return fail(TT_ECUDA, "cuBLAS handle creation failed");
+      break;
+    }
+  return TT_OK;
+}
+
 tt_status enqueue_problem(const Plan& P, const void* tensor, const float* const* omegas, uint64_t seed,
                           float* const* cores_out, char* ws, int* status, cudaStream_t st) {
-  tt_status s = TT_OK;
+  tt_status s = ensure_blas(P);
+  if (s != TT_OK) return s;
   const int d = P.d;
   for (int k = 0; k < d - 1; ++k) {
     const void* C;
@@ -434,7 +467,7 @@ double plan_cost(const Plan& P) {
   for (int k = 0; k < P.d - 1; ++k) {
     const ModePlan& M = P.modes[k];
     const double e = (double)esize(k == 0 ? P.storage : P.remainder);
-    const bool gram = M.gram_route || M.gram_cols;
+    const bool gram = M.gram_route || M.gram_cols || M.gram_power;
     const double passes = gram ? 2.0 : 2.0 + 2.0 * (double)M.blocks.size();
     us += passes * (double)M.m * (double)M.n * e / 1.0e6;
     us += M.gram_route ? 60.0 : M.gram_cols ? 110.0 : 50.0 * (double)M.blocks.size() + 30.0 + 0.02 * (double)M.kq * M.kq;
@@ -832,6 +865,10 @@ tt_status tt_rbki_batched_graph_create(int count, const tt_problem* problems, vo
   if (s != TT_OK) return s;
   s = check_batch_ws(L, workspace, ws_bytes);
   if (s != TT_OK) return s;
+  for (const Plan& P : L.plans) {
+    s = ensure_blas(P);
+    if (s != TT_OK) return s;
+  }
   cudaStream_t cs;
   TTR_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   cudaGraph_t g = nullptr;

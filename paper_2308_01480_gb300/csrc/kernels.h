@@ -92,6 +92,14 @@ bool orth_cluster_ok(int64_t m, int kq, int b);
 cudaError_t launch_orth_cluster(const float* W, int64_t ldw, int64_t m, int b, int c, float* Q, int64_t ldq, int kq,
                                 int* flag, cudaStream_t st);
 
+// ---- plain GEMMs through cuBLAS (blas.cu): the Gram-power route
+constexpr size_t kBlasWorkspace = size_t(8) << 20;
+cudaError_t blas_init();
+cudaError_t blas_gram(const void* C, int c_bf16, int64_t m, int64_t n, float* G, void* ws, size_t ws_bytes,
+                      cudaStream_t st);
+cudaError_t blas_gram_apply(const float* G, int64_t m, const float* X, int64_t ldx, int c, float* W, int64_t ldw,
+                            void* ws, size_t ws_bytes, cudaStream_t st);
+
 // ---- register-tiled symmetric eigensolver, k <= 160, r <= 32 (eig_reg.cu)
 bool eig_reg_ok(int k, int r);
 // scratch: k * k + 3 k floats
