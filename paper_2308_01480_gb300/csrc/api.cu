@@ -142,10 +142,16 @@ tt_status build_plan(const int64_t* dims, int d, const int64_t* ranks, int p, in
     // Krylov powers over a short unfolding (n <= 8192) are latency-bound
     // passes over few column tiles; when there are at least two, one Gram
     // G = C C^T (m^2 n flops, a plain GEMM) and small GEMMs W = G X replace
-    // them.  G stays below 16 MB.
+    // them.  For a BF16 unfolding of at most 1024 rows the tensor-core Gram
+    // (2 m n flops per entry of C) also beats three or more streaming
+    // passes (4 b flops per entry each, HBM-bound) at any n.  G stays below
+    // 16 MB.
     {
       const size_t powers = (P.o.method == TT_METHOD_RSI) ? (size_t)M.iters + 1 : M.blocks.size();
-      M.gram_power = !M.gram_route && !M.gram_cols && powers >= 2 && M.m <= 2048 && M.n <= 8192;
+      const int cdt_k = (k == 0) ? P.storage : P.remainder;
+      M.gram_power = !M.gram_route && !M.gram_cols &&
+                     ((powers >= 2 && M.m <= 2048 && M.n <= 8192) ||
+                      (cdt_k == TT_BF16 && powers >= 3 && M.m <= 1024 && M.n < (int64_t(1) << 31)));
     }
     if (!M.gram_route && !M.gram_cols && M.kq > 256)
       return fail(TT_EUNSUPPORTED, "Krylov basis larger than 256 columns");

@@ -93,7 +93,7 @@ cudaError_t launch_orth_cluster(const float* W, int64_t ldw, int64_t m, int b, i
                                 int* flag, cudaStream_t st);
 
 // ---- plain GEMMs through cuBLAS (blas.cu): the Gram-power route
-constexpr size_t kBlasWorkspace = size_t(8) << 20;
+constexpr size_t kBlasWorkspace = size_t(32) << 20;
 cudaError_t blas_init();
 cudaError_t blas_gram(const void* C, int c_bf16, int64_t m, int64_t n, float* G, void* ws, size_t ws_bytes,
                       cudaStream_t st);
