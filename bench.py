@@ -39,7 +39,6 @@ CONFIG_ID = 3
 # kernel family; an entry is removed when its kernel changes after the
 # capture.
 NCU_TRAFFIC = {
-    "gram_apply_tc": 106368819.0,   # the five mode-2 powers (mode 3 takes the Gram-power route)
     "proj_tc": 124948309.0,
     "cs_tc": 54547584.0,
     "gram_tc": 208040192.0,

@@ -67,7 +67,9 @@ cudaError_t blas_gram_apply(const float* G, int64_t m, const float* X, int64_t l
   cudaError_t e = prepare(&h, ws, ws_bytes, st);
   if (e != cudaSuccess) return e;
   const float one = 1.f, zero = 0.f;
-  ProfScope prof("gram_power", st, (double)m * m * 4, 2.0 * m * m * c);
+  // G (at most 16 MB) is read from L2 by every power: no algorithmic HBM
+  // bytes are counted for it
+  ProfScope prof("gram_power", st, 0.0, 2.0 * m * m * c);
   note_launch("gram_power");
   const cublasStatus_t s = cublasSgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, c, (int)m, (int)m, &one, X, (int)ldx, G, (int)m,
                                        &zero, W, (int)ldw);
