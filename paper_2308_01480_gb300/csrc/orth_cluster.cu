@@ -53,6 +53,16 @@ struct ClusterOrthArgs {
 
 __host__ __device__ inline int pad4(int x) { return (x + 3) & ~3; }
 
+// 4-byte asynchronous global -> shared copy; with ok = false it reads
+// nothing and writes zero (src-size 0)
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool ok) {
+  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(ok ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
 __device__ __forceinline__ float warp_max(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -172,25 +182,26 @@ __global__ void __launch_bounds__(OC_THREADS, 1) k_orth_cluster(ClusterOrthArgs 
   float* Qc = Zn + rp * bp;
   const bool report = rank == 0;
 
-  // zero-padded copies of the CTA's rows of Q and W (a warp per row, lanes
-  // along the row, four rows in flight per warp); zero T and P
+  // zero-padded copies of the CTA's rows of Q and W by asynchronous copies
+  // (a warp per row, lanes along the row; padding entries are zero-filled
+  // copies that read nothing), all in flight together; zero T and P
   {
     const int lane = tid & 31, nw = blockDim.x >> 5;
-    for (int i0 = tid >> 5; i0 < rp; i0 += 4 * nw) {
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int i = i0 + u * nw;
-        if (i < rp) {
-          const float* qrow = a.Q + (r0 + i) * a.ldq;
-          const float* wrow = a.W + (r0 + i) * a.ldw;
-          for (int t = lane; t < kp; t += 32) Qc[i * kp + t] = (i < rc && t < kq) ? qrow[t] : 0.f;
-          for (int j = lane; j < bp; j += 32) {
-            Zc[i * bp + j] = (i < rc && j < b) ? wrow[j] : 0.f;
-            Zn[i * bp + j] = 0.f;
-          }
-        }
+    for (int i = tid >> 5; i < rp; i += nw) {
+      const bool row_ok = i < rc;
+      const float* qrow = row_ok ? a.Q + (r0 + i) * a.ldq : a.Q;
+      const float* wrow = row_ok ? a.W + (r0 + i) * a.ldw : a.W;
+      for (int t = lane; t < kp; t += 32) {
+        const bool ok = row_ok && t < kq;
+        cp_async4(&Qc[i * kp + t], ok ? qrow + t : a.Q, ok);
+      }
+      for (int j = lane; j < bp; j += 32) {
+        const bool ok = row_ok && j < b;
+        cp_async4(&Zc[i * bp + j], ok ? wrow + j : a.W, ok);
+        Zn[i * bp + j] = 0.f;
       }
     }
+    cp_async_wait_all();
   }
   for (int x = tid; x < bp * bp; x += blockDim.x) T[x] = 0.f;
   for (int x = tid; x < kp * bp; x += blockDim.x) P[x] = 0.f;
