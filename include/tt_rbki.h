@@ -96,7 +96,14 @@ typedef struct {
                            (C C^T)^q C W only (b columns), re-orthonormalised
                            after every power.  Either with q = 0 is TT-rSVD
                            (Alg. 2).  Both truncate by Rayleigh-Ritz.         */
-  int32_t reserved[3];  /* must be zero                                       */
+  int32_t gram_power;   /* 1 (default): when a mode has several Krylov powers
+                           over an unfolding with n <= 8192 columns (at most
+                           2048 rows), or at least three over a BF16 one of
+                           at most 1024 rows, form G = C C^T once (a plain
+                           cuBLAS GEMM, FP32 accumulation) and compute each
+                           power as G X: the same Krylov space, fewer passes
+                           over C.  0: every power streams C.                 */
+  int32_t reserved[2];  /* must be zero                                       */
 } tt_options;
 
 enum { TT_METHOD_RBKI = 0, TT_METHOD_RSI = 1 };

@@ -37,10 +37,12 @@ def _stream_handle(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def options(storage=N.TT_F32, remainder=None, exhaust_gram=True, batch_streams=0, method=N.TT_METHOD_RBKI):
+def options(storage=N.TT_F32, remainder=None, exhaust_gram=True, batch_streams=0, method=N.TT_METHOD_RBKI,
+            gram_power=True):
     """tt_options with the given fields (remainder None = same as storage;
     method TT_METHOD_RBKI (Alg. 3) or TT_METHOD_RSI (Alg. 4); q = 0 with
-    either is TT-rSVD, Alg. 2)."""
+    either is TT-rSVD, Alg. 2; gram_power False makes every Krylov power
+    stream the unfolding)."""
     o = N.TTOptions()
     N.check(N.lib().tt_rbki_default_options(ctypes.byref(o)))
     o.storage = int(storage)
@@ -48,6 +50,7 @@ def options(storage=N.TT_F32, remainder=None, exhaust_gram=True, batch_streams=0
     o.exhaust_gram = 1 if exhaust_gram else 0
     o.batch_streams = int(batch_streams)
     o.method = int(method)
+    o.gram_power = 1 if gram_power else 0
     return o
 
 

@@ -22,7 +22,8 @@ STATUS_NAMES = {0: "TT_OK", 1: "TT_EINVAL", 2: "TT_ENOMEM", 3: "TT_ECUDA", 4: "T
 class TTOptions(ctypes.Structure):
     _fields_ = [("storage", ctypes.c_int32), ("remainder", ctypes.c_int32),
                 ("exhaust_gram", ctypes.c_int32), ("batch_streams", ctypes.c_int32),
-                ("method", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("method", ctypes.c_int32), ("gram_power", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class TTProblem(ctypes.Structure):

@@ -62,7 +62,8 @@ tt_status resolve_options(const tt_options* in, tt_options* out) {
   if (out->remainder != TT_F32 && out->remainder != TT_BF16) return fail(TT_EINVAL, "options.remainder must be TT_F32 or TT_BF16");
   if (out->method != TT_METHOD_RBKI && out->method != TT_METHOD_RSI)
     return fail(TT_EINVAL, "options.method must be TT_METHOD_RBKI or TT_METHOD_RSI");
-  for (int i = 0; i < 3; ++i)
+  if (out->gram_power != 0 && out->gram_power != 1) return fail(TT_EINVAL, "options.gram_power must be 0 or 1");
+  for (int i = 0; i < 2; ++i)
     if (out->reserved[i] != 0) return fail(TT_EINVAL, "options.reserved must be zero");
   return TT_OK;
 }
@@ -149,7 +150,7 @@ tt_status build_plan(const int64_t* dims, int d, const int64_t* ranks, int p, in
     {
       const size_t powers = (P.o.method == TT_METHOD_RSI) ? (size_t)M.iters + 1 : M.blocks.size();
       const int cdt_k = (k == 0) ? P.storage : P.remainder;
-      M.gram_power = !M.gram_route && !M.gram_cols &&
+      M.gram_power = P.o.gram_power && !M.gram_route && !M.gram_cols &&
                      ((powers >= 2 && M.m <= 2048 && M.n <= 8192) ||
                       (cdt_k == TT_BF16 && powers >= 3 && M.m <= 1024 && M.n < (int64_t(1) << 31)));
     }
@@ -616,6 +617,7 @@ tt_status tt_rbki_default_options(tt_options* o) {
   o->storage = TT_F32;
   o->remainder = -1;
   o->exhaust_gram = 1;
+  o->gram_power = 1;
   return TT_OK;
 }
 

@@ -80,6 +80,11 @@ def test_invalid_arguments_rejected_on_host(L):
     opts.reserved[0] = 1
     assert L.tt_rbki_workspace_size(N.i64_array([5, 4, 3]), 3, N.i64_array([2, 2]), 1, 1, ctypes.byref(opts),
                                     ctypes.byref(nb)) == N.TT_EINVAL
+    L.tt_rbki_default_options(ctypes.byref(opts))
+    assert opts.gram_power == 1
+    opts.gram_power = 2
+    assert L.tt_rbki_workspace_size(N.i64_array([5, 4, 3]), 3, N.i64_array([2, 2]), 1, 1, ctypes.byref(opts),
+                                    ctypes.byref(nb)) == N.TT_EINVAL
     perm = (ctypes.c_int * 3)(0, 0, 1)
     assert L.tt_permute_convert(ctypes.c_void_p(256), 0, N.i64_array([2, 3, 4]), N.i64_array([12, 4, 1]),
                                 perm, 3, ctypes.c_void_p(512), 0, None) == N.TT_EINVAL

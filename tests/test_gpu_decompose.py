@@ -25,14 +25,15 @@ def tt():
     return tt
 
 
-def gpu_decompose(tt, A, ranks, p, q, storage="f32", omegas=None, seed=0, exhaust=True, remainder=None):
+def gpu_decompose(tt, A, ranks, p, q, storage="f32", omegas=None, seed=0, exhaust=True, remainder=None,
+                  gram_power=True):
     t = torch.from_numpy(np.ascontiguousarray(A, dtype=np.float32)).cuda()
     code = tt.TT_F32
     if storage == "bf16":
         t = t.to(torch.bfloat16)
         code = tt.TT_BF16
     rem = None if remainder is None else (tt.TT_BF16 if remainder == "bf16" else tt.TT_F32)
-    opts = tt.options(storage=code, remainder=rem, exhaust_gram=exhaust)
+    opts = tt.options(storage=code, remainder=rem, exhaust_gram=exhaust, gram_power=gram_power)
     om = [torch.from_numpy(o).cuda() for o in omegas] if omegas is not None else None
     cores, rr = tt.decompose(t, ranks, p, q, omega_seed=seed, omegas=om, opts=opts)
     torch.cuda.synchronize()
@@ -116,6 +117,40 @@ def test_bf16_error_criterion(tt, case):
         got, _ = gpu_decompose(tt, A, ranks, p, q, storage="bf16", seed=3, remainder=rem)
         eps = oracle.tt_error(A, got)
         assert eps <= 1.05 * eps_ref + 1e-4, (rem, eps, eps_ref)
+
+
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("gram_power", [True, False])
+def test_fp32_power_routes_match_oracle(tt, case, gram_power):
+    """Both ways of applying (C C^T)^j: through the m x m Gram matrix formed
+    once, and through alternating projections with C and C^T."""
+    dims, gr, ranks, p, q, noise = case
+    A = noisy_tt(dims, gr, 41, noise)
+    rr = oracle.clamp_ranks(dims, ranks)
+    om = W.explicit_omegas(dims, rr, p, 43)
+    ref = oracle.tt_rbki(A.astype(np.float32), ranks, p, q, omegas=om)
+    tt.profile_begin(event_timing=False)
+    got, _ = gpu_decompose(tt, A, ranks, p, q, omegas=om, exhaust=False, gram_power=gram_power)
+    fams = tt.profile_end()
+    assert oracle.tt_distance(got, ref) <= FP32_TOL
+    if not gram_power:
+        assert "gram_power" not in fams and "gram_blas" not in fams
+
+
+@pytest.mark.parametrize("case", CASES_TC)
+@pytest.mark.parametrize("gram_power", [True, False])
+def test_bf16_power_routes_error_criterion(tt, case, gram_power):
+    dims, gr, ranks, p, q, noise = case
+    A = noisy_tt(dims, gr, 47, noise)
+    eps_ref = oracle.tt_error(A, oracle.tt_rbki(A, ranks, p, q, seed=5))
+    tt.profile_begin(event_timing=False)
+    got, _ = gpu_decompose(tt, A, ranks, p, q, storage="bf16", seed=5, gram_power=gram_power)
+    fams = tt.profile_end()
+    eps = oracle.tt_error(A, got)
+    assert eps <= 1.05 * eps_ref + 1e-4, (gram_power, eps, eps_ref)
+    # the 40^4 case applies q = 4 powers to an 800 x 1600 unfolding at mode 2
+    if dims == (40, 40, 40, 40):
+        assert ("gram_power" in fams) == gram_power
 
 
 def test_nonfinite_input_flagged(tt):
