@@ -42,9 +42,9 @@ CONFIG_ID = 3
 LIBRARY_FAMILIES = ("gram_blas", "gram_power")
 
 NCU_TRAFFIC = {
-    "proj_tc": 124948309.0,
-    "cs_tc": 54547584.0,
-    "gram_tc": 208040192.0,
+    "proj_tc": 125112917.0,
+    "cs_tc": 54580736.0,
+    "gram_tc": 204879360.0,
 }
 
 

@@ -61,6 +61,8 @@ struct TcParams {
   int chunk_rows;   // proj: rows of C per chunk (multiple of 16)
   int x_resident;   // proj: X^T loaded once (single chunk)
   int slack_bytes;  // shared memory after the ring covering MMA reads past short boxes
+  int o_bytes;      // proj: output staging buffer of one epilogue warp (b rows x 32
+                    // columns); 0 = one scalar store per output element
 };
 
 struct TcShared {
@@ -91,7 +93,8 @@ k_tc_stream(const __grid_constant__ CUtensorMap mapC, const __grid_constant__ CU
   uint8_t* ring = smem;
   uint8_t* xres = ring + (size_t)p.stages * p.stage_bytes + p.slack_bytes;   // resident X^T
   uint8_t* tbuf = xres + p.x_res_bytes;                         // ga: T buffers
-  TcShared* sh = reinterpret_cast<TcShared*>(tbuf + 2 * p.t_bytes);
+  uint8_t* obuf = tbuf + 2 * p.t_bytes;                         // proj: output staging
+  TcShared* sh = reinterpret_cast<TcShared*>(obuf + 4 * p.o_bytes);
   volatile int* abortp = &sh->abort_flag;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -437,7 +440,39 @@ k_tc_stream(const __grid_constant__ CUtensorMap mapC, const __grid_constant__ CU
         if (lane == 0) mbar_arrive(&sh->dempty[buf]);
         const int64_t tile = cta_in_group + it * ctas_in_group;
         const int64_t col = tile * 128 + lrow;
-        if (OP == OPK_PROJ) {
+        if (OP == OPK_PROJ && p.o_bytes) {
+          // the warp's 32 columns of the b output rows go through shared
+          // memory (row-major b x 32, conflict-free), then out as 16-byte
+          // stores: 8 rows (BF16) or 4 rows (FP32) per warp instruction
+          // instead of one 2- or 4-byte store per row
+          uint8_t* ob = obuf + (size_t)q * p.o_bytes;
+          __syncwarp();
+          const int nc = p.split_hi_lo ? 32 : 64;
+#pragma unroll
+          for (int c = 0; c < 64; ++c)
+            if (c < nc && c < p.b) {
+              const float x = p.split_hi_lo ? __uint_as_float(r[c]) + __uint_as_float(r[(c + 32) & 63])
+                                            : __uint_as_float(r[c]);
+              if (p.out_bf16)
+                reinterpret_cast<__nv_bfloat16*>(ob)[c * 32 + lane] = __float2bfloat16_rn(x);
+              else
+                reinterpret_cast<float*>(ob)[c * 32 + lane] = x;
+            }
+          __syncwarp();
+          const int esz = p.out_bf16 ? 2 : 4;
+          const int cpr = 2 * esz;             // 16-byte chunks per staged row
+          const int ch = lane % cpr;
+          // first column of this lane's chunk; n % 8 == 0, so a chunk that
+          // starts inside the row ends inside it
+          const int64_t xc = tile * 128 + q * 32 + (int64_t)ch * (16 / esz);
+          for (int c0 = 0; c0 < p.b; c0 += 32 / cpr) {
+            const int c = c0 + lane / cpr;
+            if (c < p.b && xc < p.n) {
+              const uint4 v = *reinterpret_cast<const uint4*>(ob + (size_t)c * 32 * esz + ch * 16);
+              *reinterpret_cast<uint4*>(reinterpret_cast<uint8_t*>(p.out) + ((int64_t)c * p.ld_out + xc) * esz) = v;
+            }
+          }
+        } else if (OP == OPK_PROJ) {
           if (col < p.n) {
             if (p.split_hi_lo) {
               // S[c] = hi part (column c) + lo part (column c + 32), c < b <= 32
@@ -570,7 +605,7 @@ int num_sms() {
 
 size_t tc_smem_bytes(const TcParams& p) {
   return 1024 + (size_t)p.stages * p.stage_bytes + p.slack_bytes + p.x_res_bytes + 2 * (size_t)p.t_bytes +
-         sizeof(TcShared) + 64;
+         4 * (size_t)p.o_bytes + sizeof(TcShared) + 64;
 }
 
 // Rows of a C box: the 16-rounded row count when it is below 128.
@@ -582,7 +617,8 @@ int box_rows_for(int64_t m, int cap) { return (int)imin(cap, (m + 15) / 16 * 16)
 // flight than one deeper ring; else one CTA with the whole shared memory.
 // Sets p.stages; returns the CTAs per SM.
 int choose_residency(TcParams& p, int maxst, bool allow_two = true) {
-  const int64_t fixed = 1024 + (int64_t)p.slack_bytes + p.x_res_bytes + 2 * (int64_t)p.t_bytes + sizeof(TcShared) + 64;
+  const int64_t fixed = 1024 + (int64_t)p.slack_bytes + p.x_res_bytes + 2 * (int64_t)p.t_bytes + 4 * (int64_t)p.o_bytes +
+                        sizeof(TcShared) + 64;
   const int64_t half = (SMEM_HALF - fixed) / p.stage_bytes;
   if (allow_two && half >= 3) {
     p.stages = (int)imin(maxst, half);
@@ -734,10 +770,11 @@ size_t tc_proj_scratch_bytes(int64_t m, int b, int split) {
   return (size_t)rows * ldt * 2 + 256;
 }
 
-TcShape proj_shape(int64_t m, int64_t n, int b, int split) {
+TcShape proj_shape(int64_t m, int64_t n, int b, int split, int o_bytes) {
   TcShape t;
   TcParams& p = t.p;
   p.m = m; p.n = n; p.b = b;
+  p.o_bytes = o_bytes;
   p.split_hi_lo = split;
   p.lo_off = split ? 32 : 0;
   p.npad = split ? 64 : pad16(b);
@@ -761,7 +798,12 @@ TcShape proj_shape(int64_t m, int64_t n, int b, int split) {
 cudaError_t tc_proj(const __nv_bfloat16* C, int64_t m, int64_t n, const float* X, int64_t ldx, int b, int split,
                     void* S, int s_bf16, int64_t lds, void* scratch, int* status, cudaStream_t st) {
   if (!tc_shape_ok(m, n) || (split ? b > 32 : b > 64)) return cudaErrorInvalidValue;
-  TcShape t = proj_shape(m, n, b, split);
+  // staged 16-byte stores need S and its row stride 16-byte aligned; the
+  // four warps' buffers take at most 32 KB (b <= 64)
+  const int esz = s_bf16 ? 2 : 4;
+  const int o_bytes = (int)(((int64_t)b * 32 * esz + 127) / 128 * 128);
+  const bool staged = reinterpret_cast<uintptr_t>(S) % 16 == 0 && (lds * esz) % 16 == 0 && 4 * o_bytes <= 32768;
+  TcShape t = proj_shape(m, n, b, split, staged ? o_bytes : 0);
   TcParams& p = t.p;
   p.out_bf16 = s_bf16; p.ld_out = lds; p.out = S; p.status = status;
   const int rows = p.npad;

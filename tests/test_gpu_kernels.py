@@ -141,6 +141,24 @@ def test_pass_project(tt, m, n, b, bf16):
     assert np.max(np.abs(_host64(yb) - ref)) <= 2 ** -8 * np.max(np.abs(ref)) + 1e-5 * np.max(bound)
 
 
+@pytest.mark.parametrize("b", [20, 64])
+@pytest.mark.parametrize("bf16_out", [False, True])
+def test_pass_project_unaligned_output(tt, b, bf16_out):
+    """An output that is not 16-byte aligned takes one scalar store per
+    element instead of the staged 16-byte stores; both give the same bits."""
+    m, n = 40, 4104
+    C = _as_dev(_rand((m, n), 5), True)
+    X = torch.from_numpy(_rand((m, b), 6)).cuda()
+    dt = torch.bfloat16 if bf16_out else torch.float32
+    y = tt.tt_pass(tt.TT_PASS_PROJECT, C, x=X, y_dtype=dt)
+    big = torch.zeros(b * n + 1, dtype=dt, device="cuda")
+    out = big[1:].view(b, n)
+    assert out.data_ptr() % 16 != 0
+    tt.tt_pass(tt.TT_PASS_PROJECT, C, x=X, out=out)
+    assert torch.equal(out, y)
+    assert big[0].item() == 0
+
+
 @pytest.mark.parametrize("m,n", [(1, 1), (7, 31), (40, 4097), (64, 1000), (128, 333), (100, 65),
                                  (40, 4104), (128, 2048), (100, 1000), (1, 64), (17, 8200)])
 @pytest.mark.parametrize("bf16", [False, True])
