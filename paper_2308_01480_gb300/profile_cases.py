@@ -3,8 +3,9 @@ time (each runs its case three times, so that a profiler told to skip the
 first launches of a kernel sees a warm third one):
 
     python -m paper_2308_01480_gb300.profile_cases pass ga 800 64000 30
-        one streaming pass (gram | proj | cs | ga) over a seeded BF16 m x n
-        unfolding, b columns
+        one streaming pass (gram | proj | proj_bf16 | cs | ga) over a seeded
+        BF16 m x n unfolding, b columns (proj_bf16: BF16 output, as the
+        decomposition writes its remainders)
     python -m paper_2308_01480_gb300.profile_cases eig 150 20
         the Rayleigh-Ritz eigensolver on a k x k PSD matrix, top r
     python -m paper_2308_01480_gb300.profile_cases decompose 3
@@ -22,16 +23,16 @@ def _pass(op, m, n, b):
     import paper_2308_01480_gb300 as tt
     g = torch.Generator(device="cuda").manual_seed(1)
     C = torch.randn(m, n, device="cuda", generator=g).to(torch.bfloat16)
-    code = {"gram": tt.TT_PASS_GRAM, "proj": tt.TT_PASS_PROJECT, "cs": tt.TT_PASS_SKETCH,
-            "ga": tt.TT_PASS_GRAMAPPLY}[op]
+    code = {"gram": tt.TT_PASS_GRAM, "proj": tt.TT_PASS_PROJECT, "proj_bf16": tt.TT_PASS_PROJECT,
+            "cs": tt.TT_PASS_SKETCH, "ga": tt.TT_PASS_GRAMAPPLY}[op]
     x = None
     if op == "cs":
         x = torch.randn(n, b, device="cuda", generator=g)
-    elif op in ("proj", "ga"):
+    elif op in ("proj", "proj_bf16", "ga"):
         x = torch.randn(m, b, device="cuda", generator=g)
     ws = torch.empty(tt.pass_workspace_size(code, m, n, b, tt.TT_BF16), dtype=torch.uint8, device="cuda")
     for _ in range(3):
-        y = tt.tt_pass(code, C, x=x, workspace=ws)
+        y = tt.tt_pass(code, C, x=x, workspace=ws, y_dtype=torch.bfloat16 if op == "proj_bf16" else None)
     torch.cuda.synchronize()
     print(op, m, n, b, float(y.float().abs().sum()))
 
