@@ -447,17 +447,27 @@ k_tc_stream(const __grid_constant__ CUtensorMap mapC, const __grid_constant__ CU
           // instead of one 2- or 4-byte store per row
           uint8_t* ob = obuf + (size_t)q * p.o_bytes;
           __syncwarp();
-          const int nc = p.split_hi_lo ? 32 : 64;
+          // rows c < b; the loops stop at b instead of running predicated
+          // over every accumulator column
+          auto stage = [&](int c, float x) {
+            if (p.out_bf16)
+              reinterpret_cast<__nv_bfloat16*>(ob)[c * 32 + lane] = __float2bfloat16_rn(x);
+            else
+              reinterpret_cast<float*>(ob)[c * 32 + lane] = x;
+          };
+          if (p.split_hi_lo) {
 #pragma unroll
-          for (int c = 0; c < 64; ++c)
-            if (c < nc && c < p.b) {
-              const float x = p.split_hi_lo ? __uint_as_float(r[c]) + __uint_as_float(r[(c + 32) & 63])
-                                            : __uint_as_float(r[c]);
-              if (p.out_bf16)
-                reinterpret_cast<__nv_bfloat16*>(ob)[c * 32 + lane] = __float2bfloat16_rn(x);
-              else
-                reinterpret_cast<float*>(ob)[c * 32 + lane] = x;
+            for (int c = 0; c < 32; ++c) {
+              if (c >= p.b) break;
+              stage(c, __uint_as_float(r[c]) + __uint_as_float(r[c + 32]));
             }
+          } else {
+#pragma unroll
+            for (int c = 0; c < 64; ++c) {
+              if (c >= p.b) break;
+              stage(c, __uint_as_float(r[c]));
+            }
+          }
           __syncwarp();
           const int esz = p.out_bf16 ? 2 : 4;
           const int cpr = 2 * esz;             // 16-byte chunks per staged row
