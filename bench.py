@@ -42,7 +42,7 @@ CONFIG_ID = 3
 LIBRARY_FAMILIES = ("gram_blas", "gram_power")
 
 NCU_TRAFFIC = {
-    "proj_tc": 125112917.0,
+    "proj_tc": 126750464.0,
     "cs_tc": 54580736.0,
     "gram_tc": 204879360.0,
 }
