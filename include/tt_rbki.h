@@ -131,6 +131,45 @@ TT_API tt_status tt_rbki_workspace_size(const int64_t* dims, int d, const int64_
                                  size_t* bytes);
 
 /*
+ * How each mode of a decomposition will run (the plan tt_rbki_decompose
+ * follows for the same arguments).  Planning only: no GPU work, no
+ * allocation, callable without a device.  Every route computes the rank-r_k'
+ * truncation of Alg. 3 steps 3-10 for the unfolding C (m x n, D = min(m, n)):
+ *   TT_ROUTE_KRYLOV      sketch C W, Krylov powers C (C^T X) streamed over C,
+ *                        block orthonormalisation, Rayleigh-Ritz;
+ *   TT_ROUTE_GRAM_ROWS   the basis would span all D = m rows (exhaustion):
+ *                        one Gram pass C C^T and its top r_k' eigenvectors
+ *                        (the exact truncated SVD);
+ *   TT_ROUTE_GRAM_COLS   exhaustion with D = n < m: the n x n Gram C^T C;
+ *   TT_ROUTE_GRAM_POWER  as TT_ROUTE_KRYLOV, with G = C C^T formed once and
+ *                        every power computed as G X.
+ *   modes      host, at least d-1 entries; entry k-1 describes mode k.
+ *   max_modes  capacity of modes.
+ * Errors: TT_EINVAL for a NULL modes or max_modes < d-1; otherwise the
+ * errors of tt_rbki_workspace_size.
+ */
+enum { TT_ROUTE_KRYLOV = 0, TT_ROUTE_GRAM_ROWS = 1, TT_ROUTE_GRAM_COLS = 2, TT_ROUTE_GRAM_POWER = 3 };
+
+typedef struct tt_mode_plan {
+  int64_t m, n;          /* unfolding: r_{k-1}' I_k rows, I_{k+1}..I_d columns  */
+  int64_t r_in, r_out;   /* clamped ranks r_{k-1}', r_k'                        */
+  int32_t b;             /* block width r_k' + p                                */
+  int32_t basis_cols;    /* columns of the Krylov (Alg. 3) or subspace (Alg. 4)
+                            basis, at most D                                    */
+  int32_t blocks;        /* Krylov blocks; 1 for Alg. 4                         */
+  int32_t powers;        /* products C (C^T X) applied, the one that feeds
+                            Rayleigh-Ritz included; 0 on the Gram routes        */
+  int32_t route;         /* TT_ROUTE_*                                          */
+  int32_t tensor_cores;  /* 1: the passes over C run on the tensor cores (BF16
+                            C with n % 8 == 0 and n >= 64)                      */
+  int32_t fused_power;   /* 1: a power streaming C is one fused pass            */
+  int32_t reserved;      /* 0                                                   */
+} tt_mode_plan;
+
+TT_API tt_status tt_rbki_plan_modes(const int64_t* dims, int d, const int64_t* ranks, int oversample,
+                                    int q, const tt_options* opts, tt_mode_plan* modes, int max_modes);
+
+/*
  * TT-rBKI decomposition (Alg. 3) with Omega drawn on the device.
  *   tensor     device, prod(dims) elements of opts->storage, row-major.
  *   omega_seed 64-bit seed.  Omega_k (n_k x (r_k' + p), n_k = I_{k+1}..I_d)

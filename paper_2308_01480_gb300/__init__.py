@@ -12,7 +12,7 @@ from ._native import (TT_BF16, TT_F32, TT_METHOD_RBKI, TT_METHOD_RSI, TT_PASS_GR
                       TT_PASS_GRAMAPPLY, TT_PASS_PROJECT, TT_PASS_SKETCH, TTError)
 
 __all__ = ["decompose", "tt_svd", "workspace_size", "core_sizes", "omega_generate", "permute_convert",
-           "tt_pass", "device_status", "options", "profile_begin", "profile_end", "TTError", "TT_F32",
+           "tt_pass", "device_status", "options", "plan_modes", "profile_begin", "profile_end", "TTError", "TT_F32",
            "TT_BF16", "Problem", "batched_workspace_size", "decompose_batched", "batched_device_status",
            "BatchGraph"]
 
@@ -70,6 +70,27 @@ def workspace_size(dims, ranks, oversample, q, opts=None):
                                            ctypes.byref(opts) if opts is not None else None,
                                            ctypes.byref(nbytes)))
     return nbytes.value
+
+
+ROUTE_NAMES = {N.TT_ROUTE_KRYLOV: "krylov", N.TT_ROUTE_GRAM_ROWS: "gram_rows",
+               N.TT_ROUTE_GRAM_COLS: "gram_cols", N.TT_ROUTE_GRAM_POWER: "gram_power"}
+
+
+def plan_modes(dims, ranks, oversample, q, opts=None):
+    """The per-mode plan tt_rbki_decompose follows for these arguments (no
+    GPU needed): a list of dicts, one per mode 1..d-1, with the unfolding
+    shape, clamped ranks, block width, basis columns, Krylov blocks, powers,
+    the route name and whether the passes run on the tensor cores."""
+    d = len(dims)
+    arr = (N.TTModePlan * max(1, d - 1))()
+    N.check(N.lib().tt_rbki_plan_modes(N.i64_array(dims), d, N.i64_array(ranks), int(oversample), int(q),
+                                       ctypes.byref(opts) if opts is not None else None, arr, d - 1))
+    out = []
+    for e in arr[:d - 1]:
+        out.append(dict(m=e.m, n=e.n, r_in=e.r_in, r_out=e.r_out, b=e.b, basis_cols=e.basis_cols,
+                        blocks=e.blocks, powers=e.powers, route=ROUTE_NAMES[e.route],
+                        tensor_cores=bool(e.tensor_cores), fused_power=bool(e.fused_power)))
+    return out
 
 
 def decompose(tensor, ranks, oversample, q, omega_seed=0, omegas=None, opts=None, workspace=None,

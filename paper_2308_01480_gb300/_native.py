@@ -14,6 +14,7 @@ TT_OK, TT_EINVAL, TT_ENOMEM, TT_ECUDA, TT_EBREAKDOWN, TT_ENONFINITE, TT_EUNSUPPO
 TT_F32, TT_BF16 = 0, 1
 TT_PASS_SKETCH, TT_PASS_GRAMAPPLY, TT_PASS_PROJECT, TT_PASS_GRAM = range(4)
 TT_METHOD_RBKI, TT_METHOD_RSI = range(2)
+TT_ROUTE_KRYLOV, TT_ROUTE_GRAM_ROWS, TT_ROUTE_GRAM_COLS, TT_ROUTE_GRAM_POWER = range(4)
 
 STATUS_NAMES = {0: "TT_OK", 1: "TT_EINVAL", 2: "TT_ENOMEM", 3: "TT_ECUDA", 4: "TT_EBREAKDOWN",
                 5: "TT_ENONFINITE", 6: "TT_EUNSUPPORTED", 7: "TT_ETIMEOUT"}
@@ -24,6 +25,13 @@ class TTOptions(ctypes.Structure):
                 ("exhaust_gram", ctypes.c_int32), ("batch_streams", ctypes.c_int32),
                 ("method", ctypes.c_int32), ("gram_power", ctypes.c_int32),
                 ("reserved", ctypes.c_int32 * 2)]
+
+
+class TTModePlan(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("r_in", ctypes.c_int64), ("r_out", ctypes.c_int64),
+                ("b", ctypes.c_int32), ("basis_cols", ctypes.c_int32), ("blocks", ctypes.c_int32),
+                ("powers", ctypes.c_int32), ("route", ctypes.c_int32), ("tensor_cores", ctypes.c_int32),
+                ("fused_power", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class TTProblem(ctypes.Structure):
@@ -56,6 +64,8 @@ _SIGNATURES = {
     "tt_rbki_core_sizes": ([_i64p, ctypes.c_int, _i64p, _i64p, _i64p], ctypes.c_int),
     "tt_rbki_workspace_size": ([_i64p, ctypes.c_int, _i64p, ctypes.c_int, ctypes.c_int,
                                 ctypes.POINTER(TTOptions), ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "tt_rbki_plan_modes": ([_i64p, ctypes.c_int, _i64p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(TTOptions),
+                            ctypes.POINTER(TTModePlan), ctypes.c_int], ctypes.c_int),
     "tt_rbki_decompose": ([_vp, _i64p, ctypes.c_int, _i64p, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
                            _vpp, _i64p, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(TTOptions)], ctypes.c_int),
     "tt_rbki_decompose_omega": ([_vp, _i64p, ctypes.c_int, _i64p, ctypes.c_int, ctypes.c_int, _vpp,

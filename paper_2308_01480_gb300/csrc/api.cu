@@ -643,6 +643,38 @@ tt_status tt_rbki_workspace_size(const int64_t* dims, int d, const int64_t* rank
   return TT_OK;
 }
 
+tt_status tt_rbki_plan_modes(const int64_t* dims, int d, const int64_t* ranks, int oversample, int q,
+                             const tt_options* opts, tt_mode_plan* modes, int max_modes) {
+  if (!modes) return fail(TT_EINVAL, "modes is NULL");
+  Plan P;
+  tt_status s = build_plan(dims, d, ranks, oversample, q, opts, P);
+  if (s != TT_OK) return s;
+  if (max_modes < d - 1) return fail(TT_EINVAL, "max_modes must be >= d - 1");
+  for (int k = 0; k < d - 1; ++k) {
+    const ModePlan& M = P.modes[k];
+    tt_mode_plan& o = modes[k];
+    std::memset(&o, 0, sizeof(o));
+    o.m = M.m;
+    o.n = M.n;
+    o.r_in = M.r_in;
+    o.r_out = M.r_out;
+    o.b = M.b;
+    o.basis_cols = M.kq;
+    o.blocks = (int32_t)M.blocks.size();
+    const bool exhaustion = M.gram_route || M.gram_cols;
+    o.powers = exhaustion ? 0 : (P.o.method == TT_METHOD_RSI ? M.iters + 1 : (int32_t)M.blocks.size());
+    o.route = M.gram_route ? TT_ROUTE_GRAM_ROWS
+            : M.gram_cols  ? TT_ROUTE_GRAM_COLS
+            : M.gram_power ? TT_ROUTE_GRAM_POWER
+                           : TT_ROUTE_KRYLOV;
+    const int cdt = (k == 0) ? P.storage : P.remainder;
+    const bool tc = cdt == TT_BF16 && ttr::tc_shape_ok(M.m, M.n);
+    o.tensor_cores = tc ? 1 : 0;
+    if (!exhaustion && !M.gram_power) o.fused_power = (tc ? ttr::tc_ga_ok(M.m, M.n, M.b) : M.fused_ga) ? 1 : 0;
+  }
+  return TT_OK;
+}
+
 tt_status tt_rbki_decompose(const void* tensor, const int64_t* dims, int d, const int64_t* ranks, int oversample,
                             int q, uint64_t omega_seed, float* const* cores_out, int64_t* ranks_out,
                             void* workspace, size_t ws_bytes, void* stream, const tt_options* opts) {
