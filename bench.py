@@ -164,6 +164,13 @@ def workload_config(w, world):
     }
 
 
+def plan_summary(tt, w, opts):
+    """The route the planner takes at each mode of the timed decomposition
+    (host-only query), e.g. "800x64000 gram_power tc"."""
+    return [f"{e['m']}x{e['n']} {e['route']}" + (" tc" if e["tensor_cores"] else "")
+            for e in tt.plan_modes(w.dims, w.ranks, w.oversample, w.q, opts)]
+
+
 def max_over_ranks(x, dist, device=None):
     """Largest value of x over all ranks (x itself without a process group)."""
     if dist is None:
@@ -356,6 +363,7 @@ def run_ours(args):
         "dtype": "bf16",
         "data": "synthetic (seeded; paper's datasets unavailable)",
         "config": workload_config(w, world),
+        "plan": plan_summary(tt, w, opts_bf),
         "tt_error": {"bf16": eps_bf, "fp32": eps_32},
         "methods_bf16": methods,
         "fp32_form": {"ms_per_step": ms32 / fp32_steps, "decompositions_per_s": fp32_steps / (ms32 * 1e-3),

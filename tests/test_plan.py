@@ -84,3 +84,12 @@ def test_argument_errors():
     arr = (N.TTModePlan * 1)()
     assert N.lib().tt_rbki_plan_modes(N.i64_array(DIMS), 5, N.i64_array(RANKS), 10, 4, None, arr, 1) == N.TT_EINVAL
     assert N.lib().tt_rbki_plan_modes(N.i64_array(DIMS), 5, N.i64_array(RANKS), 10, 4, None, None, 4) == N.TT_EINVAL
+
+
+def test_bench_plan_summary():
+    import bench
+    from paper_2308_01480_gb300 import workloads as W
+    w = W.CONFIGS[bench.CONFIG_ID]
+    got = bench.plan_summary(tt, w, bf16())
+    assert got == ["40x2560000 gram_rows tc", "800x64000 gram_power tc", "800x1600 gram_power tc",
+                   "800x40 gram_cols"]
