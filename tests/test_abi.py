@@ -197,3 +197,38 @@ def test_method_option_validated(L):
     assert rsi > 0 and nb.value > 0
     o.method = 2
     assert L.tt_rbki_workspace_size(dims, 4, ranks, 5, 2, ctypes.byref(o), ctypes.byref(nb)) == N.TT_EINVAL
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """The ctypes mirrors of the header's structs have the C compiler's field
+    offsets, field sizes and total size."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    mirrors = {"tt_options": N.TTOptions, "tt_mode_plan": N.TTModePlan, "tt_problem": N.TTProblem,
+               "tt_kernel_stat": N.TTKernelStat}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "tt_rbki.h"', "int main(void) {"]
+    for cname, cls in mirrors.items():
+        lines.append(f'  printf("{cname} . %zu %zu\\n", (size_t)0, sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu %zu\\n", offsetof({cname}, {fname}), '
+                         f"sizeof((({cname}*)0)->{fname}));")
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    seen = 0
+    for line in filter(None, out):
+        cname, fname, off, size = line.split()
+        cls = mirrors[cname]
+        if fname == ".":
+            assert ctypes.sizeof(cls) == int(size), cname
+        else:
+            field = getattr(cls, fname)
+            assert (field.offset, field.size) == (int(off), int(size)), (cname, fname)
+        seen += 1
+    assert seen == sum(len(c._fields_) + 1 for c in mirrors.values())
