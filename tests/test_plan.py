@@ -93,3 +93,15 @@ def test_bench_plan_summary():
     got = bench.plan_summary(tt, w, bf16())
     assert got == ["40x2560000 gram_rows tc", "800x64000 gram_power tc", "800x1600 gram_power tc",
                    "800x40 gram_cols"]
+
+
+def test_bench_family_names_exist_in_the_library():
+    """The kernel families bench.py reads (DRAM traffic, library GEMMs) are
+    names the library's launch accounting actually records."""
+    import glob
+    import re
+    import bench
+    src = "".join(open(f).read() for f in glob.glob(os.path.join(os.path.dirname(N.__file__), "csrc", "*.cu")))
+    names = set(re.findall(r'ProfScope \w+\("(\w+)"', src))
+    assert set(bench.NCU_TRAFFIC) <= names
+    assert set(bench.LIBRARY_FAMILIES) <= names
