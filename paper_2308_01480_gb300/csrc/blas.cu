@@ -12,6 +12,8 @@
 namespace ttr {
 
 namespace {
+// The handles live until the process exits: a destructor run at thread or
+// process exit could come after the CUDA context is already torn down.
 cudaError_t handle(cublasHandle_t* out) {
   thread_local std::map<int, cublasHandle_t> per_device;
   int dev = 0;
