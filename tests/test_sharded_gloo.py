@@ -1,4 +1,5 @@
-"""TT-rBKI split over ranks by the last mode, on CPU (gloo, world size 2).
+"""TT-rBKI and TT-rSI split over ranks by the last mode, on CPU (gloo,
+world size 2).
 
 Rank g holds the slab A[..., S_g] of the last mode.  Every unfolding of the
 remainder then splits by columns, C = [C_g], because the last mode index is
@@ -69,8 +70,10 @@ def _allreduce(a):
     return t.numpy()
 
 
-def _sharded_tt_rbki(A_g, dims, slab, ranks, p, q, omegas):
-    """Alg. 3 on this rank's slab; products with C summed over the ranks."""
+def _sharded_tt(A_g, dims, slab, ranks, p, q, omegas, method):
+    """Alg. 3 (method "rbki") or Alg. 4 ("rsi") on this rank's slab; products
+    with C summed over the ranks.  The subspace iteration takes each step as
+    one power, Q <- orth(C (C^T Q)): the span of Alg. 4's two half steps."""
     d = len(dims)
     rr = oracle.clamp_ranks(dims, ranks)
     R_g = A_g
@@ -91,6 +94,9 @@ def _sharded_tt_rbki(A_g, dims, slab, ranks, p, q, omegas):
             if Q.shape[1] >= D:
                 break
             Z = _allreduce(C_g @ (C_g.T @ X))
+            if method == "rsi":
+                X = Q = oracle.orth_top(Z, Q.shape[1])
+                continue
             for _ in range(2):
                 Z = Z - Q @ (Q.T @ Z)
             c = min(b, D - Q.shape[1])
@@ -108,7 +114,7 @@ def _sharded_tt_rbki(A_g, dims, slab, ranks, p, q, omegas):
     return cores
 
 
-def _worker(rank, world, port, case, out):
+def _worker(rank, world, port, case, method, out):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
@@ -117,8 +123,8 @@ def _worker(rank, world, port, case, out):
         rr = oracle.clamp_ranks(dims, ranks)
         om = W.explicit_omegas(dims, rr, p, 7)
         slab = _slab(dims[-1], rank, world)
-        cores = _sharded_tt_rbki(np.ascontiguousarray(A[..., slab]), dims, slab, ranks, p, q, om)
-        ref = oracle.tt_rbki(A, ranks, p, q, omegas=om)
+        cores = _sharded_tt(np.ascontiguousarray(A[..., slab]), dims, slab, ranks, p, q, om, method)
+        ref = (oracle.tt_rsi if method == "rsi" else oracle.tt_rbki)(A, ranks, p, q, omegas=om)
         mine = [c.tobytes() for c in cores]
         theirs = [None] * world
         dist.all_gather_object(theirs, mine)
@@ -130,12 +136,14 @@ def _worker(rank, world, port, case, out):
         dist.destroy_process_group()
 
 
+@pytest.mark.parametrize("method", ["rbki", "rsi"])
 @pytest.mark.parametrize("case", CASES)
-def test_sharded_matches_single_process_oracle(case):
+def test_sharded_matches_single_process_oracle(case, method):
     ctx = mp.get_context("spawn")
     with ctx.Manager() as mgr:
         out = mgr.dict()
-        mp.start_processes(_worker, args=(2, _free_port(), case, out), nprocs=2, join=True, start_method="spawn")
+        mp.start_processes(_worker, args=(2, _free_port(), case, method, out), nprocs=2, join=True,
+                           start_method="spawn")
         res = dict(out)
     assert set(res) == {0, 1}
     assert res[0]["slab"] + res[1]["slab"] == case[0][-1] and res[1]["slab"] >= 1
