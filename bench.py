@@ -38,8 +38,9 @@ CONFIG_ID = 3
 # averaged over the launches of one decomposition of this workload) by
 # kernel family; an entry is removed when its kernel changes after the
 # capture.
-# kernel families that are cuBLAS calls (plain GEMMs), not this library's kernels
-LIBRARY_FAMILIES = ("gram_blas", "gram_power")
+# kernel families that are library calls (cuBLAS and the like), not this
+# library's kernels: none on the decomposition path
+LIBRARY_FAMILIES = ()
 
 NCU_TRAFFIC = {
     "proj_tc": 126750464.0,

@@ -99,10 +99,10 @@ typedef struct {
   int32_t gram_power;   /* 1 (default): when a mode has several Krylov powers
                            over an unfolding with n <= 8192 columns (at most
                            2048 rows), or at least three over a BF16 one of
-                           at most 1024 rows, form G = C C^T once (a plain
-                           cuBLAS GEMM, FP32 accumulation) and compute each
-                           power as G X: the same Krylov space, fewer passes
-                           over C.  0: every power streams C.                 */
+                           at most 1024 rows, form G = C C^T once (tensor
+                           cores for BF16, FP32 accumulation) and compute
+                           each power as G X: the same Krylov space, fewer
+                           passes over C.  0: every power streams C.          */
   int32_t reserved[2];  /* must be zero                                       */
 } tt_options;
 
@@ -324,11 +324,11 @@ TT_API tt_status tt_omega_generate(uint64_t seed, int mode, int64_t n, int b, vo
  *   op = TT_PASS_GRAMAPPLY: Y = C (C^T X)    X = x: m x b FP32 (device)
  *   op = TT_PASS_PROJECT  : Y = X^T C        X = x: m x b FP32; Y is b x n,
  *                                            written in y_dtype (F32/BF16)
- *   op = TT_PASS_GRAM     : Y = C C^T        x unused; Y is m x m
+ *   op = TT_PASS_GRAM     : Y = C C^T        x unused; Y is m x m, m <= 2048
  * For SKETCH/GRAMAPPLY/GRAM, y is m x b (m x m) FP32.  The pass needs the
  * workspace size returned by tt_pass_workspace_size for the same arguments.
  * These are Alg. 3 steps 4 (sketch and Krylov powers), 10 (projection) and
- * the Gram route taken at exhaustion.
+ * the Gram formed at exhaustion or for the Gram-power route.
  */
 enum { TT_PASS_SKETCH = 0, TT_PASS_GRAMAPPLY = 1, TT_PASS_PROJECT = 2, TT_PASS_GRAM = 3 };
 
@@ -337,6 +337,19 @@ TT_API tt_status tt_pass_workspace_size(int op, int64_t m, int64_t n, int b, int
 TT_API tt_status tt_pass(int op, const void* C, int c_dtype, int64_t m, int64_t n, int b,
                   const float* x, void* y, int y_dtype, void* workspace, size_t ws_bytes,
                   void* stream);
+
+/*
+ * One Krylov power through a formed Gram matrix (Alg. 3 step 4 on the
+ * Gram-power route): W = G X.
+ *   G      device, m x m float32 row-major, symmetric (G = C C^T).
+ *   X      device, m x c float32, row stride ldx >= c; 1 <= c <= 64.
+ *   W      device, m x c float32, row stride ldw >= c, written; must not
+ *          overlap X or G.
+ * FP32 products with FP32 accumulation in a fixed order (bit-reproducible).
+ * Allocates nothing.  Errors: TT_EINVAL, TT_EUNSUPPORTED (c > 64), TT_ECUDA.
+ */
+TT_API tt_status tt_gram_power(const float* G, int64_t m, const float* X, int64_t ldx, int c, float* W,
+                               int64_t ldw, void* stream);
 
 /*
  * Top-r eigenpairs of a small symmetric matrix: the Rayleigh-Ritz step of

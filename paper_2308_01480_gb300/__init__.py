@@ -12,7 +12,7 @@ from ._native import (TT_BF16, TT_F32, TT_METHOD_RBKI, TT_METHOD_RSI, TT_PASS_GR
                       TT_PASS_GRAMAPPLY, TT_PASS_PROJECT, TT_PASS_SKETCH, TTError)
 
 __all__ = ["decompose", "tt_svd", "workspace_size", "core_sizes", "omega_generate", "permute_convert",
-           "tt_pass", "device_status", "options", "plan_modes", "profile_begin", "profile_end", "TTError", "TT_F32",
+           "tt_pass", "gram_power", "device_status", "options", "plan_modes", "profile_begin", "profile_end", "TTError", "TT_F32",
            "TT_BF16", "Problem", "batched_workspace_size", "decompose_batched", "batched_device_status",
            "BatchGraph"]
 
@@ -250,6 +250,19 @@ def tt_pass(op, C, b=None, x=None, y_dtype=None, stream=None, workspace=None, ou
                             ctypes.c_void_p(x.data_ptr() if x is not None else 0),
                             ctypes.c_void_p(out.data_ptr()), _dtype_code(out),
                             ctypes.c_void_p(workspace.data_ptr()), workspace.numel(), _stream_handle(stream)))
+    return out
+
+
+def gram_power(G, X, stream=None, out=None):
+    """W = G X through a formed Gram matrix (tt_gram_power): G (m, m) and
+    X (m, c) float32 CUDA tensors, X with unit column stride."""
+    torch = _torch()
+    m, c = X.shape
+    if out is None:
+        out = torch.empty((m, c), dtype=torch.float32, device=X.device)
+    N.check(N.lib().tt_gram_power(ctypes.c_void_p(G.data_ptr()), int(m), ctypes.c_void_p(X.data_ptr()),
+                                  int(X.stride(0)), int(c), ctypes.c_void_p(out.data_ptr()), int(out.stride(0)),
+                                  _stream_handle(stream)))
     return out
 
 

@@ -95,6 +95,8 @@ _SIGNATURES = {
                                 ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "tt_gram_apply_noalloc": ([_vp, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, _vp, _vp,
                                _vp], ctypes.c_int),
+    "tt_gram_power": ([_vp, ctypes.c_int64, _vp, ctypes.c_int64, ctypes.c_int, _vp, ctypes.c_int64, _vp],
+                      ctypes.c_int),
     "tt_sym_eig_workspace_size": ([ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "tt_sym_eig_top": ([_vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, ctypes.c_size_t, _vp],
                        ctypes.c_int),

@@ -51,7 +51,7 @@ struct Plan {
   std::vector<ModePlan> modes;
   // workspace offsets in bytes
   size_t off_status = 0, off_R0 = 0, off_R1 = 0, off_S = 0, off_T = 0, off_part = 0, off_Y = 0,
-         off_Q = 0, off_W = 0, off_U = 0, off_G = 0, off_small = 0, off_X = 0, off_blas = 0, total = 0;
+         off_Q = 0, off_W = 0, off_U = 0, off_G = 0, off_small = 0, off_X = 0, total = 0;
 };
 
 tt_status resolve_options(const tt_options* in, tt_options* out) {
@@ -110,7 +110,6 @@ tt_status build_plan(const int64_t* dims, int d, const int64_t* ranks, int p, in
   int64_t n = total;
   size_t maxR = 0, maxS = 0, maxT = 0, maxPart = 0, maxY = 0, maxQ = 0, maxU = 0, maxG = 0, maxSmall = 0,
          maxX = 0;
-  bool need_blas = false;
   for (int k = 0; k < d - 1; ++k) {
     ModePlan& M = P.modes[k];
     n /= dims[k];
@@ -142,7 +141,7 @@ tt_status build_plan(const int64_t* dims, int d, const int64_t* ranks, int p, in
     M.fused_ga = ttr::simt_ga_fused_ok(M.m, M.b);
     // Krylov powers over a short unfolding (n <= 8192) are latency-bound
     // passes over few column tiles; when there are at least two, one Gram
-    // G = C C^T (m^2 n flops, a plain GEMM) and small GEMMs W = G X replace
+    // G = C C^T (m^2 n flops, gram.cu) and small products W = G X replace
     // them.  For a BF16 unfolding of at most 1024 rows the tensor-core Gram
     // (2 m n flops per entry of C) also beats three or more streaming
     // passes (4 b flops per entry each, HBM-bound) at any n.  G stays below
@@ -150,7 +149,7 @@ tt_status build_plan(const int64_t* dims, int d, const int64_t* ranks, int p, in
     {
       const size_t powers = (P.o.method == TT_METHOD_RSI) ? (size_t)M.iters + 1 : M.blocks.size();
       const int cdt_k = (k == 0) ? P.storage : P.remainder;
-      M.gram_power = P.o.gram_power && !M.gram_route && !M.gram_cols &&
+      M.gram_power = P.o.gram_power && !M.gram_route && !M.gram_cols && ttr::gram_power_ok(M.m, M.b) &&
                      ((powers >= 2 && M.m <= 2048 && M.n <= 8192) ||
                       (cdt_k == TT_BF16 && powers >= 3 && M.m <= 1024 && M.n < (int64_t(1) << 31)));
     }
@@ -197,7 +196,7 @@ tt_status build_plan(const int64_t* dims, int d, const int64_t* ranks, int p, in
     }
     if (M.gram_power) {
       maxG = std::max(maxG, (size_t)(M.m * M.m));
-      need_blas = true;
+      maxPart = std::max(maxPart, ttr::gram_tiled_partials(M.m, M.n, cdt == TT_BF16 ? 1 : 0));
     }
   }
   size_t off = 0;
@@ -215,7 +214,6 @@ tt_status build_plan(const int64_t* dims, int d, const int64_t* ranks, int p, in
   P.off_G = take(maxG * 4);
   P.off_small = take(maxSmall * 4);
   P.off_X = take(maxX);
-  P.off_blas = take(need_blas ? ttr::kBlasWorkspace : 0);
   P.total = off;
   return TT_OK;
 }
@@ -301,13 +299,11 @@ tt_status run_mode(const Plan& P, int k, const TIn* C, char* ws, int* status, co
       return TT_OK;
     };
     float* Gp = (float*)(ws + P.off_G);
-    void* blas_ws = ws + P.off_blas;
-    if (M.gram_power)
-      TTR_CUDA(ttr::blas_gram(C, kBf16 ? 1 : 0, M.m, M.n, Gp, blas_ws, ttr::kBlasWorkspace, st));
+    if (M.gram_power) TTR_CUDA(ttr::gram_tiled(C, kBf16 ? 1 : 0, M.m, M.n, part, Gp, status, st));
     // one power: Wj = C C^T Xj (cj columns; row stride kq for both)
     auto power = [&](const float* Xj, float* Wj, int cj) -> tt_status {
       if (M.gram_power) {
-        TTR_CUDA(ttr::blas_gram_apply(Gp, M.m, Xj, kq, cj, Wj, kq, blas_ws, ttr::kBlasWorkspace, st));
+        TTR_CUDA(ttr::gram_power(Gp, M.m, Xj, kq, cj, Wj, kq, st));
       } else if (use_tc) {
         if (ttr::tc_ga_ok(M.m, M.n, cj)) {
           TTR_CUDA(ttr::tc_ga(Cb, M.m, M.n, Xj, kq, cj, part, Wj, kq, xs, status, st));
@@ -384,21 +380,9 @@ tt_status check_problem(const Plan& P, const void* tensor, const float* const* o
 // Enqueues the whole mode loop of Alg. 3 for one problem on `st`.  `ws`
 // holds P.total bytes (its own status area unused); `status` points to the
 // problem's 256-byte status area, cleared by the caller.
-// The cuBLAS handle of the Gram-power route, created before any work is
-// enqueued (and before a capture begins), never while capturing.
-tt_status ensure_blas(const Plan& P) {
-  for (const ModePlan& M : P.modes)
-    if (M.gram_power) {
-      if (ttr::blas_init() != cudaSuccess) return fail(TT_ECUDA, "cuBLAS handle creation failed");
-      break;
-    }
-  return TT_OK;
-}
-
 tt_status enqueue_problem(const Plan& P, const void* tensor, const float* const* omegas, uint64_t seed,
                           float* const* cores_out, char* ws, int* status, cudaStream_t st) {
-  tt_status s = ensure_blas(P);
-  if (s != TT_OK) return s;
+  tt_status s = TT_OK;
   const int d = P.d;
   for (int k = 0; k < d - 1; ++k) {
     const void* C;
@@ -763,8 +747,9 @@ static tt_status pass_layout(int op, int64_t m, int64_t n, int b, int c_dtype, P
       if (tc) xt = ttr::tc_proj_scratch_bytes(m, b, b <= 32 ? 1 : 0);
       break;
     case TT_PASS_GRAM:
-      if (m > 128) return fail(TT_EUNSUPPORTED, "Gram pass needs m <= 128");
-      part = tc ? ttr::tc_gram_partials(m, n) : ttr::simt_gram_partials(m, n);
+      if (m > 2048) return fail(TT_EUNSUPPORTED, "Gram pass needs m <= 2048");
+      if (m > 128) part = ttr::gram_tiled_partials(m, n, c_dtype == TT_BF16 ? 1 : 0);
+      else part = tc ? ttr::tc_gram_partials(m, n) : ttr::simt_gram_partials(m, n);
       break;
     default:
       return fail(TT_EINVAL, "unknown op");
@@ -848,11 +833,21 @@ tt_status tt_pass(int op, const void* C, int c_dtype, int64_t m, int64_t n, int 
       }
       break;
     case TT_PASS_GRAM:
-      if (L.tc) TTR_CUDA(ttr::tc_gram(Cb, m, n, part, (float*)y, status, st));
+      if (m > 128) TTR_CUDA(ttr::gram_tiled(C, bf ? 1 : 0, m, n, part, (float*)y, status, st));
+      else if (L.tc) TTR_CUDA(ttr::tc_gram(Cb, m, n, part, (float*)y, status, st));
       else if (bf) TTR_CUDA(ttr::simt_gram<__nv_bfloat16>(Cb, m, n, part, (float*)y, st));
       else TTR_CUDA(ttr::simt_gram<float>((const float*)C, m, n, part, (float*)y, st));
       break;
   }
+  return TT_OK;
+}
+
+tt_status tt_gram_power(const float* G, int64_t m, const float* X, int64_t ldx, int c, float* W, int64_t ldw,
+                        void* stream) {
+  if (!G || !X || !W) return fail(TT_EINVAL, "NULL argument");
+  if (m < 1 || c < 1 || ldx < c || ldw < c) return fail(TT_EINVAL, "bad shape");
+  if (!ttr::gram_power_ok(m, c)) return fail(TT_EUNSUPPORTED, "c must be <= 64");
+  TTR_CUDA(ttr::gram_power(G, m, X, ldx, c, W, ldw, (cudaStream_t)stream));
   return TT_OK;
 }
 
@@ -905,10 +900,6 @@ tt_status tt_rbki_batched_graph_create(int count, const tt_problem* problems, vo
   if (s != TT_OK) return s;
   s = check_batch_ws(L, workspace, ws_bytes);
   if (s != TT_OK) return s;
-  for (const Plan& P : L.plans) {
-    s = ensure_blas(P);
-    if (s != TT_OK) return s;
-  }
   cudaStream_t cs;
   TTR_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   cudaGraph_t g = nullptr;

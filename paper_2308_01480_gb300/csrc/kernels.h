@@ -92,13 +92,18 @@ bool orth_cluster_ok(int64_t m, int kq, int b);
 cudaError_t launch_orth_cluster(const float* W, int64_t ldw, int64_t m, int b, int c, float* Q, int64_t ldq, int kq,
                                 int* flag, cudaStream_t st);
 
-// ---- plain GEMMs through cuBLAS (blas.cu): the Gram-power route
-constexpr size_t kBlasWorkspace = size_t(32) << 20;
-cudaError_t blas_init();
-cudaError_t blas_gram(const void* C, int c_bf16, int64_t m, int64_t n, float* G, void* ws, size_t ws_bytes,
-                      cudaStream_t st);
-cudaError_t blas_gram_apply(const float* G, int64_t m, const float* X, int64_t ldx, int c, float* W, int64_t ldw,
-                            void* ws, size_t ws_bytes, cudaStream_t st);
+// ---- Gram matrix for 128 < m <= 2048 and the Gram power W = G X (gram.cu)
+bool gram_tiled_ok(int64_t m);
+bool gram_tc_tiled_ok(int64_t m, int64_t n);
+size_t gram_tiled_partials(int64_t m, int64_t n, int c_bf16);   // floats
+// G (m x m, FP32, both triangles) = C C^T; C BF16 (tensor cores when
+// tc_shape_ok) or FP32 (SIMT)
+cudaError_t gram_tiled(const void* C, int c_bf16, int64_t m, int64_t n, float* partials, float* G, int* status,
+                       cudaStream_t st);
+bool gram_power_ok(int64_t m, int c);
+// W (m x c, row stride ldw) = G X, G m x m FP32, X m x c (row stride ldx)
+cudaError_t gram_power(const float* G, int64_t m, const float* X, int64_t ldx, int c, float* W, int64_t ldw,
+                       cudaStream_t st);
 
 // ---- register-tiled symmetric eigensolver, k <= 160, r <= 32 (eig_reg.cu)
 bool eig_reg_ok(int k, int r);

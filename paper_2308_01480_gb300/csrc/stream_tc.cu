@@ -106,10 +106,15 @@ k_tc_stream(const __grid_constant__ CUtensorMap mapC, const __grid_constant__ CU
   // tiles handled by this CTA: cta_in_group, + ctas_in_group, ...
   const int64_t my_tiles =
       (p.tiles > cta_in_group) ? (p.tiles - cta_in_group + ctas_in_group - 1) / ctas_in_group : 0;
+  // gram: two accumulation buffers of npad columns (see the MMA issuer)
+  const int acc_cols = (OP == OPK_GRAM) ? 2 * p.npad : p.mb * p.npad;
   const uint32_t tmem_cols = (OP == OPK_PROJ) ? 128u
                             : (OP == OPK_GA ? (128 + p.mb * p.npad <= 256 ? 256u : 512u)
-                                            : (p.mb * p.npad <= 32 ? 32u : p.mb * p.npad <= 64 ? 64u
-                                               : p.mb * p.npad <= 128 ? 128u : 256u));
+                                            : (acc_cols <= 32 ? 32u : acc_cols <= 64 ? 64u
+                                               : acc_cols <= 128 ? 128u : 256u));
+  // gram: column tiles per TMEM accumulation chunk (16 or 32 MMAs)
+  const int gram_ck = (p.kb >= 8) ? 1 : 2;
+  const int64_t gram_chunks = (my_tiles + gram_ck - 1) / gram_ck;
   const bool ga_tall = (OP == OPK_GA) && p.nchunks > 1;
 
   if (threadIdx.x == 0) {
@@ -218,23 +223,36 @@ k_tc_stream(const __grid_constant__ CUtensorMap mapC, const __grid_constant__ CU
       const DescGen gT(ring_s, 128, 2048, SW_NONE);
       const uint32_t xres_off = (uint32_t)(xres - ring), tbuf_off = (uint32_t)(tbuf - ring);
       if (OP == OPK_GRAM) {
+        // The tensor cores' FP32 accumulation does not round to nearest, so
+        // its error grows with the MMAs added into one accumulator: the
+        // tiles go in chunks of gram_ck into two alternating TMEM buffers
+        // (dfull / dempty), and the epilogue adds each chunk into FP32
+        // registers with round-to-nearest while the next chunk accumulates.
         const uint32_t idesc = idesc_bf16(128, p.npad, 0, 0);
-        for (int64_t it = 0; it < my_tiles && ok; ++it, ++fill) {
-          const int s = (int)(fill % S);
-          if (!mbar_wait(&sh->full[s], (uint32_t)((fill / S) & 1), abortp)) { tc_abort(sh, p.status); ok = false; break; }
+        for (int64_t c = 0; c < gram_chunks && ok; ++c) {
+          const int buf = (int)(c & 1);
+          if (!mbar_wait(&sh->dempty[buf], (uint32_t)(((c >> 1) & 1) ^ 1), abortp)) { tc_abort(sh, p.status); ok = false; break; }
           tc_fence_after();
-          const uint32_t soff = (uint32_t)s * (uint32_t)p.stage_bytes;
-          for (int kb = 0; kb < p.kb; ++kb) {
-            const uint32_t boff = soff + (uint32_t)(kb * p.c_box_bytes);
+          const uint32_t d = tmem + (uint32_t)(buf * p.npad);
+          const int64_t ite = imin(my_tiles, (c + 1) * gram_ck);
+          for (int64_t it = c * gram_ck; it < ite; ++it, ++fill) {
+            const int s = (int)(fill % S);
+            if (!mbar_wait(&sh->full[s], (uint32_t)((fill / S) & 1), abortp)) { tc_abort(sh, p.status); ok = false; break; }
+            tc_fence_after();
+            const uint32_t soff = (uint32_t)s * (uint32_t)p.stage_bytes;
+            const bool first = it == c * gram_ck;
+            for (int kb = 0; kb < p.kb; ++kb) {
+              const uint32_t boff = soff + (uint32_t)(kb * p.c_box_bytes);
 #pragma unroll
-            for (int k4 = 0; k4 < 4; ++k4) {
-              const uint64_t da = gK.at(boff + k4 * 32);
-              mma_bf16(tmem, da, da, idesc, (it > 0 || kb > 0 || k4 > 0) ? 1u : 0u);
+              for (int k4 = 0; k4 < 4; ++k4) {
+                const uint64_t da = gK.at(boff + k4 * 32);
+                mma_bf16(d, da, da, idesc, (!first || kb > 0 || k4 > 0) ? 1u : 0u);
+              }
             }
+            mma_commit(&sh->empty[s]);
           }
-          mma_commit(&sh->empty[s]);
+          mma_commit(&sh->dfull[buf]);
         }
-        mma_commit(&sh->zfull);
       } else if (OP == OPK_CS) {
         const uint32_t idesc = idesc_bf16(128, p.npad, 0, 0);
         for (int64_t it = 0; it < my_tiles && ok; ++it, ++fill) {
@@ -531,15 +549,46 @@ k_tc_stream(const __grid_constant__ CUtensorMap mapC, const __grid_constant__ CU
         }
       }
     }
-    if (OP != OPK_PROJ) {
+    if (OP == OPK_GRAM) {
+      // chunk sums of this lane's row (npad <= 128 columns) added in FP32
+      float acc[128];
+#pragma unroll
+      for (int i = 0; i < 128; ++i) acc[i] = 0.f;
+      bool ok = true;
+      for (int64_t c = 0; c < gram_chunks; ++c) {
+        const int buf = (int)(c & 1);
+        if (!mbar_wait(&sh->dfull[buf], (uint32_t)((c >> 1) & 1), abortp)) { tc_abort(sh, p.status); ok = false; break; }
+        tc_fence_after();
+        const uint32_t ta = tmem + lane_addr + (uint32_t)(buf * p.npad);
+#pragma unroll
+        for (int g = 0; g < 8; ++g) {
+          if (g * 16 < p.npad) {
+            uint32_t r[16];
+            tmem_ld16<0>(ta + (uint32_t)(g * 16), r);
+            tmem_wait_ld();
+#pragma unroll
+            for (int t = 0; t < 16; ++t) acc[g * 16 + t] += __uint_as_float(r[t]);
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sh->dempty[buf]);
+      }
+      if (ok && !*abortp && lrow < p.m) {
+        float* P = reinterpret_cast<float*>(p.out) + (int64_t)blockIdx.x * p.m * p.m + (int64_t)lrow * p.m;
+#pragma unroll
+        for (int i = 0; i < 128; ++i)
+          if (i < p.m) P[i] = acc[i];
+      }
+    } else if (OP != OPK_PROJ) {
       // final accumulators -> per-CTA partials (rows of this CTA, FP32),
       // 16 columns at a time
       if (mbar_wait(&sh->zfull, 0, abortp)) {
         tc_fence_after();
         float* P = reinterpret_cast<float*>(p.out) + (int64_t)blockIdx.x * p.m * p.b;
-        const int mbn = (OP == OPK_GRAM) ? 1 : p.mb;
+        const int mbn = p.mb;
         const uint32_t zoff = (OP == OPK_GA) ? 128u : 0u;
-        const int ncol = (OP == OPK_GRAM) ? (int)p.m : p.b;
+        const int ncol = p.b;
         for (int b = 0; b < mbn; ++b) {
           const int64_t row = row0 + (int64_t)b * 128 + lrow;
           for (int c0 = 0; c0 < p.npad; c0 += 16) {

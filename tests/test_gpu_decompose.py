@@ -134,7 +134,7 @@ def test_fp32_power_routes_match_oracle(tt, case, gram_power):
     fams = tt.profile_end()
     assert oracle.tt_distance(got, ref) <= FP32_TOL
     if not gram_power:
-        assert "gram_power" not in fams and "gram_blas" not in fams
+        assert "gram_power" not in fams and "gram_tc_tiled" not in fams and "gram_simt_tiled" not in fams
 
 
 @pytest.mark.parametrize("case", CASES_TC)

@@ -171,7 +171,50 @@ def test_pass_gram(tt, m, n, bf16):
     assert np.max(np.abs(_host64(y) - ref)) <= 1e-5 * np.max(bound)
 
 
+def _gram_ref64(C):
+    """FP64 Gram of the stored values and its |.| bound, on the device."""
+    c = C.double()
+    return c @ c.T, c.abs() @ c.abs().T
+
+
+# 128 < m <= 2048: 128 x 256 tensor-core tiles (BF16, n % 8 == 0), SIMT
+# 64 x 64 tiles otherwise; ragged in m against both tile grids and in n
+# against the 64-column k-boxes and the split ranges
+@pytest.mark.parametrize("m,n", [(129, 64), (200, 1000), (256, 2048), (257, 4104), (300, 777), (511, 520),
+                                 (800, 1600), (800, 6400), (1024, 1032), (1500, 2000), (2048, 4096),
+                                 (2048, 96), (640, 65), (1111, 8200)])
+@pytest.mark.parametrize("bf16", [False, True])
+def test_pass_gram_tiled(tt, m, n, bf16):
+    C = _as_dev(_rand((m, n), 11), bf16)
+    tt.profile_begin(event_timing=False)
+    y = tt.tt_pass(tt.TT_PASS_GRAM, C)
+    fams = tt.profile_end()
+    ref, bound = _gram_ref64(C)
+    err = (y.double() - ref).abs().max().item()
+    assert err <= 1e-5 * bound.max().item()
+    assert torch.equal(y, y.T)                       # both triangles from the same sums
+    fam = "gram_tc_tiled" if _tc_path(n, bf16) else "gram_simt_tiled"
+    assert fam in fams, fams
+    assert torch.equal(tt.tt_pass(tt.TT_PASS_GRAM, C), y)   # fixed-order reduction
+
+
+@pytest.mark.parametrize("m,c", [(1, 1), (17, 5), (200, 30), (800, 30), (801, 13), (1024, 64), (1537, 40),
+                                 (2048, 32), (130, 63)])
+def test_gram_power(tt, m, c):
+    g = torch.Generator(device="cpu").manual_seed(m + c)
+    A = torch.randn(m, m + 3, generator=g)
+    G = (A @ A.T).float().cuda()
+    X = torch.randn(m, c + 7, generator=g).cuda()[:, 2:2 + c]     # row stride c + 7
+    W = tt.gram_power(G, X)
+    ref = G.double() @ X.double()
+    bound = G.double().abs() @ X.double().abs()
+    assert (W.double() - ref).abs().max().item() <= 1e-5 * bound.max().item()
+    assert torch.equal(tt.gram_power(G, X), W)
+
+
 def test_pass_rejects_unsupported(tt):
-    C = torch.zeros((200, 10), device="cuda")
+    C = torch.zeros((2049, 10), device="cuda")
     with pytest.raises(tt.TTError):
         tt.tt_pass(tt.TT_PASS_GRAM, C)
+    with pytest.raises(tt.TTError):
+        tt.gram_power(torch.zeros((8, 8), device="cuda"), torch.zeros((8, 65), device="cuda"))
