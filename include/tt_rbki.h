@@ -342,11 +342,14 @@ TT_API tt_status tt_pass(int op, const void* C, int c_dtype, int64_t m, int64_t 
  * One Krylov power through a formed Gram matrix (Alg. 3 step 4 on the
  * Gram-power route): W = G X.
  *   G      device, m x m float32 row-major, symmetric (G = C C^T).
- *   X      device, m x c float32, row stride ldx >= c; 1 <= c <= 64.
+ *   X      device, m x c float32, 16-byte aligned, row stride ldx a
+ *          multiple of 4 with ldx >= c rounded up to 4 (columns past c are
+ *          read but do not affect W); 1 <= c <= 64.
  *   W      device, m x c float32, row stride ldw >= c, written; must not
  *          overlap X or G.
  * FP32 products with FP32 accumulation in a fixed order (bit-reproducible).
- * Allocates nothing.  Errors: TT_EINVAL, TT_EUNSUPPORTED (c > 64), TT_ECUDA.
+ * Allocates nothing.  Errors: TT_EINVAL (including a misaligned X),
+ * TT_EUNSUPPORTED (c > 64), TT_ECUDA.
  */
 TT_API tt_status tt_gram_power(const float* G, int64_t m, const float* X, int64_t ldx, int c, float* W,
                                int64_t ldw, void* stream);

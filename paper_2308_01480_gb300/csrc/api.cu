@@ -51,7 +51,7 @@ struct Plan {
   std::vector<ModePlan> modes;
   // workspace offsets in bytes
   size_t off_status = 0, off_R0 = 0, off_R1 = 0, off_S = 0, off_T = 0, off_part = 0, off_Y = 0,
-         off_Q = 0, off_W = 0, off_U = 0, off_G = 0, off_small = 0, off_X = 0, total = 0;
+         off_Q = 0, off_W = 0, off_U = 0, off_G = 0, off_small = 0, off_X = 0, off_Xg = 0, total = 0;
 };
 
 tt_status resolve_options(const tt_options* in, tt_options* out) {
@@ -109,7 +109,7 @@ tt_status build_plan(const int64_t* dims, int d, const int64_t* ranks, int p, in
   for (int k = 0; k < d; ++k) total *= dims[k];
   int64_t n = total;
   size_t maxR = 0, maxS = 0, maxT = 0, maxPart = 0, maxY = 0, maxQ = 0, maxU = 0, maxG = 0, maxSmall = 0,
-         maxX = 0;
+         maxX = 0, maxXg = 0;
   for (int k = 0; k < d - 1; ++k) {
     ModePlan& M = P.modes[k];
     n /= dims[k];
@@ -197,6 +197,8 @@ tt_status build_plan(const int64_t* dims, int d, const int64_t* ranks, int p, in
     if (M.gram_power) {
       maxG = std::max(maxG, (size_t)(M.m * M.m));
       maxPart = std::max(maxPart, ttr::gram_tiled_partials(M.m, M.n, cdt == TT_BF16 ? 1 : 0));
+      // padded copy of the current block for the power
+      maxXg = std::max(maxXg, (size_t)M.m * (size_t)((M.b + 3) & ~3));
     }
   }
   size_t off = 0;
@@ -214,6 +216,7 @@ tt_status build_plan(const int64_t* dims, int d, const int64_t* ranks, int p, in
   P.off_G = take(maxG * 4);
   P.off_small = take(maxSmall * 4);
   P.off_X = take(maxX);
+  P.off_Xg = take(maxXg * 4);
   P.total = off;
   return TT_OK;
 }
@@ -286,7 +289,22 @@ tt_status run_mode(const Plan& P, int k, const TIn* C, char* ws, int* status, co
     // orthonormalise a block: cluster (or multi-CTA) CholeskyQR path with
     // the one-CTA robust path as fallback, run only if the fast path flagged
     // a breakdown; the one-CTA path alone for shapes neither fast path takes
+    // the block just appended, padded and 16-byte aligned, for the power
+    float* Xg = (float*)(ws + P.off_Xg);
+    const int xld = (M.b + 3) & ~3;
+    bool xg_written = false;
     auto orth = [&](const float* Z, int64_t ldz, int zc, int kq0, int c, uint64_t sd) -> tt_status {
+      xg_written = false;
+      if (ttr::orth_cluster_rs_ok(M.m, kq0, zc, c)) {
+        // one cluster launch, rank-deficient columns repaired inside
+        const cudaError_t e = ttr::launch_orth_cluster_rs(Z, ldz, zc, M.m, c, kq0, Q, kq, M.gram_power ? Xg : nullptr,
+                                                          xld, sd, status, st);
+        if (e == cudaSuccess) {
+          xg_written = M.gram_power;
+          return TT_OK;
+        }
+        if (e != cudaErrorNotSupported) TTR_CUDA(e);
+      }
       if (ttr::orth_cluster_ok(M.m, kq0, zc)) {
         TTR_CUDA(ttr::launch_orth_cluster(Z, ldz, M.m, zc, c, Q, kq, kq0, flag, st));
         TTR_CUDA(ttr::launch_orth_block(Z, ldz, M.m, zc, Q, kq, kq0, c, small, sd, status, flag, st));
@@ -303,7 +321,10 @@ tt_status run_mode(const Plan& P, int k, const TIn* C, char* ws, int* status, co
     // one power: Wj = C C^T Xj (cj columns; row stride kq for both)
     auto power = [&](const float* Xj, float* Wj, int cj) -> tt_status {
       if (M.gram_power) {
-        TTR_CUDA(ttr::gram_power(Gp, M.m, Xj, kq, cj, Wj, kq, st));
+        if (!xg_written)   // the block lives only in Q: pack it
+          TTR_CUDA(cudaMemcpy2DAsync(Xg, sizeof(float) * xld, Xj, sizeof(float) * kq, sizeof(float) * cj, M.m,
+                                     cudaMemcpyDeviceToDevice, st));
+        TTR_CUDA(ttr::gram_power(Gp, M.m, Xg, xld, cj, Wj, kq, st));
       } else if (use_tc) {
         if (ttr::tc_ga_ok(M.m, M.n, cj)) {
           TTR_CUDA(ttr::tc_ga(Cb, M.m, M.n, Xj, kq, cj, part, Wj, kq, xs, status, st));
@@ -845,7 +866,8 @@ tt_status tt_pass(int op, const void* C, int c_dtype, int64_t m, int64_t n, int 
 tt_status tt_gram_power(const float* G, int64_t m, const float* X, int64_t ldx, int c, float* W, int64_t ldw,
                         void* stream) {
   if (!G || !X || !W) return fail(TT_EINVAL, "NULL argument");
-  if (m < 1 || c < 1 || ldx < c || ldw < c) return fail(TT_EINVAL, "bad shape");
+  if (m < 1 || c < 1 || ldx < ((c + 3) & ~3) || ldw < c) return fail(TT_EINVAL, "bad shape");
+  if (ldx % 4 != 0 || ((uintptr_t)X & 15) != 0) return fail(TT_EINVAL, "X must be 16-byte aligned with ldx % 4 == 0");
   if (!ttr::gram_power_ok(m, c)) return fail(TT_EUNSUPPORTED, "c must be <= 64");
   TTR_CUDA(ttr::gram_power(G, m, X, ldx, c, W, ldw, (cudaStream_t)stream));
   return TT_OK;

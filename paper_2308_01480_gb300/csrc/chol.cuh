@@ -15,13 +15,14 @@ namespace ttr {
 // One barrier per column: row j of R is formed from the unscaled row j of G
 // while the trailing block (rows and columns > j) is updated in place.
 __device__ inline void chol_inv_cta(float* G, int ldg, int b, const float* diag0, float* R, int ldr, float* T,
-                                    int ldt, int* flag, bool report) {
+                                    int ldt, int* flag, bool report, unsigned long long* badmask = nullptr) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
   __syncthreads();
   for (int j = 0; j < b; ++j) {
     float dj = G[j * ldg + j];
     if (!(dj > 1e-6f * diag0[j])) {
-      if (report && tid == 0) atomicExch(flag, 1);
+      if (report && tid == 0 && flag) atomicExch(flag, 1);
+      if (badmask && tid == 0) atomicOr(badmask, 1ull << j);
       dj = 1.f;
     }
     const float rj = sqrtf(dj), inv = 1.f / rj, inv2 = inv * inv;
@@ -71,7 +72,8 @@ __device__ inline void chol_inv_cta(float* G, int ldg, int b, const float* diag0
 // 1e-6 of diag0 (or non-positive) raises *flag when report and is replaced
 // by 1.  Callers use the out-of-line copy below.
 __device__ __forceinline__ void chol_inv_warp(const float* G, int ldg, int b, const float* diag0, float* R,
-                                                   int ldr, float* T, int ldt, int* flag, bool report) {
+                                                   int ldr, float* T, int ldt, int* flag, bool report,
+                                                   unsigned long long* badmask) {
   __shared__ __align__(16) float Rs[32][36];   // Rs[j][s] = R[j][j + 1 + s], zero past column b
   const unsigned full = 0xffffffffu;
   const int l = threadIdx.x & 31;
@@ -88,6 +90,7 @@ __device__ __forceinline__ void chol_inv_warp(const float* G, int ldg, int b, co
     for (int i = 0; i < 32; ++i) a[i] = (i <= l && l < b) ? G[i * ldg + l] : 0.f;
     const float d0 = (l < b) ? diag0[l] : 1.f;
     bool bad = false;
+    unsigned long long badbits = 0ull;
     __syncwarp();
 #pragma unroll 1
     for (int j = 0; j < b; ++j) {
@@ -95,6 +98,7 @@ __device__ __forceinline__ void chol_inv_warp(const float* G, int ldg, int b, co
       const float dref = __shfl_sync(full, d0, j);
       if (!(djj > 1e-6f * dref)) {
         bad = true;
+        badbits |= 1ull << j;
         djj = 1.f;
       }
       const float inv = rsqrtf(djj);
@@ -117,7 +121,8 @@ __device__ __forceinline__ void chol_inv_warp(const float* G, int ldg, int b, co
       }
       a[31] = 0.f;
     }
-    if (report && bad && l == 0) atomicExch(flag, 1);
+    if (report && bad && l == 0 && flag) atomicExch(flag, 1);
+    if (badmask && badbits && l == 0) atomicOr(badmask, badbits);
   }
   __syncwarp();
   // T[i][l] = (delta_il - sum_{k > i} R[i][k] T[k][l]) / R[i][i], i = b-1 .. 0
@@ -156,16 +161,18 @@ __device__ __forceinline__ void chol_inv_warp(const float* G, int ldg, int b, co
 
 // Out-of-line copy (one per kernel, its own register allocation).
 static __device__ __noinline__ void chol_inv_warp_ool(const float* G, int ldg, int b, const float* diag0, float* R,
-                                                       int ldr, float* T, int ldt, int* flag, bool report) {
-  chol_inv_warp(G, ldg, b, diag0, R, ldr, T, ldt, flag, report);
+                                                       int ldr, float* T, int ldt, int* flag, bool report,
+                                                       unsigned long long* badmask) {
+  chol_inv_warp(G, ldg, b, diag0, R, ldr, T, ldt, flag, report, badmask);
 }
 
 // chol_inv_cta's contract for b <= 32: the CTA synchronises, warp 0 alone
 // factors (the other warps do not enter the call), the CTA synchronises.
 __device__ __forceinline__ void chol_inv_warp32_call(const float* G, int ldg, int b, const float* diag0, float* R,
-                                                     int ldr, float* T, int ldt, int* flag, bool report) {
+                                                     int ldr, float* T, int ldt, int* flag, bool report,
+                                                     unsigned long long* badmask = nullptr) {
   __syncthreads();
-  if (threadIdx.x < 32) chol_inv_warp_ool(G, ldg, b, diag0, R, ldr, T, ldt, flag, report);
+  if (threadIdx.x < 32) chol_inv_warp_ool(G, ldg, b, diag0, R, ldr, T, ldt, flag, report, badmask);
   __syncthreads();
 }
 
@@ -179,7 +186,7 @@ __device__ __forceinline__ void chol_inv_warp32_call(const float* G, int ldg, in
 // 1e-6 of its original diagonal (or non-positive) raises *flag when report.
 __device__ inline void pchol_select_cta(float* G, int ldg, int b, int c, const float* diag0, float* R, int ldr,
                                         float* Tf, int ldt, int bt, int* perm, float* dsw, int* flag,
-                                        bool report) {
+                                        bool report, unsigned long long* badmask = nullptr) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
   __shared__ int s_piv;
   for (int i = tid; i < b; i += blockDim.x) {
@@ -221,7 +228,8 @@ __device__ inline void pchol_select_cta(float* G, int ldg, int b, int c, const f
     }
     float dj = G[j * ldg + j];
     if (!(dj > 1e-6f * dsw[j])) {
-      if (report && tid == 0) atomicExch(flag, 1);
+      if (report && tid == 0 && flag) atomicExch(flag, 1);
+      if (badmask && tid == 0) atomicOr(badmask, 1ull << j);
       dj = 1.f;
     }
     const float rj = sqrtf(dj), inv = 1.f / rj, inv2 = inv * inv;

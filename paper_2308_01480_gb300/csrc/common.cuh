@@ -27,6 +27,17 @@ __device__ __forceinline__ void st_elem(__nv_bfloat16* p, int64_t i, float v) {
   p[i] = __float2bfloat16_rn(v);
 }
 
+// Deterministic pseudo-random value in [-1, 1) from two 64-bit words (a
+// SplitMix64-style finaliser), for replacing numerically vanished basis
+// columns by directions that carry no information of their own.
+__device__ __forceinline__ float hash_uniform(uint64_t a, uint64_t b) {
+  uint64_t z = a * 0x9E3779B97F4A7C15ull + b + 0x632BE59BD9B4E019ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (float)(z >> 40) * (1.0f / 8388608.0f) - 1.0f;
+}
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -19,9 +19,10 @@
 // 64 x 64 upper-triangular tiles with 4 x 4 register tiles, split-K, the same
 // fixed-order reduction.
 //
-// Power: W (m x c) = G X, FP32, 16 rows of W per CTA, K in 128-wide chunks
-// double-buffered by asynchronous copies, a 2 x 4 register tile per thread
-// and a fixed-order sum over the CTA's K groups.
+// Power: W (m x c) = G X, FP32, X a 16-byte-aligned padded block; 8 rows of
+// W per CTA over many CTAs, four 128-row K chunks in flight by 16-byte
+// asynchronous copies, 2 x 4 register tiles, a fixed-order sum over the
+// CTA's K groups.
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -407,12 +408,19 @@ void gs_plan(int64_t m, int64_t n, int* tiles, int* splits) {
 }
 
 // ------------------------------------------------------------ power W = G X
-constexpr int GP_RB = 16;     // rows of W per CTA
+// X is a padded block (m x ldx, ldx % 4 == 0, 16-byte aligned), so both
+// operands arrive by 16-byte asynchronous copies, GP_ST chunks of 128 rows of
+// K in flight (the work per SM is small and latency decides it).  Each CTA
+// owns 8 rows of W; a thread owns a 2 x 4 tile and one of KG groups that
+// split each chunk, summed in group order at the end (fixed order).
+constexpr int GP_RB = 8;      // rows of W per CTA
 constexpr int GP_KC = 128;    // K chunk
+constexpr int GP_ST = 4;      // chunks in flight
+constexpr int GP_GLD = GP_KC + 4;
 
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+__device__ __forceinline__ void cp_async16z(void* dst, const void* src, bool ok) {
   const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(ok ? 16 : 0) : "memory");
 }
 __device__ __forceinline__ void cp_async4z(float* dst, const float* src, bool ok) {
   const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
@@ -422,76 +430,66 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// Thread layout: tile (rp, cq) = rows 2 rp, 2 rp + 1 and columns 4 cq..4 cq + 3
-// of the CTA's 16 x CP block; ntiles = 8 * CP / 4 tiles, KG = 256 / ntiles
-// K groups, group g taking chunk columns g, g + KG, ...
 __global__ void __launch_bounds__(256) k_gram_power(const float* __restrict__ G, int64_t m,
                                                     const float* __restrict__ X, int64_t ldx, int c,
                                                     float* __restrict__ W, int64_t ldw) {
   extern __shared__ __align__(16) float gp_sm[];
   const int CP = (c + 3) & ~3;
-  float* Gs = gp_sm;                                 // [2][GP_RB][GP_KC]
-  float* Xs = Gs + 2 * GP_RB * GP_KC;                // [2][GP_KC][CP]
-  float* Rd = Xs + 2 * GP_KC * CP;                   // [KG][GP_RB][CP]
-  const int64_t r0 = (int64_t)blockIdx.x * GP_RB;
-  const int ntl = 8 * (CP / 4);
+  const int tcq = CP / 4, ntl = (GP_RB / 2) * tcq;
   const int KG = 256 / ntl;
+  float* Gs = gp_sm;                                  // [GP_ST][GP_RB][GP_GLD]
+  float* Xs = Gs + GP_ST * GP_RB * GP_GLD;            // [GP_ST][GP_KC][CP]
+  float* Rd = Xs + GP_ST * GP_KC * CP;                // [KG][GP_RB][CP]
+  const int64_t r0 = (int64_t)blockIdx.x * GP_RB;
   const int tid = threadIdx.x;
   const int tl = tid % ntl, g = tid / ntl;
-  const int rp = tl / (CP / 4), cq = tl % (CP / 4);
+  const int rp = tl / tcq, cq = tl % tcq;
   const bool active = g < KG;
   const int64_t nchunks = ceil_div(m, GP_KC);
-  const bool gvec = (m % 4) == 0;
+  const bool gvec = (m % 4) == 0 && (reinterpret_cast<uintptr_t>(G) % 16) == 0;
   auto load = [&](int64_t ch, int buf) {
     const int64_t k0 = ch * GP_KC;
-    float* gs = Gs + buf * GP_RB * GP_KC;
+    float* gs = Gs + buf * GP_RB * GP_GLD;
     float* xs = Xs + buf * GP_KC * CP;
     if (gvec) {
-      for (int e = tid; e < GP_RB * GP_KC / 4; e += 256) {
+      for (int e = tid; e < GP_RB * (GP_KC / 4); e += 256) {
         const int r = e / (GP_KC / 4), k4 = (e % (GP_KC / 4)) * 4;
-        const int64_t row = r0 + r, col = k0 + k4;
-        if (row < m && col + 3 < m) {
-          cp_async16(gs + r * GP_KC + k4, G + row * m + col);
-        } else {
-          for (int u = 0; u < 4; ++u) {
-            const bool ok = row < m && col + u < m;
-            cp_async4z(gs + r * GP_KC + k4 + u, ok ? G + row * m + col + u : G, ok);
-          }
-        }
+        const bool ok = r0 + r < m && k0 + k4 < m;   // m % 4 == 0: all four or none
+        cp_async16z(gs + r * GP_GLD + k4, ok ? G + (r0 + r) * m + k0 + k4 : G, ok);
       }
     } else {
       for (int e = tid; e < GP_RB * GP_KC; e += 256) {
         const int r = e / GP_KC, kk = e % GP_KC;
-        const int64_t row = r0 + r, col = k0 + kk;
-        const bool ok = row < m && col < m;
-        cp_async4z(gs + r * GP_KC + kk, ok ? G + row * m + col : G, ok);
+        const bool ok = r0 + r < m && k0 + kk < m;
+        cp_async4z(gs + r * GP_GLD + kk, ok ? G + (r0 + r) * m + k0 + kk : G, ok);
       }
     }
-    for (int e = tid; e < GP_KC * CP; e += 256) {
-      const int kk = e / CP, j = e % CP;
-      const int64_t row = k0 + kk;
-      const bool ok = row < m && j < c;
-      cp_async4z(xs + kk * CP + j, ok ? X + row * ldx + j : X, ok);
+    for (int e = tid; e < GP_KC * tcq; e += 256) {
+      const int kk = e / tcq, j4 = (e % tcq) * 4;
+      const bool ok = k0 + kk < m;
+      cp_async16z(xs + kk * CP + j4, ok ? X + (k0 + kk) * ldx + j4 : X, ok);
     }
     cp_commit();
   };
   float acc[2][4] = {};
-  load(0, 0);
+  for (int64_t ch = 0; ch < GP_ST - 1; ++ch) {
+    if (ch < nchunks) load(ch, (int)ch);
+    else cp_commit();
+  }
   for (int64_t ch = 0; ch < nchunks; ++ch) {
-    const int buf = (int)(ch & 1);
-    if (ch + 1 < nchunks) {
-      load(ch + 1, buf ^ 1);
-      cp_wait<1>();
-    } else {
-      cp_wait<0>();
-    }
+    const int buf = (int)(ch % GP_ST);
+    const int64_t nx = ch + GP_ST - 1;
+    if (nx < nchunks) load(nx, (int)(nx % GP_ST));
+    else cp_commit();
+    cp_wait<GP_ST - 1>();
     __syncthreads();
     if (active) {
-      const float* gs = Gs + buf * GP_RB * GP_KC;
-      const float* xs = Xs + buf * GP_KC * CP;
+      const float* gs = Gs + buf * GP_RB * GP_GLD + (2 * rp) * GP_GLD;
+      const float* xs = Xs + buf * GP_KC * CP + 4 * cq;
+#pragma unroll 4
       for (int kk = g; kk < GP_KC; kk += KG) {
-        const float4 x4 = *reinterpret_cast<const float4*>(xs + kk * CP + 4 * cq);
-        const float g0 = gs[(2 * rp) * GP_KC + kk], g1 = gs[(2 * rp + 1) * GP_KC + kk];
+        const float4 x4 = *reinterpret_cast<const float4*>(xs + kk * CP);
+        const float g0 = gs[kk], g1 = gs[GP_GLD + kk];
         acc[0][0] = fmaf(g0, x4.x, acc[0][0]); acc[0][1] = fmaf(g0, x4.y, acc[0][1]);
         acc[0][2] = fmaf(g0, x4.z, acc[0][2]); acc[0][3] = fmaf(g0, x4.w, acc[0][3]);
         acc[1][0] = fmaf(g1, x4.x, acc[1][0]); acc[1][1] = fmaf(g1, x4.y, acc[1][1]);
@@ -509,18 +507,17 @@ __global__ void __launch_bounds__(256) k_gram_power(const float* __restrict__ G,
   __syncthreads();
   for (int e = tid; e < GP_RB * c; e += 256) {
     const int r = e / c, j = e % c;
-    const int64_t row = r0 + r;
-    if (row >= m) continue;
+    if (r0 + r >= m) continue;
     float s = 0.f;
     for (int gg = 0; gg < KG; ++gg) s += Rd[((size_t)gg * GP_RB + r) * CP + j];
-    W[row * ldw + j] = s;
+    W[(r0 + r) * ldw + j] = s;
   }
 }
 
 size_t gp_smem_bytes(int c) {
   const int CP = (c + 3) & ~3;
-  const int KG = 256 / (8 * (CP / 4));
-  return sizeof(float) * ((size_t)2 * GP_RB * GP_KC + (size_t)2 * GP_KC * CP + (size_t)KG * GP_RB * CP);
+  const int KG = 256 / ((GP_RB / 2) * (CP / 4));
+  return sizeof(float) * ((size_t)GP_ST * GP_RB * GP_GLD + (size_t)GP_ST * GP_KC * CP + (size_t)KG * GP_RB * CP);
 }
 
 }  // namespace
@@ -585,11 +582,14 @@ cudaError_t gram_tiled(const void* C, int c_bf16, int64_t m, int64_t n, float* p
   return cudaGetLastError();
 }
 
-bool gram_power_ok(int64_t m, int c) { return m >= 1 && c >= 1 && c <= 64 && gp_smem_bytes(c) <= 227 * 1024; }
+bool gram_power_ok(int64_t m, int c) { return m >= 1 && c >= 1 && c <= 64; }
 
+// X must be 16-byte aligned with ldx % 4 == 0 (the caller's padded copy of
+// the block).
 cudaError_t gram_power(const float* G, int64_t m, const float* X, int64_t ldx, int c, float* W, int64_t ldw,
                        cudaStream_t st) {
-  if (!gram_power_ok(m, c)) return cudaErrorInvalidValue;
+  if (!gram_power_ok(m, c) || ldx % 4 != 0 || ldx < ((c + 3) & ~3) || reinterpret_cast<uintptr_t>(X) % 16 != 0)
+    return cudaErrorInvalidValue;
   const size_t smem = gp_smem_bytes(c);
   cudaError_t e = raise_smem_limit(k_gram_power);
   if (e != cudaSuccess) return e;

@@ -92,6 +92,16 @@ bool orth_cluster_ok(int64_t m, int kq, int b);
 cudaError_t launch_orth_cluster(const float* W, int64_t ldw, int64_t m, int b, int c, float* Q, int64_t ldq, int kq,
                                 int* flag, cudaStream_t st);
 
+// ---- one block on a cluster of up to 16 CTAs, reduce-scatter sums and
+// in-launch repair of deficient columns (orth_cluster_rs.cu): Y (m x zc,
+// row stride ldy) orthonormalised against Q[:, :kq0], c columns appended to
+// Q; when Xg is given the new block is also written there (m x xld, zero
+// padded to pad4(c) columns, 16-byte rows for the Gram power).  Returns
+// cudaErrorNotSupported when the device cannot hold the cluster.
+bool orth_cluster_rs_ok(int64_t m, int kq0, int zc, int c);
+cudaError_t launch_orth_cluster_rs(const float* Y, int64_t ldy, int zc, int64_t m, int c, int kq0, float* Q,
+                                   int64_t ldq, float* Xg, int xld, uint64_t seed, int* status, cudaStream_t st);
+
 // ---- Gram matrix for 128 < m <= 2048 and the Gram power W = G X (gram.cu)
 bool gram_tiled_ok(int64_t m);
 bool gram_tc_tiled_ok(int64_t m, int64_t n);
@@ -101,7 +111,8 @@ size_t gram_tiled_partials(int64_t m, int64_t n, int c_bf16);   // floats
 cudaError_t gram_tiled(const void* C, int c_bf16, int64_t m, int64_t n, float* partials, float* G, int* status,
                        cudaStream_t st);
 bool gram_power_ok(int64_t m, int c);
-// W (m x c, row stride ldw) = G X, G m x m FP32, X m x c (row stride ldx)
+// W (m x c, row stride ldw) = G X, G m x m FP32, X m x c, 16-byte aligned
+// with row stride ldx % 4 == 0 (a padded copy of the block)
 cudaError_t gram_power(const float* G, int64_t m, const float* X, int64_t ldx, int c, float* W, int64_t ldw,
                        cudaStream_t st);
 

@@ -13,14 +13,6 @@ namespace ttr {
 constexpr int SMALL_THREADS = 1024;
 
 // ------------------------------------------------------------ helpers
-// Deterministic replacement vector entry in [-1, 1) (splitmix64 finaliser).
-__device__ __forceinline__ float hash_uniform(uint64_t a, uint64_t b) {
-  uint64_t z = a * 0x9E3779B97F4A7C15ull + b + 0x632BE59BD9B4E019ull;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  z ^= z >> 31;
-  return (float)(z >> 40) * (1.0f / 8388608.0f) - 1.0f;
-}
 
 // coef[t] = sum_i B[i*ldb + t] v[i] for t < nb; one warp per basis column.
 __device__ void dots_cols(const float* B, int64_t ldb, int nb, const float* v, int64_t m,

@@ -204,7 +204,8 @@ def test_gram_power(tt, m, c):
     g = torch.Generator(device="cpu").manual_seed(m + c)
     A = torch.randn(m, m + 3, generator=g)
     G = (A @ A.T).float().cuda()
-    X = torch.randn(m, c + 7, generator=g).cuda()[:, 2:2 + c]     # row stride c + 7
+    ld = (c + 3) // 4 * 4 + 4                  # padded rows, 16-byte aligned
+    X = torch.randn(m, ld, generator=g).cuda()[:, :c]
     W = tt.gram_power(G, X)
     ref = G.double() @ X.double()
     bound = G.double().abs() @ X.double().abs()
@@ -217,4 +218,6 @@ def test_pass_rejects_unsupported(tt):
     with pytest.raises(tt.TTError):
         tt.tt_pass(tt.TT_PASS_GRAM, C)
     with pytest.raises(tt.TTError):
-        tt.gram_power(torch.zeros((8, 8), device="cuda"), torch.zeros((8, 65), device="cuda"))
+        tt.gram_power(torch.zeros((8, 8), device="cuda"), torch.zeros((8, 68), device="cuda")[:, :65])
+    with pytest.raises(tt.TTError):        # rows not 16-byte aligned
+        tt.gram_power(torch.zeros((8, 8), device="cuda"), torch.zeros((8, 11), device="cuda")[:, :10])
