@@ -1,8 +1,9 @@
 // Top-r eigenpairs of the small symmetric Rayleigh-Ritz matrix (Alg. 3
 // steps 6-8), k <= 160, in two one-CTA kernels.  The first holds H in
-// registers: 32 warps, thread (warp w, lane l) owning the entries
-// (l + 32 a, w + 32 c), a, c < KT = ceil(k / 32).  The second (16 warps, so
-// that the register-resident Cholesky of step 4 fits) does steps 2-5.
+// registers: 8 warps, thread (warp w, lane l) owning the entries
+// (l + 32 a, w + 8 c), a < KT = ceil(k / 32), c < 4 KT.  The second (16
+// warps, so that the register-resident Cholesky of step 4 fits) does steps
+// 2-5.
 //
 //  1. Householder tridiagonalisation.  Per column two barriers: the warp
 //     owning column j forms the reflector v from its registers; each warp
@@ -166,153 +167,183 @@ __host__ __device__ inline size_t er_smem_floats(int KM, int k, int r) {
          3 * 33 * 32 + 8;
 }
 
-// Step 1 in one CTA of 32 warps: T = (d, e) and the reflectors (row j of
+// Sum over the 32 lanes of NV values x[0..NV) (NV a power of two <= 32) with
+// the transposing butterfly: at each level a lane keeps half of its values
+// and sends the other half, so after log2(NV) levels every lane holds one
+// partial sum; the remaining levels are plain butterflies.  Lane l ends with
+// the total of value (l >> (5 - log2 NV)).
+template <int NV>
+__device__ __forceinline__ float lane_transpose_sum(float (&x)[NV]) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  float cur[NV];
+  sfor<NV>([&](auto i) { cur[i] = x[i]; });
+  int n = NV, o = 16;
+  // levels that halve the value count (compile-time sizes via sfor)
+  sfor<5>([&](auto lvl) {
+    constexpr int L = decltype(lvl)::value;
+    constexpr int N = NV >> L;          // values held before this level
+    if constexpr (N >= 2) {
+      constexpr int H = N / 2;
+      const int off = 16 >> L;
+      const bool up = lane & off;
+      sfor<H>([&](auto i) {
+        const float send = up ? cur[i] : cur[i + H];
+        const float keep = up ? cur[i + H] : cur[i];
+        cur[i] = keep + __shfl_xor_sync(full, send, off);
+      });
+    } else {
+      const int off = 16 >> L;
+      cur[0] += __shfl_xor_sync(full, cur[0], off);
+    }
+  });
+  (void)n;
+  (void)o;
+  return cur[0];
+}
+
+// Step 1 in one CTA of 8 warps: T = (d, e) and the reflectors (row j of
 // Vg = v_j, tau[j]) to global scratch.  Thread (warp w, lane l) holds the
-// entries (l + 32 a, w + 32 c), a, c < KT, so that column j lives in warp
-// j mod 32 alone, and so does the dot product of any column with a vector
-// spread over the rows.  Per column two barriers:
+// entries (l + 32 a, w + 8 c), a < KR, c < 4 KR, so every column lives in one
+// warp and each thread carries 20 KR entries (the per-column reductions,
+// broadcasts and barriers are spread over many multiply-adds).  Per column
+// two barriers:
 //   R  the warp owning column j forms the reflector v (and tau) from its
 //      registers and publishes it;
-//   M  every warp forms (H v)_c for its columns c by a lane reduction
-//      (H is symmetric, so the column dot is the row product), scaled by
-//      tau, and its share of v^T H v;
+//   M  every warp forms tau (H v)_c for its columns c (H is symmetric, so the
+//      column dot is the row product) and its share of v^T H v, reduced over
+//      the lanes by one transposing butterfly;
 //   U  every thread applies H -= v w^T + w v^T, w = p - (tau/2)(v^T p) v,
-//      to its entries of the trailing block; the owner of column j + 1
-//      then goes straight on to its reflector.
-// Tiles lying wholly in finished rows or columns are skipped (at compile
-// time: the column loop is split into 32-column segments).
-template <int KT>
-__global__ void __launch_bounds__(1024, 1) k_eig_tridiag(const float* __restrict__ Hin, int64_t ldh, int k,
+//      to its entries of the trailing block.
+// Tiles of finished rows (32-row blocks) and columns (8-column slots) are
+// skipped at compile time: the column loop is split into 32-column segments.
+template <int KR>
+__global__ void __launch_bounds__(256, 1) k_eig_tridiag8(const float* __restrict__ Hin, int64_t ldh, int k,
                                                         float* __restrict__ Vg, float* __restrict__ tau_g,
                                                         float* __restrict__ d_g, float* __restrict__ e_g) {
-  constexpr int KM = 32 * KT;
+  constexpr int KC = 4 * KR;
+  constexpr int KM = 32 * KR;
+  constexpr int NV = (KC + 1 <= 8) ? 8 : (KC + 1 <= 16) ? 16 : 32;
   __shared__ __align__(16) float vs[KM];
   __shared__ __align__(16) float ps[KM];
-  __shared__ __align__(16) float wsum[32];
+  __shared__ float wsum[8];
   __shared__ float scal[2];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
 
-  float A[KT][KT];   // A[a][c] = H[lane + 32 a][w + 32 c]
-  sfor<KT>([&](auto a) {
-    sfor<KT>([&](auto c) {
-      const int i = lane + 32 * a, j = w + 32 * c;
+  float A[KR][KC];   // A[a][c] = H[lane + 32 a][w + 8 c]
+  sfor<KR>([&](auto a) {
+    sfor<KC>([&](auto c) {
+      const int i = lane + 32 * a, j = w + 8 * c;
       A[a][c] = (i < k && j < k) ? 0.5f * (Hin[(int64_t)i * ldh + j] + Hin[(int64_t)j * ldh + i]) : 0.f;
     });
   });
-  // rows k - 2 and k - 1 of Vg carry no reflector
   const int z0 = (k >= 2) ? (k - 2) * k : 0;
-  for (int x = z0 + tid; x < k * k; x += 1024) Vg[x] = 0.f;
-  // Columns 32 s .. 32 s + 31 form segment s: there the tiles a < s and
-  // c < s are finished (compile-time), so each segment is its own loop with
-  // only its live tiles.  (At the segment's last column tile s is finished
-  // too; it only adds exact zeros.)
-  sfor<KT>([&](auto seg) {
+  for (int x = z0 + tid; x < k * k; x += 256) Vg[x] = 0.f;
+  sfor<KR>([&](auto seg) {
     constexpr int S = decltype(seg)::value;
     const int jend = min(32 * S + 32, k - 2);
     for (int j = 32 * S; j < jend; ++j) {
-      // R: the reflector of column j, in the warp that owns the column
-      if (w == (j & 31)) {
+      // R: the reflector of column j (slot cj in warp j & 7)
+      if (w == (j & 7)) {
+        const int t = (j >> 3) - 4 * S;   // 0..3
+        float colv[KR];
+        sfor<KR>([&](auto a) {
+          float x = 0.f;
+          if constexpr (a >= S) {
+            sfor<4>([&](auto u) {
+              if constexpr (4 * S + u < KC)
+                if (t == u) x = A[a][4 * S + u];
+            });
+          }
+          colv[a] = x;
+        });
         float part = 0.f, sel = 0.f;
-        const bool next_seg = (j + 1) >> 5 != S;
-        sfor<KT>([&](auto a) {
-          if (a >= S) {
-            const float x = A[a][S];
+        const int a1 = (j + 1) >> 5;
+        sfor<KR>([&](auto a) {
+          if constexpr (a >= S) {
+            const float x = colv[a];
             const int i = lane + 32 * a;
             if (i >= j + 2 && i < k) part = fmaf(x, x, part);
-            if (a == S && !next_seg) sel = x;
-            if (a == S + 1 && next_seg) sel = x;
+            if (a == a1) sel = x;
             if (i == j) d_g[j] = x;
           }
         });
         const float sigma = warp_sum(part);
         const float x0 = __shfl_sync(0xffffffffu, sel, (j + 1) & 31);
-        float t = 0.f, iv = 0.f, beta = x0;
+        float tt = 0.f, iv = 0.f, beta = x0;
         if (sigma > 0.f) {
           const float mu = sqrtf(fmaf(x0, x0, sigma));
           const float v0 = (x0 <= 0.f) ? x0 - mu : __fdividef(-sigma, x0 + mu);
-          t = __fdividef(2.f * v0 * v0, fmaf(v0, v0, sigma));
+          tt = __fdividef(2.f * v0 * v0, fmaf(v0, v0, sigma));
           beta = mu;
           iv = __fdividef(1.f, v0);
         }
-        sfor<KT>([&](auto a) {
+        sfor<KR>([&](auto a) {
           const int i = lane + 32 * a;
-          const float v = (a < S) ? 0.f : ((i == j + 1) ? 1.f : ((i > j + 1 && i < k) ? A[a][S] * iv : 0.f));
+          const float v = (a < S) ? 0.f : ((i == j + 1) ? 1.f : ((i > j + 1 && i < k) ? colv[a] * iv : 0.f));
           vs[i] = v;
-          if (i < k) Vg[(size_t)j * k + i] = (t != 0.f) ? v : 0.f;
+          if (i < k) Vg[(size_t)j * k + i] = (tt != 0.f) ? v : 0.f;
         });
         if (lane == 0) {
-          scal[j & 1] = t;
-          tau_g[j] = t;
+          scal[j & 1] = tt;
+          tau_g[j] = tt;
           e_g[j] = beta;
         }
       }
       __syncthreads();
-      const float t = scal[j & 1];
-      if (t == 0.f) continue;               // the same decision in every thread
-      // M: p_c = tau (H v)_c for this warp's live columns, share of v^T H v.
-      // The KT column sums and the share (slot 7) are reduced over the lanes
-      // together: each butterfly level keeps half of the values and sends the
-      // other half, 9 shuffles in all, after which lanes 4i .. 4i + 3 hold sum i.
-      float vr[KT], vc[KT];
-      sfor<KT>([&](auto a) { vr[a] = (a >= S) ? vs[lane + 32 * a] : 0.f; });
-      sfor<KT>([&](auto c) { vc[c] = (c >= S) ? vs[w + 32 * c] : 0.f; });
-      float x8[8];
-      sfor<8>([&](auto c) { x8[c] = 0.f; });
-      sfor<KT>([&](auto c) {
-        if (c >= S) {
+      const float tau = scal[j & 1];
+      if (tau == 0.f) continue;              // the same decision in every thread
+      // M: (H v)_c for this thread's live columns, its share of v^T H v
+      float vr[KR], vc[KC];
+      sfor<KR>([&](auto a) { vr[a] = (a >= S) ? vs[lane + 32 * a] : 0.f; });
+      sfor<KC>([&](auto c) { vc[c] = (c >= 4 * S) ? vs[w + 8 * c] : 0.f; });
+      float xv[NV];
+      sfor<NV>([&](auto c) { xv[c] = 0.f; });
+      sfor<KC>([&](auto c) {
+        if constexpr (c >= 4 * S) {
           float acc = 0.f;
-          sfor<KT>([&](auto a) {
-            if (a >= S) acc = fmaf(A[a][c], vr[a], acc);
+          sfor<KR>([&](auto a) {
+            if constexpr (a >= S) acc = fmaf(A[a][c], vr[a], acc);
           });
-          x8[c] = acc;
-          x8[7] = fmaf(vc[c], acc, x8[7]);
+          xv[c] = acc;
+          xv[KC] = fmaf(vc[c], acc, xv[KC]);
         }
       });
+      const float tot = lane_transpose_sum<NV>(xv);
       {
-        const unsigned full = 0xffffffffu;
-        const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4;
-        float x4[4], x2[2];
-        sfor<4>([&](auto q) {
-          const float send = h4 ? x8[q] : x8[q + 4], keep = h4 ? x8[q + 4] : x8[q];
-          x4[q] = keep + __shfl_xor_sync(full, send, 16);
-        });
-        sfor<2>([&](auto q) {
-          const float send = h3 ? x4[q] : x4[q + 2], keep = h3 ? x4[q + 2] : x4[q];
-          x2[q] = keep + __shfl_xor_sync(full, send, 8);
-        });
-        float x1 = (h2 ? x2[1] : x2[0]) + __shfl_xor_sync(full, h2 ? x2[0] : x2[1], 4);
-        x1 += __shfl_xor_sync(full, x1, 2);
-        x1 += __shfl_xor_sync(full, x1, 1);
-        const int slot = (lane >> 2) & 7;
-        if ((lane & 3) == 0) {
-          if (slot < KT) {
-            const int col = w + 32 * slot;
-            ps[col] = (col > j && col < k) ? t * x1 : 0.f;
-          } else if (slot == 7) {
-            wsum[w] = x1;
+        constexpr int shift = (NV == 32) ? 0 : (NV == 16) ? 1 : 2;
+        const int vi = lane >> shift;
+        if ((lane & ((1 << shift) - 1)) == 0) {
+          if (vi < KC) {
+            const int col = w + 8 * vi;
+            if (col < KM) ps[col] = (col > j && col < k) ? tau * tot : 0.f;
+          } else if (vi == KC) {
+            wsum[w] = tot;
           }
         }
       }
       __syncthreads();
-      // U: rank-2 update of the live tiles; v^T H v from the 32 shares
-      const float vhv = warp_sum(wsum[lane]);
-      const float K = 0.5f * t * t * vhv;   // (tau / 2) v^T p
-      float wr[KT], wc[KT];
-      sfor<KT>([&](auto a) { wr[a] = (a >= S) ? fmaf(-K, vr[a], ps[lane + 32 * a]) : 0.f; });
-      sfor<KT>([&](auto c) { wc[c] = (c >= S) ? fmaf(-K, vc[c], ps[w + 32 * c]) : 0.f; });
-      sfor<KT>([&](auto a) {
-        if (a >= S) {
-          sfor<KT>([&](auto c) {
-            if (c >= S) A[a][c] -= fmaf(vr[a], wc[c], wr[a] * vc[c]);
+      // U: rank-2 update of the live tiles
+      float vhv = 0.f;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) vhv += wsum[q];
+      const float K = 0.5f * tau * tau * vhv;
+      float wr[KR], wc[KC];
+      sfor<KR>([&](auto a) { wr[a] = (a >= S) ? fmaf(-K, vr[a], ps[lane + 32 * a]) : 0.f; });
+      sfor<KC>([&](auto c) { wc[c] = (c >= 4 * S) ? fmaf(-K, vc[c], ps[w + 8 * c]) : 0.f; });
+      sfor<KR>([&](auto a) {
+        if constexpr (a >= S) {
+          sfor<KC>([&](auto c) {
+            if constexpr (c >= 4 * S) A[a][c] -= fmaf(vr[a], wc[c], wr[a] * vc[c]);
           });
         }
       });
     }
   });
   // trailing 2 x 2 (or 1 x 1) block, written by the owners of its entries
-  sfor<KT>([&](auto a) {
-    sfor<KT>([&](auto c) {
-      const int i = lane + 32 * a, jj = w + 32 * c;
+  sfor<KR>([&](auto a) {
+    sfor<KC>([&](auto c) {
+      const int i = lane + 32 * a, jj = w + 8 * c;
       if (k >= 2 && i == k - 2 && jj == k - 2) d_g[k - 2] = A[a][c];
       if (k >= 2 && i == k - 1 && jj == k - 2) e_g[k - 2] = A[a][c];
       if (i == k - 1 && jj == k - 1) d_g[k - 1] = A[a][c];
@@ -614,7 +645,7 @@ static cudaError_t launch_kt(const float* H, int64_t ldh, int k, int r, float* V
   float* tau = Vg + (size_t)k * k;
   float* d = tau + k;
   float* e = d + k;
-  k_eig_tridiag<KT><<<1, 1024, 0, st>>>(H, ldh, k, Vg, tau, d, e);
+  k_eig_tridiag8<KT><<<1, 256, 0, st>>>(H, ldh, k, Vg, tau, d, e);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   const size_t smem = er_smem_floats(32 * KT, k, r) * 4;
