@@ -10,9 +10,10 @@ Modules
 -------
 tt_oracle   TT-SVD (Alg. 1), TT-rBKI (Alg. 3, left block Krylov reading with
             Rayleigh-Ritz truncation; q = 0 is TT-rSVD, Alg. 2), TT-rSI
-            (Alg. 4, subspace iteration), Krylov-basis helper, tail energies
-            (Def. 3), TT contraction, the relative error and the PSNR of
-            Sec. 4.
+            (Alg. 4, subspace iteration), both also with the paper's steps
+            taken literally (right-side Krylov matrix, first-r truncation),
+            Krylov-basis helper, tail energies (Def. 3), TT contraction, the
+            relative error and the PSNR of Sec. 4.
 philox      Philox4x32-10 counter-based generator (Salmon et al., SC'11) and the
             Box-Muller transform that expand an Omega seed into the Gaussian
             test matrices of Alg. 3 step 3.
@@ -32,6 +33,10 @@ from .tt_oracle import (  # noqa: F401
     subspace_basis,
     rsi_mode,
     tt_rsi,
+    literal_rbki_mode,
+    literal_rsi_mode,
+    tt_rbki_literal,
+    tt_rsi_literal,
     tt_svd,
     tt_full,
     tt_error,

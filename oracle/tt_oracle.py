@@ -196,6 +196,57 @@ def tt_rsi(A, ranks, oversample, q, omegas=None, seed=None):
     return _tt_randomized(A, ranks, oversample, q, omegas, seed, rsi_mode)
 
 
+def literal_rbki_mode(C, r, Omega, q):
+    """One mode of Alg. 3 taken literally (the right-side Krylov matrix and
+    the first-r truncation of steps 7-8; a study option beside the
+    Rayleigh-Ritz reading used by rbki_mode):
+        K = [C^T C W, (C^T C)^2 W, ..., (C^T C)^q W]     step 4
+        U = qr(K, 0)                                      step 5
+        Y = C U                                           step 6
+        Q = qr(Y, 0)(:, 1:r)                              steps 7-8
+    With q = 0 the matrix K is empty; that case is Alg. 2 (TT-rSVD) taken
+    literally, Y = C W (steps 4-6 of Alg. 2).  numpy's QR is Householder
+    based (LAPACK geqrf), the economy form of MATLAB's qr(., 0).
+    Returns (Q, R = Q^T C, None)."""
+    if q == 0:
+        Y = C @ Omega
+    else:
+        blocks = []
+        B = Omega
+        for _ in range(q):
+            B = C.T @ (C @ B)               # (C^T C)^j W
+            blocks.append(B)
+        K = np.hstack(blocks)
+        U, _ = np.linalg.qr(K)              # economy QR
+        Y = C @ U
+    Qy, _ = np.linalg.qr(Y)
+    Q = Qy[:, :r]
+    return Q, Q.T @ C, None
+
+
+def literal_rsi_mode(C, r, Omega, q):
+    """One mode of Alg. 4 taken literally: Q_0 = qr(C W) (steps 4-5); q times
+    Yhat = C^T Q, Qhat = qr(Yhat), Y = C Qhat, Q = qr(Y) (steps 6-11); then
+    Q = Q(:, 1:r) (step 12).  Returns (Q, R = Q^T C, None)."""
+    Q, _ = np.linalg.qr(C @ Omega)
+    for _ in range(q):
+        Qh, _ = np.linalg.qr(C.T @ Q)
+        Q, _ = np.linalg.qr(C @ Qh)
+    Q = Q[:, :r]
+    return Q, Q.T @ C, None
+
+
+def tt_rbki_literal(A, ranks, oversample, q, omegas=None, seed=None):
+    """TT-rBKI with Alg. 3 steps 4-8 taken literally (literal_rbki_mode);
+    arguments and result as tt_rbki.  q = 0 is Alg. 2 taken literally."""
+    return _tt_randomized(A, ranks, oversample, q, omegas, seed, literal_rbki_mode)
+
+
+def tt_rsi_literal(A, ranks, oversample, q, omegas=None, seed=None):
+    """TT-rSI with Alg. 4 taken literally (literal_rsi_mode)."""
+    return _tt_randomized(A, ranks, oversample, q, omegas, seed, literal_rsi_mode)
+
+
 def tt_svd(A, ranks=None, eps=None):
     """TT-SVD (Alg. 1) in float64.
 
