@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-form measurement")
+    ap.add_argument("--no-extra-configs", action="store_true",
+                    help="skip the lines for the other single-GPU workloads")
     ap.add_argument("--config", type=int, default=CONFIG_ID, choices=sorted(W.CONFIGS),
                     help="workload (default: the 40^5 BF16 workload the metric is quoted on)")
     return ap.parse_args()
@@ -172,6 +174,56 @@ def plan_summary(tt, w, opts):
             for e in tt.plan_modes(w.dims, w.ranks, w.oversample, w.q, opts)]
 
 
+def algorithmic_bytes(tt, w, opts, elem):
+    """Bytes the method must move for one decomposition: per mode, (q_eff + 2)
+    reads of the unfolding C (sketch, q_eff Krylov steps, projection), one
+    read of Omega and one write of the remainder, q_eff = min(q, ceil(D / b) - 1)
+    (the Krylov dimension cap), elem bytes per entry."""
+    total = 0
+    for e in tt.plan_modes(w.dims, w.ranks, w.oversample, w.q, opts):
+        m, n, b, r = e["m"], e["n"], e["b"], e["r_out"]
+        d = min(m, n)
+        q_eff = min(w.q, -(-d // b) - 1)
+        total += ((q_eff + 2) * m * n + n * b + r * n) * elem
+    return total
+
+
+def config_line(tt, torch, dev, cfg_id, forms, steps, sync_all, peaks):
+    """Time one decomposition of workload cfg_id in each storage form
+    ("bf16" and/or "fp32", graph-launched), with its TT error against the
+    float64 tensor and its whole-step HBM roofline fraction."""
+    w = W.CONFIGS[cfg_id]
+    A = W.make_tensor(w)
+    A32 = torch.from_numpy(A.astype(np.float32)).to(dev)
+    A64 = torch.from_numpy(A).to(dev)
+    out = {"workload": f"{w.name}: {w.notes}", "dims": list(w.dims), "ranks": list(w.ranks),
+           "oversample": w.oversample, "q": w.q}
+    for form in forms:
+        code = tt.TT_BF16 if form == "bf16" else tt.TT_F32
+        x = tt.permute_convert(A32, dst_dtype=torch.bfloat16) if form == "bf16" else A32
+        opts = tt.options(storage=code, remainder=code)
+        prob = tt.Problem(x, w.ranks, w.oversample, w.q, w.omega_seed)
+        g = tt.BatchGraph([prob], opts)
+        ms = time_steps(g.launch, steps, 3, sync_all)
+        if g.device_status() != [0]:
+            raise RuntimeError(f"device status not OK on config {cfg_id} ({form})")
+        g.close()
+        nbytes = algorithmic_bytes(tt, w, opts, 2 if form == "bf16" else 4)
+        per = ms / steps
+        out[form] = {"ms_per_step": per, "decompositions_per_s": 1e3 / per,
+                     "tt_error": rel_error_dev(A64, prob.cores),
+                     "algorithmic_bytes": nbytes,
+                     "step_roofline": {"achieved": nbytes / (per * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
+                                       "unit": "GB/s", "frac": nbytes / (per * 1e-3) / 1e9 / peaks["hbm_gbs"]},
+                     "plan": plan_summary(tt, w, opts)}
+        del x
+    if "bf16" in out and "fp32" in out:
+        out["speedup_bf16_over_fp32"] = out["fp32"]["ms_per_step"] / out["bf16"]["ms_per_step"]
+        out["bf16_meets_error_criterion"] = out["bf16"]["tt_error"] <= 1.05 * out["fp32"]["tt_error"] + 1e-4
+    del A64, A32
+    return out
+
+
 def max_over_ranks(x, dist, device=None):
     """Largest value of x over all ranks (x itself without a process group)."""
     if dist is None:
@@ -284,9 +336,13 @@ def run_ours(args):
     # headline
     methods = {}
     cores_m = {}
-    for name, method, qm in (("tt_rsi", tt.TT_METHOD_RSI, q), ("tt_rsvd", tt.TT_METHOD_RBKI, 0)):
+    # the paper's Alg. 3 taken literally (right-side Krylov matrix, first-r
+    # truncation): the study form beside the Rayleigh-Ritz reading
+    for name, method, qm, lit in (("tt_rsi", tt.TT_METHOD_RSI, q, False), ("tt_rsvd", tt.TT_METHOD_RBKI, 0, False),
+                                  ("tt_rbki_literal", tt.TT_METHOD_RBKI, q, True)):
         pm = tt.Problem(Abf, ranks, p, qm, seed)
-        gm = tt.BatchGraph([pm], tt.options(storage=tt.TT_BF16, remainder=tt.TT_BF16, method=method))
+        gm = tt.BatchGraph([pm], tt.options(storage=tt.TT_BF16, remainder=tt.TT_BF16, method=method,
+                                            paper_literal=lit))
         msm = time_steps(gm.launch, fp32_steps, 2, barrier_sync)
         if gm.device_status() != [0]:
             raise RuntimeError(f"device status not OK after {name}")
@@ -337,18 +393,40 @@ def run_ours(args):
     graph_bf.close()
     graph_32.close()
 
-    # ---- roofline of the dominant kernel
+    # ---- roofline of the dominant streaming kernel (HBM-bound family)
     peaks, peak_src = measured_peaks()
-    pass_stats = {k: v for k, v in stats.items() if v["bytes"] > 0 and v["ms"] > 0}
+    hbm_fams = {"proj_tc", "cs_tc", "gram_tc", "gram_apply_tc"}
+    pass_stats = {k: v for k, v in stats.items() if k in hbm_fams and v["bytes"] > 0 and v["ms"] > 0}
     dom_name, dom = max(pass_stats.items(), key=lambda kv: kv[1]["ms"])
     launches_dom = max(1, dom["launches"])
     per_launch_ms = dom["ms"] / launches_dom
     per_launch_bytes = dom["bytes"] / launches_dom
     achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
     traffic = NCU_TRAFFIC.get(dom_name)
-    # the Gram-power route's GEMMs are cuBLAS kernels: counted apart
     library = {k: v["launches"] for k, v in stats.items() if k in LIBRARY_FAMILIES}
     total_launches = sum(v["launches"] for k, v in stats.items() if k not in LIBRARY_FAMILIES)
+    # where the time goes: the family with the largest share of the timed
+    # kernel time, and the whole step against the HBM roofline
+    kern_ms = sum(v["ms"] for v in stats.values())
+    top_name, top = max(stats.items(), key=lambda kv: kv[1]["ms"])
+    step_bytes = algorithmic_bytes(tt, w, opts_bf, 2)
+    step_ms = ms_max / args.steps
+    dominant = {"kernel": top_name, "share": top["ms"] / kern_ms if kern_ms else None,
+                "ms_per_step": top["ms"] / args.steps,
+                "bound": "hbm" if top_name in hbm_fams else
+                         ("tensor" if top_name == "gram_tc_tiled" else "latency (small dense algebra on one SM or cluster)")}
+    step_roof = {"achieved": step_bytes / (step_ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                 "frac": step_bytes / (step_ms * 1e-3) / 1e9 / peaks["hbm_gbs"], "algorithmic_bytes": step_bytes,
+                 "ideal_ms": step_bytes / (peaks["hbm_gbs"] * 1e9) * 1e3}
+    gram_roof = None
+    if "gram_tc_tiled" in stats and stats["gram_tc_tiled"]["ms"] > 0:
+        gstat = stats["gram_tc_tiled"]
+        tflops = gstat["flops"] / (gstat["ms"] * 1e-3) / 1e12
+        gram_roof = {"bound": "tensor", "kernel": "gram_tc_tiled", "achieved": tflops,
+                     "peak": peaks["bf16_tflops"], "unit": "TFLOP/s", "frac": tflops / peaks["bf16_tflops"],
+                     "flops_note": "algorithmic 2 m^2 n per Gram (both triangles), averaged over the launches "
+                                   "(the 800 x 64000 and 800 x 1600 unfoldings)",
+                     "launches": gstat["launches"], "ms_per_launch": gstat["ms"] / gstat["launches"]}
 
     result = {
         "metric": METRIC,
@@ -376,6 +454,9 @@ def run_ours(args):
         "launch": "one CUDA graph per decomposition (library graph API); kernel timings from a second "
                   "timed pass of the same steps launched eagerly with per-kernel CUDA events",
         "profiled_ms_per_step": ms_prof / args.steps,
+        "step_roofline": step_roof,
+        "dominant_kernel": dominant,
+        "gram_roofline": gram_roof,
         "roofline": {"bound": "hbm", "kernel": dom_name, "achieved": achieved,
                      "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
                      "peak_source": peak_src, "traffic": traffic,
@@ -388,6 +469,13 @@ def run_ours(args):
         "input_gen_s": gen_s,
     }
 
+    if not args.no_extra_configs:
+        # the other single-GPU workloads: 256 x 256 x 64 x 32 in both forms
+        # (the largest), 32^5 in the plain FP32 form
+        result["other_configs"] = {
+            "config4": config_line(tt, torch, dev, 4, ("bf16", "fp32"), 10, barrier_sync, peaks),
+            "config2": config_line(tt, torch, dev, 2, ("fp32",), 10, barrier_sync, peaks),
+        }
     if not args.no_batched:
         result["batched"] = batched_measure(tt, torch, dev, barrier_sync)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -103,7 +103,19 @@ typedef struct {
                            cores for BF16, FP32 accumulation) and compute
                            each power as G X: the same Krylov space, fewer
                            passes over C.  0: every power streams C.          */
-  int32_t reserved[2];  /* must be zero                                       */
+  int32_t paper_literal;/* 0 (default): Rayleigh-Ritz truncation of the left
+                           Krylov basis (above).  1: the paper's steps taken
+                           literally, a study form: Alg. 3 builds its Krylov
+                           matrix on the right and keeps the first r_k
+                           columns of an unpivoted QR of Y = C U (steps 4-8);
+                           those columns span (C C^T) C W(:, 1:r_k), which is
+                           what this form computes (one power of the first
+                           r_k columns of W for q >= 1; Alg. 2, C W(:, 1:r_k),
+                           for q = 0), orthonormalised and stored as the core
+                           without Rayleigh-Ritz.  With TT_METHOD_RSI, Alg. 4
+                           taken literally: (C C^T)^q C W(:, 1:r_k).  The
+                           exhaustion Gram routes are not used.               */
+  int32_t reserved;     /* must be zero                                       */
 } tt_options;
 
 enum { TT_METHOD_RBKI = 0, TT_METHOD_RSI = 1 };

@@ -38,11 +38,12 @@ def _stream_handle(stream):
 
 
 def options(storage=N.TT_F32, remainder=None, exhaust_gram=True, batch_streams=0, method=N.TT_METHOD_RBKI,
-            gram_power=True):
+            gram_power=True, paper_literal=False):
     """tt_options with the given fields (remainder None = same as storage;
     method TT_METHOD_RBKI (Alg. 3) or TT_METHOD_RSI (Alg. 4); q = 0 with
     either is TT-rSVD, Alg. 2; gram_power False makes every Krylov power
-    stream the unfolding)."""
+    stream the unfolding; paper_literal True takes the paper's steps
+    literally, first-r truncation without Rayleigh-Ritz)."""
     o = N.TTOptions()
     N.check(N.lib().tt_rbki_default_options(ctypes.byref(o)))
     o.storage = int(storage)
@@ -51,6 +52,7 @@ def options(storage=N.TT_F32, remainder=None, exhaust_gram=True, batch_streams=0
     o.batch_streams = int(batch_streams)
     o.method = int(method)
     o.gram_power = 1 if gram_power else 0
+    o.paper_literal = 1 if paper_literal else 0
     return o
 
 

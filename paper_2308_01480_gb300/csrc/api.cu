@@ -41,6 +41,7 @@ struct ModePlan {
   bool gram_cols = false;    // exhaustion with D == n < m: the n x n Gram C^T C
   bool gram_power = false;   // short unfolding: G = C C^T formed once, each power W = G X
   bool fused_ga = false;     // Gram-apply fused in one pass over C
+  bool literal = false;      // the paper's steps taken literally (first-r truncation)
 };
 
 struct Plan {
@@ -63,8 +64,8 @@ tt_status resolve_options(const tt_options* in, tt_options* out) {
   if (out->method != TT_METHOD_RBKI && out->method != TT_METHOD_RSI)
     return fail(TT_EINVAL, "options.method must be TT_METHOD_RBKI or TT_METHOD_RSI");
   if (out->gram_power != 0 && out->gram_power != 1) return fail(TT_EINVAL, "options.gram_power must be 0 or 1");
-  for (int i = 0; i < 2; ++i)
-    if (out->reserved[i] != 0) return fail(TT_EINVAL, "options.reserved must be zero");
+  if (out->paper_literal != 0 && out->paper_literal != 1) return fail(TT_EINVAL, "options.paper_literal must be 0 or 1");
+  if (out->reserved != 0) return fail(TT_EINVAL, "options.reserved must be zero");
   return TT_OK;
 }
 
@@ -138,6 +139,17 @@ tt_status build_plan(const int64_t* dims, int d, const int64_t* ranks, int p, in
     M.gram_route = P.o.exhaust_gram && cols == M.D && M.D == M.m && M.m <= 128;
     M.gram_cols = P.o.exhaust_gram && !M.gram_route && cols == M.D && M.D == M.n && M.n < M.m &&
                   ttr::eig_top_ok((int)M.n);
+    if (P.o.paper_literal) {
+      // Alg. 3 steps 4-8 (Alg. 4 steps 4-12, Alg. 2 for q = 0) taken
+      // literally: the kept r columns span (C C^T)^s C W(:, 1:r), s = min(q, 1)
+      // for Alg. 3 (only the first block of its right-side Krylov matrix
+      // reaches the first r columns of qr(Y)) and s = q for Alg. 4
+      M.literal = true;
+      M.blocks.assign(1, M.r_out);
+      M.kq = M.r_out;
+      M.iters = (P.o.method == TT_METHOD_RSI) ? q : std::min(q, 1);
+      M.gram_route = M.gram_cols = false;
+    }
     M.fused_ga = ttr::simt_ga_fused_ok(M.m, M.b);
     // Krylov powers over a short unfolding (n <= 8192) are latency-bound
     // passes over few column tiles; when there are at least two, one Gram
@@ -147,7 +159,8 @@ tt_status build_plan(const int64_t* dims, int d, const int64_t* ranks, int p, in
     // passes (4 b flops per entry each, HBM-bound) at any n.  G stays below
     // 16 MB.
     {
-      const size_t powers = (P.o.method == TT_METHOD_RSI) ? (size_t)M.iters + 1 : M.blocks.size();
+      const size_t powers = M.literal ? (size_t)M.iters
+                          : (P.o.method == TT_METHOD_RSI) ? (size_t)M.iters + 1 : M.blocks.size();
       const int cdt_k = (k == 0) ? P.storage : P.remainder;
       M.gram_power = P.o.gram_power && !M.gram_route && !M.gram_cols && ttr::gram_power_ok(M.m, M.b) &&
                      ((powers >= 2 && M.m <= 2048 && M.n <= 8192) ||
@@ -277,12 +290,14 @@ tt_status run_mode(const Plan& P, int k, const TIn* C, char* ws, int* status, co
       TTR_CUDA(ttr::launch_omega_transpose_any(omega_explicit, M.n, M.b, S, om_dt, st));
     else
       TTR_CUDA(ttr::launch_omega(seed, k, M.n, M.b, S, om_dt, 1, M.n, st));
-    // sketch Y = C Omega, first basis block
+    // sketch Y = C Omega, first basis block (the literal form sketches with
+    // the first r columns of Omega: the first r rows of its transpose S)
+    const int bw = M.literal ? r : M.b;
     if (use_tc)
-      TTR_CUDA(ttr::tc_cs(Cb, M.m, M.n, reinterpret_cast<const __nv_bfloat16*>(S), M.n, M.b, part, Y, M.b, status,
+      TTR_CUDA(ttr::tc_cs(Cb, M.m, M.n, reinterpret_cast<const __nv_bfloat16*>(S), M.n, bw, part, Y, bw, status,
                           st));
     else
-      TTR_CUDA(ttr::simt_cs<TIn>(C, M.m, M.n, S, M.n, M.b, part, Y, M.b, st));
+      TTR_CUDA(ttr::simt_cs<TIn>(C, M.m, M.n, S, M.n, bw, part, Y, bw, st));
     const uint64_t rseed = 0x5EEDull * (uint64_t)(k + 1);
     int* flag = status + 1;
     unsigned* ticket = reinterpret_cast<unsigned*>(status + 2);
@@ -341,6 +356,20 @@ tt_status run_mode(const Plan& P, int k, const TIn* C, char* ws, int* status, co
       }
       return TT_OK;
     };
+    if (M.literal) {
+      // Q = orth((C C^T)^s C W(:, 1:r)): orthonormalise after every power
+      // (the same leading-column spans as the literal QRs); Q is the core
+      tt_status os = orth(Y, r, r, 0, r, rseed);
+      if (os != TT_OK) return os;
+      for (int it = 0; it < M.iters; ++it) {
+        os = power(Q, W, r);
+        if (os != TT_OK) return os;
+        os = orth(W, kq, r, 0, r, rseed + 7919ull * (it + 1));
+        if (os != TT_OK) return os;
+      }
+      TTR_CUDA(cudaMemcpyAsync(U, Q, sizeof(float) * (size_t)M.m * r, cudaMemcpyDeviceToDevice, st));
+      TTR_CUDA(cudaMemcpyAsync(core, Q, sizeof(float) * (size_t)M.m * r, cudaMemcpyDeviceToDevice, st));
+    } else {
     tt_status os = orth(Y, M.b, M.b, 0, M.blocks[0], rseed);
     if (os != TT_OK) return os;
     if (P.o.method == TT_METHOD_RSI) {
@@ -373,6 +402,7 @@ tt_status run_mode(const Plan& P, int k, const TIn* C, char* ws, int* status, co
       TTR_CUDA(ttr::launch_rr_fast(Q, W, kq, M.m, kq, r, 0, small, U, core, st));
     else
       TTR_CUDA(ttr::launch_rayleigh_ritz(Q, W, kq, M.m, kq, r, 0, small, U, core, st));
+    }
   }
   // Alg. 3 step 10: next remainder R = U^T C (r x n)
   char* Rout = ws + ((k % 2 == 0) ? P.off_R0 : P.off_R1);
@@ -667,7 +697,9 @@ tt_status tt_rbki_plan_modes(const int64_t* dims, int d, const int64_t* ranks, i
     o.basis_cols = M.kq;
     o.blocks = (int32_t)M.blocks.size();
     const bool exhaustion = M.gram_route || M.gram_cols;
-    o.powers = exhaustion ? 0 : (P.o.method == TT_METHOD_RSI ? M.iters + 1 : (int32_t)M.blocks.size());
+    o.powers = exhaustion ? 0
+             : M.literal ? M.iters
+             : (P.o.method == TT_METHOD_RSI ? M.iters + 1 : (int32_t)M.blocks.size());
     o.route = M.gram_route ? TT_ROUTE_GRAM_ROWS
             : M.gram_cols  ? TT_ROUTE_GRAM_COLS
             : M.gram_power ? TT_ROUTE_GRAM_POWER

@@ -77,12 +77,17 @@ def test_invalid_arguments_rejected_on_host(L):
     assert st == N.TT_EINVAL     # misaligned workspace
     opts = N.TTOptions()
     L.tt_rbki_default_options(ctypes.byref(opts))
-    opts.reserved[0] = 1
+    opts.reserved = 1
     assert L.tt_rbki_workspace_size(N.i64_array([5, 4, 3]), 3, N.i64_array([2, 2]), 1, 1, ctypes.byref(opts),
                                     ctypes.byref(nb)) == N.TT_EINVAL
     L.tt_rbki_default_options(ctypes.byref(opts))
     assert opts.gram_power == 1
     opts.gram_power = 2
+    assert L.tt_rbki_workspace_size(N.i64_array([5, 4, 3]), 3, N.i64_array([2, 2]), 1, 1, ctypes.byref(opts),
+                                    ctypes.byref(nb)) == N.TT_EINVAL
+    L.tt_rbki_default_options(ctypes.byref(opts))
+    assert opts.paper_literal == 0
+    opts.paper_literal = 2
     assert L.tt_rbki_workspace_size(N.i64_array([5, 4, 3]), 3, N.i64_array([2, 2]), 1, 1, ctypes.byref(opts),
                                     ctypes.byref(nb)) == N.TT_EINVAL
     perm = (ctypes.c_int * 3)(0, 0, 1)

@@ -105,3 +105,13 @@ def test_bench_family_names_exist_in_the_library():
     names = set(re.findall(r'ProfScope \w+\("(\w+)"', src))
     assert set(bench.NCU_TRAFFIC) <= names
     assert set(bench.LIBRARY_FAMILIES) <= names
+
+
+def test_literal_plan_counts_powers():
+    """paper_literal: r_k columns, one power for Alg. 3 (q >= 1), none for
+    q = 0, q powers for Alg. 4; never an exhaustion Gram route."""
+    dims, ranks = (40, 40, 40, 40, 40), (20, 20, 20, 20)
+    for method, q, want in ((tt.TT_METHOD_RBKI, 4, 1), (tt.TT_METHOD_RBKI, 0, 0), (tt.TT_METHOD_RSI, 3, 3)):
+        modes = tt.plan_modes(dims, ranks, 10, q, tt.options(storage=tt.TT_BF16, method=method, paper_literal=True))
+        assert all(e["powers"] == want and e["basis_cols"] == e["r_out"] for e in modes)
+        assert all(e["route"] in ("krylov", "gram_power") for e in modes)
