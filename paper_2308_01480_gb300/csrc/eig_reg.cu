@@ -20,8 +20,8 @@
 //     QR twice (columns in descending eigenvalue order, so the result is
 //     the Gram-Schmidt basis), or Gram-Schmidt twice when a Cholesky pivot
 //     is too small.
-//  5. Back-transformation by the stored reflectors, a warp per two vectors
-//     held in registers.
+//  5. Back-transformation by the stored reflectors, four at a time, a warp
+//     per two vectors held in registers.
 #include <float.h>
 
 #include <utility>
@@ -356,6 +356,81 @@ __global__ void __launch_bounds__(256, 1) k_eig_tridiag8(const float* __restrict
   }
 }
 
+// Step 5 for NV vectors held by one warp: x <- P_0 P_1 ... P_{k-3} x, the
+// reflectors taken four at a time from the last (gg holds each group's six
+// inner products), each vector's entries i = lane + 32 c in registers.
+template <int KT, int NV>
+__device__ __forceinline__ void back_transform_warp(const float* Vs, const float* tau, const float* gg, int k,
+                                                    const float* cur, int ldx, const int (&js)[NV], float* V,
+                                                    int ldv) {
+  const int lane = threadIdx.x & 31;
+  const int ng = (k - 2 + 3) / 4;
+  float x[NV][KT];
+#pragma unroll
+  for (int u = 0; u < NV; ++u)
+#pragma unroll
+    for (int c = 0; c < KT; ++c) {
+      const int i = lane + 32 * c;
+      x[u][c] = (i < k) ? cur[(size_t)js[u] * ldx + i] : 0.f;
+    }
+  for (int g = 0; g < ng; ++g) {
+    const int ht = k - 3 - 4 * g;
+    const int c0 = (max(ht - 3, 0) + 1) >> 5;   // first chunk with a nonzero entry
+    float v[4][KT];
+    float dd[4 * NV];
+#pragma unroll
+    for (int q = 0; q < 4 * NV; ++q) dd[q] = 0.f;
+#pragma unroll
+    for (int c = 0; c < KT; ++c) {
+      if (c >= c0) {                     // warp-uniform: chunks below c0 are zero
+        const int i = lane + 32 * c;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          v[a][c] = (ht - a >= 0 && i < k) ? Vs[(size_t)(ht - a) * k + i] : 0.f;
+#pragma unroll
+          for (int u = 0; u < NV; ++u) dd[4 * u + a] = fmaf(v[a][c], x[u][c], dd[4 * u + a]);
+        }
+      }
+    }
+    // lane (32 / (4 NV)) q ends with the total of dd[q]
+    const float tot = lane_transpose_sum<4 * NV>(dd);
+    float d[4 * NV];
+#pragma unroll
+    for (int q = 0; q < 4 * NV; ++q) d[q] = __shfl_sync(0xffffffffu, tot, (32 / (4 * NV)) * q);
+    const float* gq = gg + g * 8;
+    const float g01 = gq[0], g02 = gq[1], g03 = gq[2], g12 = gq[3], g13 = gq[4], g23 = gq[5];
+    float t[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) t[a] = (ht - a >= 0) ? tau[ht - a] : 0.f;
+#pragma unroll
+    for (int u = 0; u < NV; ++u) {
+      const float* du = d + 4 * u;
+      const float c0v = t[0] * du[0];
+      const float c1v = t[1] * fmaf(-g01, c0v, du[1]);
+      const float c2v = t[2] * fmaf(-g12, c1v, fmaf(-g02, c0v, du[2]));
+      const float c3v = t[3] * fmaf(-g23, c2v, fmaf(-g13, c1v, fmaf(-g03, c0v, du[3])));
+#pragma unroll
+      for (int c = 0; c < KT; ++c) {
+        if (c >= c0) {
+          float s = x[u][c];
+          s = fmaf(-c0v, v[0][c], s);
+          s = fmaf(-c1v, v[1][c], s);
+          s = fmaf(-c2v, v[2][c], s);
+          s = fmaf(-c3v, v[3][c], s);
+          x[u][c] = s;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < KT; ++c) {
+    const int i = lane + 32 * c;
+    if (i < k)
+#pragma unroll
+      for (int u = 0; u < NV; ++u) V[(size_t)i * ldv + js[u]] = x[u][c];
+  }
+}
+
 // Steps 2-5 in one CTA of 16 warps, from T and the reflectors in global
 // scratch (the reflectors are staged in shared memory).
 template <int KT>
@@ -526,6 +601,38 @@ __global__ void __launch_bounds__(512, 1) k_eig_vectors(const float* __restrict_
         }
       }
       __syncthreads();
+      if (round == 1 && pass == 1) {
+        // after one Cholesky QR the Gram is usually within rounding of the
+        // identity: then X (1.5 I - 0.5 G) (first-order polar correction,
+        // orthogonality error O(|G - I|^2), same span) replaces the second
+        float dev = 0.f;
+        for (int x = tid; x < r * r; x += NT) {
+          const int a = x / r, b = x % r;
+          if (b >= a) dev = fmaxf(dev, fabsf(G[a * 33 + b] - (a == b ? 1.f : 0.f)));
+        }
+        dev = warp_max_f(dev);
+        if (lane == 0) red[32 + ty] = dev;
+        __syncthreads();
+        dev = warp_max_f(lane < NW ? red[32 + lane] : 0.f);
+        if (dev < 1e-4f) {                // the same decision in every thread
+          for (int x = tid; x < r * r; x += NT) {
+            const int a = x / r, b = x % r;
+            const float g = (b >= a) ? G[a * 33 + b] : G[b * 33 + a];
+            Tm[a * 33 + b] = (a == b ? 1.5f : 0.f) - 0.5f * g;
+          }
+          __syncthreads();
+          for (int x = tid; x < r * k; x += NT) {
+            const int j = x / k, i = x % k;
+            float s = 0.f;
+            for (int a = 0; a < r; ++a) s = fmaf(cur[(size_t)a * ldx + i], Tm[a * 33 + j], s);
+            nxt[(size_t)j * ldx + i] = s;
+          }
+          __syncthreads();
+          float* tmp = cur; cur = nxt; nxt = tmp;
+          continue;
+        }
+        __syncthreads();
+      }
       if (tid < r) red[tid] = G[tid * 33 + tid];
       chol_inv_warp32_call(G, 33, r, red, Rm, 33, Tm, 33, sflag, true);
       if (*sflag) break;                  // uniform: fall back below
@@ -572,59 +679,54 @@ __global__ void __launch_bounds__(512, 1) k_eig_vectors(const float* __restrict_
   }
 
   // ---------------------------------------------------------------- 5
-  // a warp back-transforms vectors ty and ty + NW together: each reflector
-  // is read once for both and the two lane reductions overlap
+  // x <- P_0 P_1 ... P_{k-3} x for the r vectors, reflectors taken four at a
+  // time from the last.  For the group {h, h-1, h-2, h-3}, applied in that
+  // order, the coefficients follow from the dots d_a = v_{h-a}^T x of the
+  // group's incoming x and the group's inner products g_ab = v_{h-a}^T v_{h-b}:
+  //   c_a = tau_{h-a} (d_a - sum_{b < a} g_ba c_b),   x -= sum_a c_a v_{h-a},
+  // so a group costs one lane reduction where single reflectors cost four.
+  // v_h is zero at indices <= h (and entirely where tau_h = 0), so a group
+  // skips the 32-entry chunks below its lowest reflector.
   {
-    const int j0 = ty, j1 = ty + NW;
-    const bool has1 = j1 < r;
-    if (j0 < r) {
-      float x0[KT], x1[KT];
-      const float* s0 = cur + (size_t)j0 * ldx;
-      const float* s1 = cur + (size_t)(has1 ? j1 : j0) * ldx;
+    const int ng = (k - 2 + 3) / 4;       // groups over reflectors 0 .. k-3
+    float* gg = Tm;                       // [ng][8]: g01 g02 g03 g12 g13 g23
+    for (int g = ty; g < ng; g += NW) {
+      const int ht = k - 3 - 4 * g;
+      float p6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
       for (int c = 0; c < KT; ++c) {
         const int i = lane + 32 * c;
-        x0[c] = (i < k) ? s0[i] : 0.f;
-        x1[c] = (i < k) ? s1[i] : 0.f;
-      }
-      for (int h = k - 3; h >= 0; --h) {
-        const float th = tau[h];
-        if (th == 0.f) continue;
-        const float* vh = Vs + (size_t)h * k;
-        float vv[KT];
-        float dp0 = 0.f, dp1 = 0.f;
+        float v[4];
 #pragma unroll
-        for (int c = 0; c < KT; ++c) {
-          const int i = lane + 32 * c;
-          vv[c] = (i < k) ? vh[i] : 0.f;
-          dp0 = fmaf(vv[c], x0[c], dp0);
-          dp1 = fmaf(vv[c], x1[c], dp1);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          dp0 += __shfl_xor_sync(0xffffffffu, dp0, o);
-          dp1 += __shfl_xor_sync(0xffffffffu, dp1, o);
-        }
-        const float sc0 = th * dp0, sc1 = th * dp1;
-#pragma unroll
-        for (int c = 0; c < KT; ++c) {
-          x0[c] = fmaf(-sc0, vv[c], x0[c]);
-          x1[c] = fmaf(-sc1, vv[c], x1[c]);
-        }
+        for (int a = 0; a < 4; ++a) v[a] = (ht - a >= 0 && i < k) ? Vs[(size_t)(ht - a) * k + i] : 0.f;
+        p6[0] = fmaf(v[0], v[1], p6[0]);
+        p6[1] = fmaf(v[0], v[2], p6[1]);
+        p6[2] = fmaf(v[0], v[3], p6[2]);
+        p6[3] = fmaf(v[1], v[2], p6[3]);
+        p6[4] = fmaf(v[1], v[3], p6[4]);
+        p6[5] = fmaf(v[2], v[3], p6[5]);
       }
 #pragma unroll
-      for (int c = 0; c < KT; ++c) {
-        const int i = lane + 32 * c;
-        if (i < k) {
-          V[(size_t)i * ldv + j0] = x0[c];
-          if (has1) V[(size_t)i * ldv + j1] = x1[c];
-        }
-      }
-      if (evals && lane == 0) {
-        evals[j0] = lam[j0];
-        if (has1) evals[j1] = lam[j1];
+      for (int q = 0; q < 6; ++q) p6[q] = warp_sum(p6[q]);
+      if (lane < 6) {
+        float o = p6[0];
+#pragma unroll
+        for (int q = 1; q < 6; ++q) o = (lane == q) ? p6[q] : o;
+        gg[g * 8 + lane] = o;
       }
     }
+    __syncthreads();
+    // warps ty < r - NW take vectors ty and ty + NW (each reflector read
+    // once for both, their lane reductions merged), the others vector ty
+    if (ty + NW < r) {
+      const int js[2] = {ty, ty + NW};
+      back_transform_warp<KT, 2>(Vs, tau, gg, k, cur, ldx, js, V, ldv);
+    } else if (ty < r) {
+      const int js[1] = {ty};
+      back_transform_warp<KT, 1>(Vs, tau, gg, k, cur, ldx, js, V, ldv);
+    }
+    if (evals)
+      for (int j = tid; j < r; j += NT) evals[j] = lam[j];
   }
 }
 
