@@ -192,6 +192,8 @@ tt_status build_plan(const int64_t* dims, int d, const int64_t* ranks, int p, in
       maxSmall = std::max(maxSmall, ttr::orth_scratch_floats(M.m, M.b, M.kq));
       maxSmall = std::max(maxSmall, ttr::rr_scratch_floats(M.kq));
       maxSmall = std::max(maxSmall, ttr::orth_fast_scratch_floats(M.m, M.kq, M.b));
+      // the last block's call has the largest basis: kq0 + c <= kq
+      maxSmall = std::max(maxSmall, ttr::orth_grid_rs_scratch_floats(M.m, std::max(0, M.kq - M.b), M.b));
       maxSmall = std::max(maxSmall, ttr::rr_fast_scratch_floats(M.m, M.kq, M.r_out));
     }
     maxU = std::max(maxU, (size_t)(M.m * M.r_out));
@@ -319,6 +321,13 @@ tt_status run_mode(const Plan& P, int k, const TIn* C, char* ws, int* status, co
           return TT_OK;
         }
         if (e != cudaErrorNotSupported) TTR_CUDA(e);
+      }
+      if (ttr::orth_grid_rs_ok(M.m, kq0, zc, c)) {
+        // blocks taller than a cluster holds: one cooperative launch
+        TTR_CUDA(ttr::launch_orth_grid_rs(Z, ldz, zc, M.m, c, kq0, Q, kq, M.gram_power ? Xg : nullptr, xld, sd,
+                                          small, status, st));
+        xg_written = M.gram_power;
+        return TT_OK;
       }
       if (ttr::orth_cluster_ok(M.m, kq0, zc)) {
         TTR_CUDA(ttr::launch_orth_cluster(Z, ldz, M.m, zc, c, Q, kq, kq0, flag, st));

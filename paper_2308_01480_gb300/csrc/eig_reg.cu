@@ -27,6 +27,7 @@
 #include <utility>
 
 #include "chol.cuh"
+#include "cluster_la.cuh"
 #include "common.cuh"
 #include "kernels.h"
 
@@ -162,9 +163,12 @@ __device__ void tri_lu_solve(const float* w, int k, float* x) {
 }  // namespace
 
 // Shared-memory floats of k_eig_vectors for k (padded to KM = 32 KT) and r.
+__host__ __device__ inline size_t er_union_floats(int k, int r) {
+  const size_t a = (size_t)k * k, b = (size_t)r * 5 * k;
+  return a > b ? a : b;
+}
 __host__ __device__ inline size_t er_smem_floats(int KM, int k, int r) {
-  return (size_t)k * k + 4 * (size_t)KM + 32 + 64 + 1024 + 2 * (size_t)r * (k + 1) + (size_t)r * 5 * k +
-         3 * 33 * 32 + 8;
+  return er_union_floats(k, r) + 4 * (size_t)KM + 32 + 64 + 1024 + 2 * (size_t)r * (k + 1) + 3 * 33 * 32 + 8;
 }
 
 // Sum over the 32 lanes of NV values x[0..NV) (NV a power of two <= 32) with
@@ -442,8 +446,11 @@ __global__ void __launch_bounds__(512, 1) k_eig_vectors(const float* __restrict_
   constexpr int KM = 32 * KT;
   constexpr int NT = 32 * NW;
   extern __shared__ __align__(16) float sm[];
+  // the reflectors (step 5) and the inverse-iteration factors (step 3) are
+  // never live together: one region holds both
   float* Vs = sm;                         // [k][k], row j = reflector v_j
-  float* tau = Vs + (size_t)k * k;        // [KM]
+  float* Wk = sm;                         // [r][5k] inverse-iteration factors
+  float* tau = sm + er_union_floats(k, r);   // [KM]
   float* d = tau + KM;                    // [KM]
   float* e = d + KM;                      // [KM]
   float* e2 = e + KM;                     // [KM]
@@ -452,14 +459,12 @@ __global__ void __launch_bounds__(512, 1) k_eig_vectors(const float* __restrict_
   int* cnt = reinterpret_cast<int*>(red + 64);   // [1024]
   float* X = reinterpret_cast<float*>(cnt + 1024);   // [r][k + 1]
   float* X2 = X + (size_t)r * (k + 1);    // [r][k + 1]
-  float* Wk = X2 + (size_t)r * (k + 1);   // [r][5k] inverse-iteration factors
-  float* G = Wk + (size_t)r * 5 * k;      // [32][33]
+  float* G = X2 + (size_t)r * (k + 1);    // [32][33]
   float* Rm = G + 33 * 32;                // [32][32]
   float* Tm = Rm + 33 * 32;               // [32][32]
   int* sflag = reinterpret_cast<int*>(Tm + 33 * 32);
   const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 5;
   const int ldx = k + 1;
-  for (int x = tid; x < k * k; x += NT) Vs[x] = Vg[x];
   for (int i = tid; i < k; i += NT) {
     tau[i] = tau_g[i];
     d[i] = d_g[i];
@@ -579,6 +584,10 @@ __global__ void __launch_bounds__(512, 1) k_eig_vectors(const float* __restrict_
       for (int i = 0; i < k; ++i) x[i] *= sc;
     }
     __syncthreads();
+    // the factors are dead after the last solve: stage the reflectors for
+    // step 5 in their place while step 4 runs
+    if (round == 1)
+      for (int x = tid; x < k * k; x += NT) cp_async4(Vs + x, Vg + x, true);
 
   // ---------------------------------------------------------------- 4
     // one Cholesky QR pass keeps the vectors apart before the second solve;
@@ -679,6 +688,8 @@ __global__ void __launch_bounds__(512, 1) k_eig_vectors(const float* __restrict_
   }
 
   // ---------------------------------------------------------------- 5
+  cp_async_wait_all();
+  __syncthreads();
   // x <- P_0 P_1 ... P_{k-3} x for the r vectors, reflectors taken four at a
   // time from the last.  For the group {h, h-1, h-2, h-3}, applied in that
   // order, the coefficients follow from the dots d_a = v_{h-a}^T x of the

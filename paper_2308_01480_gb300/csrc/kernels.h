@@ -98,6 +98,15 @@ cudaError_t launch_orth_cluster(const float* W, int64_t ldw, int64_t m, int b, i
 // Q; when Xg is given the new block is also written there (m x xld, zero
 // padded to pad4(c) columns, 16-byte rows for the Gram power).  Returns
 // cudaErrorNotSupported when the device cannot hold the cluster.
+// The same sequence over all CTAs of one cooperative launch (at most one
+// per SM, shares reduced through global memory, bounded barriers) for blocks
+// with more rows than a cluster holds; scratch holds
+// orth_grid_rs_scratch_floats floats (barrier words, shares, sums).
+bool orth_grid_rs_ok(int64_t m, int kq0, int zc, int c);
+size_t orth_grid_rs_scratch_floats(int64_t m, int kq0, int zc);
+cudaError_t launch_orth_grid_rs(const float* Y, int64_t ldy, int zc, int64_t m, int c, int kq0, float* Q,
+                                int64_t ldq, float* Xg, int xld, uint64_t seed, float* scratch, int* status,
+                                cudaStream_t st);
 bool orth_cluster_rs_ok(int64_t m, int kq0, int zc, int c);
 cudaError_t launch_orth_cluster_rs(const float* Y, int64_t ldy, int zc, int64_t m, int c, int kq0, float* Q,
                                    int64_t ldq, float* Xg, int xld, uint64_t seed, int* status, cudaStream_t st);

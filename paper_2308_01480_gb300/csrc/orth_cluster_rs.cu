@@ -56,14 +56,22 @@ struct OrthRsArgs {
   int zmax;             // zc0
   int* status;
   uint64_t seed;
+  // grid form only: per-rank shares (2 x nranks x E), sums (2 x E), barrier
+  float* gparts;
+  float* gsums;
+  unsigned* gbar;
+  int eslot;            // E: floats per share
 };
 
 struct KcLayout {
   int KP, ZP, RP;
   size_t share, slice, P, Gm, T, R, misc, Zc, Zn, Qc, tmp, total;
   int slice_len;
+  int share_bufs;       // 2 for a cluster (other ranks read the shares), 1 for the grid form
 };
 
+// nc: cluster size; nc = 0 for the grid form (shares and sums in global
+// memory, no slice buffers).
 __host__ __device__ inline KcLayout kc_layout(int kqmax, int zmax, int rows, int nc) {
   KcLayout L;
   L.KP = pad4(kqmax);
@@ -71,8 +79,9 @@ __host__ __device__ inline KcLayout kc_layout(int kqmax, int zmax, int rows, int
   L.RP = pad4(rows);
   size_t o = 0;
   auto take = [&](size_t n) { size_t r = o; o += (n + 3) & ~size_t(3); return r; };
-  L.share = take(2 * (size_t)(L.KP + L.ZP) * L.ZP);
-  L.slice_len = ((L.KP + L.ZP) * L.ZP + nc - 1) / nc + 4;
+  L.share_bufs = nc > 0 ? 2 : 1;
+  L.share = take((size_t)L.share_bufs * (L.KP + L.ZP) * L.ZP);
+  L.slice_len = nc > 0 ? ((L.KP + L.ZP) * L.ZP + nc - 1) / nc + 4 : 0;
   L.slice = take(2 * (size_t)L.slice_len);
   L.P = take((size_t)L.KP * L.ZP);
   L.Gm = take((size_t)zmax * (zmax + 1));
@@ -86,14 +95,6 @@ __host__ __device__ inline KcLayout kc_layout(int kqmax, int zmax, int rows, int
   L.total = o;
   return L;
 }
-
-__device__ __forceinline__ void cp_async16z(void* dst, const void* src, bool ok) {
-  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(ok ? 16 : 0) : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // Y[i][j] = scale * sum_{t < kk} X[i][t] M[t][j] (+ Y0[i][j]) for i < rows
 // (multiple of 4), j < bp (multiple of 4), with TR x 4 register tiles so
@@ -175,14 +176,111 @@ __device__ void tn_split(const float* A, int lda, int ta, const float* B, int ld
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(KC_THREADS, 1) k_orth_cluster_rs(const __grid_constant__ OrthRsArgs a) {
-  extern __shared__ __align__(16) float sm[];
-  __shared__ unsigned long long badmask;
-  cg::cluster_group cl = cg::this_cluster();
+// The ranks of one cluster: shares summed through distributed shared memory.
+struct ClusterComm {
+  cg::cluster_group cl;
+  float* slices;        // two buffers of slice_len floats
+  int slice_len;
+  __device__ int nranks() { return (int)cl.num_blocks(); }
+  __device__ int rank() { return (int)cl.block_rank(); }
+  template <typename Put>
+  __device__ void reduce(float* mine, int phase, int e0, int e1, Put& put) {
+    cl.sync();
+    cluster_reduce_scatter_gather(cl, mine, slices + (size_t)(phase & 1) * slice_len, e0, e1, put);
+  }
+  __device__ void finish() { cl.sync(); }   // no CTA leaves while others may read its shares
+};
+
+// Barrier over all CTAs of a cooperative launch (every CTA resident): an
+// arrival counter and a generation word in global memory.  The wait gives up
+// after about two seconds, records TT_ETIMEOUT and marks the CTA dead, after
+// which its barriers return at once (results are then garbage, the status
+// says so).
+__device__ __forceinline__ void grid_barrier(unsigned* bar, unsigned n, int* status, int* dead) {
+  __syncthreads();
+  if (threadIdx.x == 0 && !*dead) {
+    volatile unsigned* gen = bar + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    if (atomicAdd(bar, 1u) == n - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      uint64_t t0 = 0;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+      while (*gen == g) {
+        uint64_t t = 0;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (t - t0 > 2000000000ull) {
+          set_status(status, TT_ETIMEOUT);
+          *dead = 1;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+// All CTAs of a cooperative launch: each writes its share to global memory,
+// CTA q sums the slice [q S, q S + S) over the ranks in rank order (the
+// ranks split over thread groups, the group partials added in group order),
+// and every CTA reads all sums back.
+struct GridComm {
+  int nr, rk;
+  float* parts;         // two buffers of nr x E floats
+  float* sums;          // two buffers of E floats
+  int E;
+  unsigned* bar;
+  int* status;
+  int* dead;            // shared-memory flag
+  float* tmp;           // shared scratch, at least blockDim.x floats
+  __device__ int nranks() { return nr; }
+  __device__ int rank() { return rk; }
+  template <typename Put>
+  __device__ void reduce(float* mine, int phase, int e0, int e1, Put& put) {
+    float* P = parts + (size_t)(phase & 1) * nr * E;
+    float* S = sums + (size_t)(phase & 1) * E;
+    for (int e = e0 + (int)threadIdx.x; e < e1; e += blockDim.x) __stcg(P + (size_t)rk * E + e, mine[e]);
+    grid_barrier(bar, nr, status, dead);
+    const int n = e1 - e0, sl = (n + nr - 1) / nr;
+    const int s0 = e0 + rk * sl, ns = max(0, min(e1, s0 + sl) - s0);
+    if (2 * ns > (int)blockDim.x) {
+      for (int x = threadIdx.x; x < ns; x += blockDim.x) {
+        float acc = 0.f;
+        for (int q = 0; q < nr; ++q) acc += __ldcg(P + (size_t)q * E + s0 + x);
+        __stcg(S + s0 + x, acc);
+      }
+    } else if (ns > 0) {
+      const int groups = min(nr, (int)blockDim.x / ns);   // >= 2
+      const int t = threadIdx.x, el = t % ns, g = t / ns;
+      if (g < groups) {
+        float acc = 0.f;
+        for (int q = g; q < nr; q += groups) acc += __ldcg(P + (size_t)q * E + s0 + el);
+        tmp[g * ns + el] = acc;
+      }
+      __syncthreads();
+      for (int x = threadIdx.x; x < ns; x += blockDim.x) {
+        float acc = 0.f;
+        for (int q = 0; q < groups; ++q) acc += tmp[q * ns + x];
+        __stcg(S + s0 + x, acc);
+      }
+    }
+    grid_barrier(bar, nr, status, dead);
+    for (int e = e0 + (int)threadIdx.x; e < e1; e += blockDim.x) put(e, __ldcg(S + e));
+  }
+  __device__ void finish() {}
+};
+
+template <class Comm>
+__device__ __forceinline__ void orth_rs_body(const OrthRsArgs& a, Comm& comm, float* sm, const KcLayout& L,
+                                             unsigned long long& badmask) {
   const int tid = threadIdx.x;
-  const KcLayout L = kc_layout(a.kqmax, a.zmax, a.rows, (int)cl.num_blocks());
   const int KP = L.KP, ZP = L.ZP, RP = L.RP;
-  const unsigned rank = cl.block_rank();
+  const unsigned rank = (unsigned)comm.rank();
   const int64_t r0 = (int64_t)rank * a.rows;
   const int rc = (int)imax(0, imin(a.rows, a.m - r0));
   float* share0 = sm + L.share;
@@ -233,17 +331,17 @@ __global__ void __launch_bounds__(KC_THREADS, 1) k_orth_cluster_rs(const __grid_
       if (tid == 0) badmask = 0ull;
       __syncthreads();
       auto reduce = [&](bool qz, bool zz) {
-        float* mine = share0 + (size_t)(phase & 1) * (KP + ZP) * ZP;
+        float* mine = share0 + (size_t)(L.share_bufs == 2 ? (phase & 1) : 0) * (KP + ZP) * ZP;
         if (qz) tn_tile(Qc, KP, kp, Zc, ZP, bz, RP, mine, bz);
         if (zz) tn_split(Zc, ZP, bz, Zc, ZP, bz, RP, mine + kp * bz, bz, tmp);
-        cl.sync();
+        __syncthreads();
         const int e0 = qz ? 0 : kp * bz, e1 = zz ? E : kp * bz;
         auto put = [&](int e, float s) {
           const int row = e / bz, j = e % bz;
           if (row < kp) P[e] = s;
           else if (row - kp < zc && j < zc) Gm[(row - kp) * (zc + 1) + j] = s;
         };
-        cluster_reduce_scatter_gather(cl, mine, sm + L.slice + (size_t)(phase & 1) * L.slice_len, e0, e1, put);
+        comm.reduce(mine, phase, e0, e1, put);
         __syncthreads();
         ++phase;
       };
@@ -350,7 +448,31 @@ __global__ void __launch_bounds__(KC_THREADS, 1) k_orth_cluster_rs(const __grid_
       a.Xg[(r0 + i) * a.xld + t] = (t < c) ? Zc[i * ZP + t] : 0.f;
     }
   }
-  cl.sync();   // no CTA leaves while others may still read its shares
+  comm.finish();
+}
+
+__global__ void __launch_bounds__(KC_THREADS, 1) k_orth_cluster_rs(const __grid_constant__ OrthRsArgs a) {
+  extern __shared__ __align__(16) float sm[];
+  __shared__ unsigned long long badmask;
+  ClusterComm comm{cg::this_cluster(), nullptr, 0};
+  const KcLayout L = kc_layout(a.kqmax, a.zmax, a.rows, comm.nranks());
+  comm.slices = sm + L.slice;
+  comm.slice_len = L.slice_len;
+  orth_rs_body(a, comm, sm, L, badmask);
+}
+
+// The same sequence over all CTAs of a cooperative launch, for blocks with
+// more rows than one cluster holds; the shares go through global memory.
+__global__ void __launch_bounds__(KC_THREADS, 1) k_orth_grid_rs(const __grid_constant__ OrthRsArgs a) {
+  extern __shared__ __align__(16) float sm[];
+  __shared__ unsigned long long badmask;
+  __shared__ int dead;
+  __shared__ float gtmp[KC_THREADS];
+  if (threadIdx.x == 0) dead = 0;
+  __syncthreads();
+  GridComm comm{(int)gridDim.x, (int)blockIdx.x, a.gparts, a.gsums, a.eslot, a.gbar, a.status, &dead, gtmp};
+  const KcLayout L = kc_layout(a.kqmax, a.zmax, a.rows, 0);
+  orth_rs_body(a, comm, sm, L, badmask);
 }
 
 }  // namespace
@@ -410,7 +532,95 @@ bool kc_schedulable(int nc, size_t smem) {
   return ok;
 }
 
+// Grid form: one CTA per SM at most (every CTA of the cooperative launch
+// resident), at least 16 rows each.
+struct KgConfig {
+  int nr = 0, rows = 0, E = 0;
+  size_t smem = 0;
+};
+
+int kg_device_ctas() {
+  static std::mutex mu;
+  static std::map<int, int> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find(dev);
+  if (it != cache.end()) return it->second;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 0;
+  int coop = 0;
+  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) sms = 0;
+  cudaGetLastError();
+  cache[dev] = sms;
+  return sms;
+}
+
+bool kg_config(int64_t m, int kqmax, int zmax, KgConfig* cfg) {
+  if (m < 1 || zmax < 1 || zmax > 64 || kqmax > 256) return false;
+  const int maxr = kg_device_ctas();
+  if (maxr < 1) return false;
+  const int64_t nr0 = imin((int64_t)maxr, imax((int64_t)1, ceil_div(m, 16)));
+  const int64_t rows = ceil_div(m, nr0);
+  const KcLayout L = kc_layout(kqmax, zmax, (int)rows, 0);
+  const size_t smem = L.total * sizeof(float);
+  if (smem > (size_t)KC_SMEM_MAX) return false;
+  cfg->rows = (int)rows;
+  cfg->nr = (int)ceil_div(m, rows);
+  cfg->E = (L.KP + L.ZP) * L.ZP;
+  cfg->smem = smem;
+  return true;
+}
+
 }  // namespace
+
+bool orth_grid_rs_ok(int64_t m, int kq0, int zc, int c) {
+  KgConfig cfg;
+  return c >= 1 && c <= zc && kg_config(m, kq0 + c, zc, &cfg);
+}
+
+size_t orth_grid_rs_scratch_floats(int64_t m, int kq0, int zc) {
+  KgConfig cfg;
+  if (!kg_config(m, kq0 + zc, zc, &cfg)) return 0;
+  return 4 + 2 * (size_t)cfg.nr * cfg.E + 2 * (size_t)cfg.E;
+}
+
+cudaError_t launch_orth_grid_rs(const float* Y, int64_t ldy, int zc, int64_t m, int c, int kq0, float* Q,
+                                int64_t ldq, float* Xg, int xld, uint64_t seed, float* scratch, int* status,
+                                cudaStream_t st) {
+  if (c < 1 || c > zc || (Xg && xld < pad4(c)) || !scratch) return cudaErrorInvalidValue;
+  OrthRsArgs a = {};
+  a.Y = Y; a.ldy = ldy; a.Q = Q; a.ldq = ldq; a.Xg = Xg; a.xld = xld; a.m = m;
+  a.kq0 = kq0; a.zc0 = zc; a.c = c; a.status = status; a.seed = seed;
+  a.kqmax = kq0 + c;
+  a.zmax = zc;
+  KgConfig cfg;
+  if (!kg_config(m, a.kqmax, zc, &cfg)) return cudaErrorInvalidValue;
+  a.rows = cfg.rows;
+  a.eslot = cfg.E;
+  a.gbar = reinterpret_cast<unsigned*>(scratch);
+  a.gparts = scratch + 4;
+  a.gsums = a.gparts + 2 * (size_t)cfg.nr * cfg.E;
+  cudaError_t e = raise_smem_limit(k_orth_grid_rs);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(a.gbar, 0, 4 * sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3(cfg.nr);
+  lc.blockDim = dim3(KC_THREADS);
+  lc.dynamicSmemBytes = cfg.smem;
+  lc.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  lc.attrs = attr;
+  lc.numAttrs = 1;
+  ProfScope prof("orth_grid", st, 0, 0);
+  note_launch("orth_grid");
+  e = cudaLaunchKernelEx(&lc, k_orth_grid_rs, a);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
 
 bool orth_cluster_rs_ok(int64_t m, int kq0, int zc, int c) {
   KcConfig cfg;

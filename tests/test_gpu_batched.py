@@ -32,7 +32,7 @@ def _noisy_tt(dims, ranks, seed, level):
 
 
 # uneven orders, ragged modes (tensor-core and SIMT passes), exhaustion and
-# Krylov modes, rank clamping
+# Krylov modes, rank clamping, blocks taller than a cluster
 SMALL = [
     ((16, 16, 16, 16), (4, 4, 4), 5, 2),
     ((37, 29, 41), (5, 6), 3, 3),
@@ -42,6 +42,7 @@ SMALL = [
     ((8, 64, 64, 16), (6, 12, 9), 5, 2),
     ((3, 200), (7,), 2, 1),
     ((12, 12, 12, 12, 12), (16, 16, 16, 16), 5, 2),
+    ((1100, 6, 5, 4), (8, 6, 4), 4, 2),          # 1100-row blocks: cooperative-launch orthonormalisation
 ]
 
 

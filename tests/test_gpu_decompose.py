@@ -183,3 +183,56 @@ def test_rank_clamp_and_order2(tt):
     got, rr = gpu_decompose(tt, B, (6,), 4, 2, seed=5)
     ref = oracle.tt_rbki(B.astype(np.float32), (6,), 4, 2, seed=5)
     assert oracle.tt_distance(got, ref) <= FP32_TOL
+
+
+# unfoldings with more rows than one thread-block cluster holds (m > 1024):
+# the block orthonormalisation runs over all CTAs of a cooperative launch
+CASES_TALL = [
+    # dims, generating ranks, target ranks, p, q, noise
+    ((1100, 6, 5, 4), (8, 6, 4), (8, 6, 4), 4, 2, 0.05),             # m = 1100 at mode 1
+    ((20, 60, 30, 24), (20, 16, 10), (20, 16, 10), 4, 2, 0.03),      # m = 1200 at mode 2
+    ((2050, 16, 16), (12, 6), (12, 6), 5, 3, 0.02),                  # m = 2050, n = 256
+]
+
+
+@pytest.mark.parametrize("case", CASES_TALL)
+def test_tall_blocks_fp32_match_oracle(tt, case):
+    dims, gr, ranks, p, q, noise = case
+    A = noisy_tt(dims, gr, 53, noise)
+    rr = oracle.clamp_ranks(dims, ranks)
+    om = W.explicit_omegas(dims, rr, p, 59)
+    ref = oracle.tt_rbki(A.astype(np.float32), ranks, p, q, omegas=om)
+    tt.profile_begin(event_timing=False)
+    got, rr_gpu = gpu_decompose(tt, A, ranks, p, q, omegas=om, exhaust=False, gram_power=False)
+    fams = tt.profile_end()
+    assert "orth_grid" in fams
+    assert rr_gpu == rr
+    assert oracle.tt_distance(got, ref) <= FP32_TOL
+    for G in got[:-1]:
+        assert oracle.left_orthogonality_defect(G) < 1e-4
+
+
+@pytest.mark.parametrize("case", CASES_TALL)
+def test_tall_blocks_bf16_error_criterion(tt, case):
+    dims, gr, ranks, p, q, noise = case
+    A = noisy_tt(dims, gr, 61, noise)
+    eps_ref = oracle.tt_error(A, oracle.tt_rbki(A, ranks, p, q, seed=7))
+    got, _ = gpu_decompose(tt, A, ranks, p, q, storage="bf16", seed=7)
+    assert oracle.tt_error(A, got) <= 1.05 * eps_ref + 1e-4
+
+
+def test_tall_rank_deficient_blocks_repaired(tt):
+    """Target ranks above the TT ranks of an exact low-rank tensor: from the
+    second Krylov block on, the blocks of the 1500-row unfolding are
+    numerically inside the span of the basis; their columns are replaced
+    inside the launch by pseudo-random vectors, the cores stay orthonormal
+    and the tensor is recovered exactly (to FP32 working accuracy)."""
+    dims = (1500, 8, 6, 5)
+    A = noisy_tt(dims, (3, 3, 2), 67, 0.0)
+    tt.profile_begin(event_timing=False)
+    got, _ = gpu_decompose(tt, A, (10, 8, 5), 3, 2, seed=9, exhaust=False, gram_power=False)
+    fams = tt.profile_end()
+    assert "orth_grid" in fams and "orth_block" not in fams
+    assert oracle.tt_error(A, got) < 2e-5
+    for G in got[:-1]:
+        assert oracle.left_orthogonality_defect(G) < 1e-4

@@ -41,7 +41,7 @@ def _spectra(k, seed):
 
 
 SIZES = [(1, 1), (2, 1), (3, 2), (17, 5), (32, 20), (33, 32), (40, 20), (64, 30), (96, 25), (150, 20),
-         (160, 32), (161, 20), (200, 30), (224, 10)]
+         (130, 31), (160, 30), (160, 32), (161, 20), (200, 30), (224, 10)]
 
 
 @pytest.mark.parametrize("k,r", SIZES)
