@@ -163,12 +163,17 @@ __device__ void tri_lu_solve(const float* w, int k, float* x) {
 }  // namespace
 
 // Shared-memory floats of k_eig_vectors for k (padded to KM = 32 KT) and r.
+// Odd row strides for the vectors (k + 1 or k + 2) and the per-vector
+// inverse-iteration factors (5 k or 5 k + 1): one thread per vector walks
+// its row, so an odd stride keeps the 32 threads on 32 banks.
+__host__ __device__ inline int er_ldx(int k) { return (k + 1) | 1; }
+__host__ __device__ inline int er_ldw(int k) { return (5 * k) | 1; }
 __host__ __device__ inline size_t er_union_floats(int k, int r) {
-  const size_t a = (size_t)k * k, b = (size_t)r * 5 * k;
+  const size_t a = (size_t)k * k, b = (size_t)r * er_ldw(k);
   return a > b ? a : b;
 }
 __host__ __device__ inline size_t er_smem_floats(int KM, int k, int r) {
-  return er_union_floats(k, r) + 4 * (size_t)KM + 32 + 64 + 1024 + 2 * (size_t)r * (k + 1) + 3 * 33 * 32 + 8;
+  return er_union_floats(k, r) + 4 * (size_t)KM + 32 + 64 + 1024 + 2 * (size_t)r * er_ldx(k) + 3 * 33 * 32 + 8;
 }
 
 // Sum over the 32 lanes of NV values x[0..NV) (NV a power of two <= 32) with
@@ -449,7 +454,7 @@ __global__ void __launch_bounds__(512, 1) k_eig_vectors(const float* __restrict_
   // the reflectors (step 5) and the inverse-iteration factors (step 3) are
   // never live together: one region holds both
   float* Vs = sm;                         // [k][k], row j = reflector v_j
-  float* Wk = sm;                         // [r][5k] inverse-iteration factors
+  float* Wk = sm;                         // [r][ldw] inverse-iteration factors
   float* tau = sm + er_union_floats(k, r);   // [KM]
   float* d = tau + KM;                    // [KM]
   float* e = d + KM;                      // [KM]
@@ -457,14 +462,14 @@ __global__ void __launch_bounds__(512, 1) k_eig_vectors(const float* __restrict_
   float* lam = e2 + KM;                   // [32]
   float* red = lam + 32;                  // [64]
   int* cnt = reinterpret_cast<int*>(red + 64);   // [1024]
-  float* X = reinterpret_cast<float*>(cnt + 1024);   // [r][k + 1]
-  float* X2 = X + (size_t)r * (k + 1);    // [r][k + 1]
-  float* G = X2 + (size_t)r * (k + 1);    // [32][33]
+  float* X = reinterpret_cast<float*>(cnt + 1024);   // [r][ldx]
+  float* X2 = X + (size_t)r * er_ldx(k);   // [r][ldx]
+  float* G = X2 + (size_t)r * er_ldx(k);  // [32][33]
   float* Rm = G + 33 * 32;                // [32][32]
   float* Tm = Rm + 33 * 32;               // [32][32]
   int* sflag = reinterpret_cast<int*>(Tm + 33 * 32);
   const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 5;
-  const int ldx = k + 1;
+  const int ldx = er_ldx(k);
   for (int i = tid; i < k; i += NT) {
     tau[i] = tau_g[i];
     d[i] = d_g[i];
@@ -566,16 +571,13 @@ __global__ void __launch_bounds__(512, 1) k_eig_vectors(const float* __restrict_
   for (int round = 0; round < 2; ++round) {
     if (tid < r) {
       float* x = cur + (size_t)tid * ldx;
-      float* w = Wk + (size_t)tid * 5 * k;
+      float* w = Wk + (size_t)tid * er_ldw(k);
       if (round == 0) {
         tri_lu(d, e, k, lam[tid], tiny, w);
-        // start vector 1 + 0.01 ((7 i + 13 tid) mod 11), the residue stepped
-        int res = (13 * tid) % 11;
-        for (int i = 0; i < k; ++i) {
-          x[i] = 1.f + 0.01f * (float)res;
-          res += 7;
-          if (res >= 11) res -= 11;
-        }
+        // start vector 1 + 0.01 h(tid, i), h pseudo-random in [-1, 1) and
+        // different for every vector: equal shifts (a cluster below FP32
+        // resolution) must not produce equal vectors
+        for (int i = 0; i < k; ++i) x[i] = fmaf(0.01f, hash_uniform(0xE16ull + (uint64_t)tid, (uint64_t)i), 1.f);
       }
       tri_lu_solve(w, k, x);
       float mx = 0.f;
@@ -658,8 +660,12 @@ __global__ void __launch_bounds__(512, 1) k_eig_vectors(const float* __restrict_
     if (*sflag) {
       // Gram-Schmidt twice in descending eigenvalue order (a Cholesky pass
       // that was applied leaves the span of each leading set unchanged)
-      for (int j = 0; j < r; ++j) {
+      for (int j = 0, attempt = 0; j < r;) {
         float* xj = cur + (size_t)j * ldx;
+        float p0 = 0.f;
+        for (int i = tid; i < k; i += NT) p0 = fmaf(xj[i], xj[i], p0);
+        const float n0 = sqrtf(block_sum(p0, red));
+        __syncthreads();
         for (int pass = 0; pass < 2 && j > 0; ++pass) {
           for (int i2 = ty; i2 < j; i2 += NW) {
             const float* xi = cur + (size_t)i2 * ldx;
@@ -679,9 +685,22 @@ __global__ void __launch_bounds__(512, 1) k_eig_vectors(const float* __restrict_
         float pp = 0.f;
         for (int i = tid; i < k; i += NT) pp = fmaf(xj[i], xj[i], pp);
         const float nrm = sqrtf(block_sum(pp, red));
+        __syncthreads();
+        if (!(nrm > 1e-4f * n0) && attempt < 3) {
+          // numerically inside the span of the earlier vectors (a cluster
+          // below FP32 resolution): any direction orthogonal to them serves,
+          // take a pseudo-random one through the same projections
+          for (int i = tid; i < k; i += NT)
+            xj[i] = hash_uniform(0x65A0ull + 64ull * (uint64_t)attempt + (uint64_t)j, (uint64_t)i);
+          __syncthreads();
+          ++attempt;
+          continue;
+        }
         const float inv = nrm > 0.f ? 1.f / nrm : 0.f;
         for (int i = tid; i < k; i += NT) xj[i] *= inv;
         __syncthreads();
+        ++j;
+        attempt = 0;
       }
     }
     __syncthreads();

@@ -97,10 +97,7 @@ __device__ void orth_finish(const OrthArgs& a, int nctas, int prod, int fin, flo
   // Cholesky and triangular inverse in shared memory, then T to global
   float* Rs = diag0 + 64;              // [b][b]
   float* Ts = Rs + b * b;              // [b][b]
-  if (b <= 32)
-    chol_inv_warp32_call(G, b + 1, b, diag0, Rs, b, Ts, b, a.flag, true);
-  else
-    chol_inv_cta(G, b + 1, b, diag0, Rs, b, Ts, b, a.flag, true);
+  chol_inv_fast(G, b + 1, b, diag0, Rs, b, Ts, b, a.flag, true);
   for (int e = tid; e < b * b; e += blockDim.x) a.T[e] = Ts[e];
 }
 

@@ -147,10 +147,7 @@ __global__ void __launch_bounds__(OC_THREADS, 1) k_orth_cluster(ClusterOrthArgs 
       for (int x = tid; x < bp * bp; x += blockDim.x) T[x] = 0.f;
       __syncthreads();
     }
-    if (bc <= 32)
-      chol_inv_warp32_call(G, b + 1, bc, diag0, R, b, T, bp, fl, rep);
-    else
-      chol_inv_cta(G, b + 1, bc, diag0, R, b, T, bp, fl, rep);
+    chol_inv_fast(G, b + 1, bc, diag0, R, b, T, bp, fl, rep);
   };
   auto write_q = [&](int cols) {
     for (int x = tid; x < rc * cols; x += blockDim.x) {

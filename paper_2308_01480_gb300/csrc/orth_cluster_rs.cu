@@ -363,10 +363,7 @@ __device__ __forceinline__ void orth_rs_body(const OrthRsArgs& a, Comm& comm, fl
       auto factor = [&](int bc) {
         for (int x = tid; x < bz * bz; x += blockDim.x) T[x] = 0.f;
         __syncthreads();
-        if (bc <= 32)
-          chol_inv_warp32_call(Gm, zc + 1, bc, diag0, R, zc, T, bz, nullptr, false, &badmask);
-        else
-          chol_inv_cta(Gm, zc + 1, bc, diag0, R, zc, T, bz, nullptr, false, &badmask);
+        chol_inv_fast(Gm, zc + 1, bc, diag0, R, zc, T, bz, nullptr, false, &badmask);
       };
       if (kq > 0) {
         reduce(true, false);                     // A

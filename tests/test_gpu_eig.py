@@ -1,6 +1,7 @@
 """The Rayleigh-Ritz eigensolver (Alg. 3 steps 6-8) against LAPACK.
 
-For symmetric H with random, graded, clustered and rank-deficient spectra
+For symmetric H with random, graded, clustered, rank-deficient spectra and
+a cluster of eigenvalues far below FP32 resolution
 the r largest eigenvalues must match numpy.linalg.eigh to 1e-5 ||H|| and
 the eigenvectors must be orthonormal with residual ||H v - lam v|| below
 2e-5 ||H||; for eigenvalues separated from the rest by a gap g, the
@@ -36,6 +37,11 @@ def _spectra(k, seed):
         "clustered": np.concatenate([np.full(k // 3, 1.0) + 1e-7 * rng.standard_normal(k // 3),
                                      rng.random(k - k // 3) * 0.5]),
         "rank_deficient": np.concatenate([rng.random(max(1, k // 4)) + 1.0, np.zeros(k - max(1, k // 4))]),
+        # a few large eigenvalues, the rest a cluster far below FP32
+        # resolution (Rayleigh-Ritz on an exactly low-rank unfolding): the
+        # wanted vectors inside the cluster must still come out orthonormal
+        "tiny_cluster": np.concatenate([rng.random(max(1, k // 16)) + 1.0,
+                                        1e-10 * rng.random(k - max(1, k // 16))]),
     }
     return out
 
