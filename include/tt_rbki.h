@@ -115,6 +115,19 @@ typedef struct {
                            without Rayleigh-Ritz.  With TT_METHOD_RSI, Alg. 4
                            taken literally: (C C^T)^q C W(:, 1:r_k).  The
                            exhaustion Gram routes are not used.               */
+  int32_t accurate_rr;  /* 0 (default): Rayleigh-Ritz on H = Q^T C C^T Q
+                           formed from the FP32 powers, eigenvectors in FP32
+                           (H holds squared singular values: directions with
+                           sigma_j / sigma_1 below ~2.4e-4 drown in its
+                           rounding).  1: the singular vectors of
+                           B = Q^T C (Alg. 3 step 7) without that loss: B by
+                           an FP32 projection pass, H = B B^T with exact FP32
+                           products and compensated (double-FP32) sums, FP64
+                           partial sums and an FP64 Cholesky H = L L^T, and
+                           one-sided Jacobi on L in FP32; the exhaustion
+                           route over rows takes B = C.  Needs bases of at
+                           most 160 columns; the column-Gram exhaustion route
+                           is not used.  Not combined with paper_literal.     */
   int32_t reserved;     /* must be zero                                       */
 } tt_options;
 

@@ -38,12 +38,14 @@ def _stream_handle(stream):
 
 
 def options(storage=N.TT_F32, remainder=None, exhaust_gram=True, batch_streams=0, method=N.TT_METHOD_RBKI,
-            gram_power=True, paper_literal=False):
+            gram_power=True, paper_literal=False, accurate_rr=False):
     """tt_options with the given fields (remainder None = same as storage;
     method TT_METHOD_RBKI (Alg. 3) or TT_METHOD_RSI (Alg. 4); q = 0 with
     either is TT-rSVD, Alg. 2; gram_power False makes every Krylov power
     stream the unfolding; paper_literal True takes the paper's steps
-    literally, first-r truncation without Rayleigh-Ritz)."""
+    literally, first-r truncation without Rayleigh-Ritz; accurate_rr True
+    takes the Rayleigh-Ritz vectors from B = Q^T C without squaring it in
+    FP32: compensated Gram, FP64 Cholesky, one-sided Jacobi)."""
     o = N.TTOptions()
     N.check(N.lib().tt_rbki_default_options(ctypes.byref(o)))
     o.storage = int(storage)
@@ -53,6 +55,7 @@ def options(storage=N.TT_F32, remainder=None, exhaust_gram=True, batch_streams=0
     o.method = int(method)
     o.gram_power = 1 if gram_power else 0
     o.paper_literal = 1 if paper_literal else 0
+    o.accurate_rr = 1 if accurate_rr else 0
     return o
 
 

@@ -24,7 +24,7 @@ class TTOptions(ctypes.Structure):
     _fields_ = [("storage", ctypes.c_int32), ("remainder", ctypes.c_int32),
                 ("exhaust_gram", ctypes.c_int32), ("batch_streams", ctypes.c_int32),
                 ("method", ctypes.c_int32), ("gram_power", ctypes.c_int32),
-                ("paper_literal", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("paper_literal", ctypes.c_int32), ("accurate_rr", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class TTModePlan(ctypes.Structure):

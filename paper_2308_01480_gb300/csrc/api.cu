@@ -52,7 +52,8 @@ struct Plan {
   std::vector<ModePlan> modes;
   // workspace offsets in bytes
   size_t off_status = 0, off_R0 = 0, off_R1 = 0, off_S = 0, off_T = 0, off_part = 0, off_Y = 0,
-         off_Q = 0, off_W = 0, off_U = 0, off_G = 0, off_small = 0, off_X = 0, off_Xg = 0, total = 0;
+         off_Q = 0, off_W = 0, off_U = 0, off_G = 0, off_small = 0, off_X = 0, off_Xg = 0, off_B = 0, off_Hd = 0,
+         off_dfp = 0, total = 0;
 };
 
 tt_status resolve_options(const tt_options* in, tt_options* out) {
@@ -65,6 +66,9 @@ tt_status resolve_options(const tt_options* in, tt_options* out) {
     return fail(TT_EINVAL, "options.method must be TT_METHOD_RBKI or TT_METHOD_RSI");
   if (out->gram_power != 0 && out->gram_power != 1) return fail(TT_EINVAL, "options.gram_power must be 0 or 1");
   if (out->paper_literal != 0 && out->paper_literal != 1) return fail(TT_EINVAL, "options.paper_literal must be 0 or 1");
+  if (out->accurate_rr != 0 && out->accurate_rr != 1) return fail(TT_EINVAL, "options.accurate_rr must be 0 or 1");
+  if (out->accurate_rr && out->paper_literal)
+    return fail(TT_EINVAL, "options.accurate_rr and options.paper_literal exclude each other");
   if (out->reserved != 0) return fail(TT_EINVAL, "options.reserved must be zero");
   return TT_OK;
 }
@@ -110,7 +114,7 @@ tt_status build_plan(const int64_t* dims, int d, const int64_t* ranks, int p, in
   for (int k = 0; k < d; ++k) total *= dims[k];
   int64_t n = total;
   size_t maxR = 0, maxS = 0, maxT = 0, maxPart = 0, maxY = 0, maxQ = 0, maxU = 0, maxG = 0, maxSmall = 0,
-         maxX = 0, maxXg = 0;
+         maxX = 0, maxXg = 0, maxB = 0, maxHd = 0, maxDf = 0;
   for (int k = 0; k < d - 1; ++k) {
     ModePlan& M = P.modes[k];
     n /= dims[k];
@@ -138,7 +142,9 @@ tt_status build_plan(const int64_t* dims, int d, const int64_t* ranks, int p, in
     M.kq = (int)cols;
     M.gram_route = P.o.exhaust_gram && cols == M.D && M.D == M.m && M.m <= 128;
     M.gram_cols = P.o.exhaust_gram && !M.gram_route && cols == M.D && M.D == M.n && M.n < M.m &&
-                  ttr::eig_top_ok((int)M.n);
+                  ttr::eig_top_ok((int)M.n) && !P.o.accurate_rr;
+    if (P.o.accurate_rr && !M.gram_route && M.kq > ttr::RR_SVD_KMAX)
+      return fail(TT_EUNSUPPORTED, "options.accurate_rr needs Krylov bases of at most 160 columns");
     if (P.o.paper_literal) {
       // Alg. 3 steps 4-8 (Alg. 4 steps 4-12, Alg. 2 for q = 0) taken
       // literally: the kept r columns span (C C^T)^s C W(:, 1:r), s = min(q, 1)
@@ -215,6 +221,15 @@ tt_status build_plan(const int64_t* dims, int d, const int64_t* ranks, int p, in
       // padded copy of the current block for the power
       maxXg = std::max(maxXg, (size_t)M.m * (size_t)((M.b + 3) & ~3));
     }
+    if (P.o.accurate_rr && !M.gram_cols) {
+      // B = Q^T C (kq x n; the row-exhaustion route takes B = C), the FP64
+      // Gram B B^T and its per-CTA partials
+      const int kk = M.gram_route ? (int)M.m : M.kq;
+      if (!ttr::rr_svd_ok(kk, M.r_out)) return fail(TT_EUNSUPPORTED, "options.accurate_rr: basis too large");
+      if (!M.gram_route) maxB = std::max(maxB, (size_t)M.kq * (size_t)M.n);
+      maxHd = std::max(maxHd, (size_t)kk * kk);
+      maxDf = std::max(maxDf, ttr::gram_df_partial_doubles(kk, M.n));
+    }
   }
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + std::max<size_t>(bytes, 1)); return o; };
@@ -232,6 +247,9 @@ tt_status build_plan(const int64_t* dims, int d, const int64_t* ranks, int p, in
   P.off_small = take(maxSmall * 4);
   P.off_X = take(maxX);
   P.off_Xg = take(maxXg * 4);
+  P.off_B = take(maxB * 4);
+  P.off_Hd = take(maxHd * 8);
+  P.off_dfp = take(maxDf * 8);
   P.total = off;
   return TT_OK;
 }
@@ -248,7 +266,14 @@ tt_status run_mode(const Plan& P, int k, const TIn* C, char* ws, int* status, co
   float* U = (float*)(ws + P.off_U);
   float* small = (float*)(ws + P.off_small);
   const int r = M.r_out;
-  if (M.gram_route) {
+  if (M.gram_route && P.o.accurate_rr) {
+    // Alg. 3 steps 6-8 at exhaustion with B = C: the compensated Gram, FP64
+    // Cholesky, one-sided Jacobi (rr_svd.cu)
+    double* Hd = (double*)(ws + P.off_Hd);
+    double* dfp = (double*)(ws + P.off_dfp);
+    TTR_CUDA(ttr::gram_df<TIn>(C, (int)M.m, M.n, M.n, dfp, Hd, st));
+    TTR_CUDA(ttr::launch_rr_svd(Hd, (int)M.m, r, nullptr, M.m, 0, U, core, status, st));
+  } else if (M.gram_route) {
     float* G = (float*)(ws + P.off_G);
     if (use_tc && M.m <= 128)
       TTR_CUDA(ttr::tc_gram(Cb, M.m, M.n, part, G, status, st));
@@ -407,10 +432,23 @@ tt_status run_mode(const Plan& P, int k, const TIn* C, char* ws, int* status, co
         col += cj;
       }
     }
-    if (ttr::eig_top_ok(kq))
+    if (P.o.accurate_rr) {
+      // Alg. 3 steps 6-8 without squaring in FP32: B = Q^T C by FP32
+      // projections (one per Krylov block width), then rr_svd.cu
+      float* Bm = (float*)(ws + P.off_B);
+      double* Hd = (double*)(ws + P.off_Hd);
+      double* dfp = (double*)(ws + P.off_dfp);
+      for (int c0 = 0; c0 < kq; c0 += M.b) {
+        const int cw = std::min(M.b, kq - c0);
+        TTR_CUDA((ttr::simt_proj<TIn, float>(C, M.m, M.n, Q + c0, kq, cw, Bm + (size_t)c0 * M.n, M.n, st, part)));
+      }
+      TTR_CUDA(ttr::gram_df<float>(Bm, kq, M.n, M.n, dfp, Hd, st));
+      TTR_CUDA(ttr::launch_rr_svd(Hd, kq, r, Q, M.m, kq, U, core, status, st));
+    } else if (ttr::eig_top_ok(kq)) {
       TTR_CUDA(ttr::launch_rr_fast(Q, W, kq, M.m, kq, r, 0, small, U, core, st));
-    else
+    } else {
       TTR_CUDA(ttr::launch_rayleigh_ritz(Q, W, kq, M.m, kq, r, 0, small, U, core, st));
+    }
     }
   }
   // Alg. 3 step 10: next remainder R = U^T C (r x n)

@@ -132,6 +132,17 @@ cudaError_t launch_eig_reg(const float* H, int64_t ldh, int k, int r, float* V, 
                            float* scratch, cudaStream_t st);
 
 // ---- Rayleigh-Ritz through a tridiagonal eigensolver (eig.cu)
+// Rayleigh-Ritz through the singular vectors of B = Q^T C (rr_svd.cu):
+// H = B B^T with exact FP32 products and compensated sums (per-CTA partials
+// summed in FP64), FP64 Cholesky, one-sided Jacobi in FP32 on the factor.
+constexpr int RR_SVD_KMAX = 160;
+int gram_df_splits(int k, int64_t n);
+size_t gram_df_partial_doubles(int k, int64_t n);
+template <typename T>
+cudaError_t gram_df(const T* B, int k, int64_t n, int64_t ldb, double* partials, double* H, cudaStream_t st);
+bool rr_svd_ok(int k, int r);
+cudaError_t launch_rr_svd(const double* H, int k, int r, const float* Q, int64_t m, int64_t ldq, float* U,
+                          float* core, int* status, cudaStream_t st);
 bool eig_top_ok(int k);
 size_t rr_fast_scratch_floats(int64_t m, int k, int r);
 size_t eig_scratch_floats(int k, int r);

@@ -90,6 +90,17 @@ def test_invalid_arguments_rejected_on_host(L):
     opts.paper_literal = 2
     assert L.tt_rbki_workspace_size(N.i64_array([5, 4, 3]), 3, N.i64_array([2, 2]), 1, 1, ctypes.byref(opts),
                                     ctypes.byref(nb)) == N.TT_EINVAL
+    L.tt_rbki_default_options(ctypes.byref(opts))
+    assert opts.accurate_rr == 0
+    opts.accurate_rr = 2
+    assert L.tt_rbki_workspace_size(N.i64_array([5, 4, 3]), 3, N.i64_array([2, 2]), 1, 1, ctypes.byref(opts),
+                                    ctypes.byref(nb)) == N.TT_EINVAL
+    opts.accurate_rr, opts.paper_literal = 1, 1      # the two study forms exclude each other
+    assert L.tt_rbki_workspace_size(N.i64_array([5, 4, 3]), 3, N.i64_array([2, 2]), 1, 1, ctypes.byref(opts),
+                                    ctypes.byref(nb)) == N.TT_EINVAL
+    opts.paper_literal = 0
+    assert L.tt_rbki_workspace_size(N.i64_array([5, 4, 3]), 3, N.i64_array([2, 2]), 1, 1, ctypes.byref(opts),
+                                    ctypes.byref(nb)) == N.TT_OK
     perm = (ctypes.c_int * 3)(0, 0, 1)
     assert L.tt_permute_convert(ctypes.c_void_p(256), 0, N.i64_array([2, 3, 4]), N.i64_array([12, 4, 1]),
                                 perm, 3, ctypes.c_void_p(512), 0, None) == N.TT_EINVAL
