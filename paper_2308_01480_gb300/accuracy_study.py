@@ -1,6 +1,7 @@
 """The paper's synthetic accuracy study (Sec. 4.1, 4.2) on the GPU: time,
-relative error and PSNR of TT-rBKI (Alg. 3), TT-rSI (Alg. 4), TT-rSVD
-(Alg. 2) and TT-SVD (Alg. 1) at fixed target ranks.
+relative error and PSNR of TT-rBKI (Alg. 3; also with the accurate_rr
+Rayleigh-Ritz, tt_rbki_acc), TT-rSI (Alg. 4), TT-rSVD (Alg. 2) and TT-SVD
+(Alg. 1) at fixed target ranks.
 
     python -m paper_2308_01480_gb300.accuracy_study e2 --ranks 2-11
     python -m paper_2308_01480_gb300.accuracy_study e6 --ranks 2-11 --snr 5
@@ -22,7 +23,7 @@ import sys
 
 import numpy as np
 
-METHODS = ("tt_rbki", "tt_rsi", "tt_rsvd", "tt_svd")
+METHODS = ("tt_rbki", "tt_rbki_acc", "tt_rsi", "tt_rsvd", "tt_svd")
 
 
 def error_and_psnr(A64, cores):
@@ -81,7 +82,8 @@ def run_case(A, ranks, oversample, q, seed, methods=METHODS):
             method = tt.TT_METHOD_RSI if name == "tt_rsi" else tt.TT_METHOD_RBKI
             qm = 0 if name == "tt_rsvd" else q
             pb = tt.Problem(t32, ranks, oversample, qm, seed)
-            g = tt.BatchGraph([pb], tt.options(storage=tt.TT_F32, method=method))
+            g = tt.BatchGraph([pb], tt.options(storage=tt.TT_F32, method=method,
+                                               accurate_rr=(name == "tt_rbki_acc")))
             ms = _time(g.launch)
             if g.device_status() != [0]:
                 raise RuntimeError(f"{name}: device status not OK")

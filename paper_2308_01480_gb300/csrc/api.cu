@@ -434,13 +434,13 @@ tt_status run_mode(const Plan& P, int k, const TIn* C, char* ws, int* status, co
     }
     if (P.o.accurate_rr) {
       // Alg. 3 steps 6-8 without squaring in FP32: B = Q^T C by FP32
-      // projections (one per Krylov block width), then rr_svd.cu
+      // projections, then rr_svd.cu
       float* Bm = (float*)(ws + P.off_B);
       double* Hd = (double*)(ws + P.off_Hd);
       double* dfp = (double*)(ws + P.off_dfp);
-      for (int c0 = 0; c0 < kq; c0 += M.b) {
-        const int cw = std::min(M.b, kq - c0);
-        TTR_CUDA((ttr::simt_proj<TIn, float>(C, M.m, M.n, Q + c0, kq, cw, Bm + (size_t)c0 * M.n, M.n, st, part)));
+      for (int c0 = 0; c0 < kq; c0 += 64) {   // one pass per 64 basis columns
+        const int cw = std::min(64, kq - c0);
+        TTR_CUDA((ttr::simt_proj<TIn, float>(C, M.m, M.n, Q + c0, kq, cw, Bm + (size_t)c0 * M.n, M.n, st, nullptr)));
       }
       TTR_CUDA(ttr::gram_df<float>(Bm, kq, M.n, M.n, dfp, Hd, st));
       TTR_CUDA(ttr::launch_rr_svd(Hd, kq, r, Q, M.m, kq, U, core, status, st));

@@ -2,7 +2,7 @@
 float64 oracle, on reduced sizes of its tensors: for the h = 5 power
 function (E2), the same with 5 dB white noise (E6) and the decaying-spectrum
 diagonal tensor (E1), each method's cores meet the FP32 parity bar
-(TT-rBKI, TT-rSI, TT-rSVD: relative TT distance <= 1e-4 to the oracle with
+(TT-rBKI with either Rayleigh-Ritz, TT-rSI, TT-rSVD: relative TT distance <= 1e-4 to the oracle with
 the same seed; for E6, whose spectrum is nearly flat at the truncation
 rank, relative errors equal to 1e-4 relative and distance <= 1e-3; TT-SVD:
 relative error within 1e-4 relative of the oracle's), and
@@ -48,10 +48,11 @@ def test_study_case_matches_oracle(study, name, r):
     refs = {"tt_rbki": oracle.tt_rbki(A32, ranks, p, q, seed=seed),
             "tt_rsi": oracle.tt_rsi(A32, ranks, p, q, seed=seed),
             "tt_rsvd": oracle.tt_rbki(A32, ranks, p, 0, seed=seed)}
+    refs["tt_rbki_acc"] = refs["tt_rbki"]       # the same method, Rayleigh-Ritz without squaring
     for m, ref in refs.items():
         method = tt.TT_METHOD_RSI if m == "tt_rsi" else tt.TT_METHOD_RBKI
         cores, _ = tt.decompose(t32, ranks, p, 0 if m == "tt_rsvd" else q, omega_seed=seed,
-                                opts=tt.options(storage=tt.TT_F32, method=method))
+                                opts=tt.options(storage=tt.TT_F32, method=method, accurate_rr=(m == "tt_rbki_acc")))
         got = [c.cpu().double().numpy() for c in cores]
         Ahat = oracle.tt_full(got)
         eps_o, psnr_o = oracle.tt_error(A, got), oracle.psnr(A, Ahat)
