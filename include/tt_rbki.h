@@ -481,6 +481,76 @@ TT_API tt_status tt_debug_fill_shared(uint32_t bits, void* stream);
 TT_API tt_status tt_debug_wait_timeout(void* workspace, void* stream);
 
 /* ------------------------------------------------------------------------
+ * Sharded form: one problem split over `world` ranks (one GPU each) by its
+ * last mode.  Rank g holds the slab A[..., lo_g : lo_g + w_g] of the last
+ * index (slab g = [ceil(g I_d / world), ceil((g + 1) I_d / world))), so
+ * every unfolding C_k of Alg. 3 splits by columns (the last index is the
+ * fastest part of every column index) and each rank streams only its own
+ * columns.  The sketch Y = C Omega (Alg. 3 step 4, first block), each
+ * streamed Krylov power C C^T X (step 4) and, on the Gram routes, the Gram
+ * C C^T are sums over the ranks of the ranks' partial products; the block
+ * orthonormalisation, Rayleigh-Ritz and the cores 1..d-1 then run
+ * replicated on the summed blocks, and the projection U^T C_k (step 10)
+ * stays on its rank as its slab of the next unfolding.  The last core is
+ * returned as this rank's slab (r_{d-1} x w_g); the caller gathers it.
+ * The column-Gram exhaustion route, paper_literal and accurate_rr are not
+ * available in this form.  The paper runs on one machine and has no
+ * counterpart.
+ * ---------------------------------------------------------------------- */
+
+/* Sums `count` floats at device address `buf` over all ranks, in place.
+ * Called on the host in stream order: the library has enqueued the kernels
+ * that produce buf on `stream` (a cudaStream_t) and enqueues its next
+ * kernels after the call returns; the sum must be visible to work enqueued
+ * on `stream` afterwards (e.g. ncclAllReduce on that stream, or a stream
+ * synchronisation, a host exchange and a copy back).  Every rank must
+ * obtain bit-identical sums (the replicated steps rely on it).  Returns 0
+ * on success; anything else aborts the decomposition with TT_ECUDA. */
+typedef int32_t (*tt_allreduce_fn)(float* buf, int64_t count, void* stream, void* ctx);
+
+typedef struct {
+  int64_t m;             /* rows of the unfolding C_k                           */
+  int64_t n_global;      /* columns of the whole unfolding                      */
+  int64_t n_local;       /* this rank's columns (n_global / I_d * w)            */
+  int32_t route;         /* TT_ROUTE_* (never TT_ROUTE_GRAM_COLS)               */
+  int32_t allreduces;    /* calls of the sum callback in this mode              */
+  int64_t allreduce_floats;  /* floats summed in this mode, all calls           */
+} tt_shard_mode;
+
+/* The host-side plan of rank `rank` of `world`: its slab of the last mode
+ * (*slab_lo, *slab_w) and, per mode k = 1..d-1, the entry modes[k-1].  Pure
+ * host computation (no device, no stream).  Errors: TT_EINVAL (bad
+ * arguments, world > I_d, NULL outputs, max_modes < d-1), TT_EUNSUPPORTED
+ * (options outside the sharded form), and those of tt_rbki_workspace_size. */
+TT_API tt_status tt_rbki_shard_plan(const int64_t* dims, int d, const int64_t* ranks, int oversample, int q,
+                                    const tt_options* opts, int32_t world, int32_t rank, int64_t* slab_lo,
+                                    int64_t* slab_w, tt_shard_mode* modes, int max_modes);
+
+/* Workspace bytes of tt_rbki_decompose_sharded for this rank. */
+TT_API tt_status tt_rbki_sharded_workspace_size(const int64_t* dims, int d, const int64_t* ranks,
+                                                int oversample, int q, const tt_options* opts, int32_t world,
+                                                int32_t rank, size_t* bytes);
+
+/* Alg. 3 (or Alg. 4 with opts->method) on this rank's slab.
+ *   local_tensor  device, the slab A[..., lo : lo + w] row-major
+ *                 (I_1 x ... x I_{d-1} x w elements of opts->storage).
+ *   dims, ranks   the whole problem's sizes (host), as tt_rbki_decompose.
+ *   omega_seed    seed of the whole problem's Omega_k; each rank draws the
+ *                 rows of its own columns, identical to the single-GPU draw.
+ *   cores_out     d device pointers: cores 1..d-1 in full (replicated),
+ *                 core d as this rank's slab (r_{d-1} x w floats).
+ *   allreduce, ctx the sum callback (above) and its argument.
+ * Orders the work on `stream`; the sum callback is called from this call.
+ * Errors: as tt_rbki_decompose, TT_EINVAL for a NULL allreduce with
+ * world > 1, TT_ECUDA when the callback fails. */
+TT_API tt_status tt_rbki_decompose_sharded(const void* local_tensor, const int64_t* dims, int d,
+                                           const int64_t* ranks, int oversample, int q, uint64_t omega_seed,
+                                           float* const* cores_out, int64_t* ranks_out, void* workspace,
+                                           size_t workspace_bytes, int32_t world, int32_t rank,
+                                           tt_allreduce_fn allreduce, void* ctx, void* stream,
+                                           const tt_options* opts);
+
+/* ------------------------------------------------------------------------
  * Kernel accounting for benchmarks (no counterpart in the paper).
  * Between tt_rbki_profile_begin and tt_rbki_profile_end every kernel launch
  * of the library is counted per kernel family; with event_timing = 1 each

@@ -98,6 +98,72 @@ def plan_modes(dims, ranks, oversample, q, opts=None):
     return out
 
 
+def shard_plan(dims, ranks, oversample, q, world, rank, opts=None):
+    """Host-side plan of rank `rank` of `world` for the sharded form (no GPU
+    needed): (slab_lo, slab_w, modes), modes a list of dicts per mode with
+    the unfolding's rows, whole and local columns, route and the number of
+    sums over ranks (and floats summed) the mode needs."""
+    d = len(dims)
+    arr = (N.TTShardMode * max(1, d - 1))()
+    lo, w = ctypes.c_int64(), ctypes.c_int64()
+    N.check(N.lib().tt_rbki_shard_plan(N.i64_array(dims), d, N.i64_array(ranks), int(oversample), int(q),
+                                       ctypes.byref(opts) if opts is not None else None, int(world), int(rank),
+                                       ctypes.byref(lo), ctypes.byref(w), arr, d - 1))
+    modes = [dict(m=e.m, n_global=e.n_global, n_local=e.n_local, route=ROUTE_NAMES[e.route],
+                  allreduces=e.allreduces, allreduce_floats=e.allreduce_floats) for e in arr[:d - 1]]
+    return lo.value, w.value, modes
+
+
+def decompose_sharded(local_tensor, dims, ranks, oversample, q, world, rank, allreduce, omega_seed=0, opts=None,
+                      stream=None):
+    """Alg. 3 on this rank's slab A[..., lo : lo + w] of the last mode (a
+    contiguous CUDA tensor).  `allreduce(buf)` receives each partial block to
+    be summed over the ranks as a float32 CUDA tensor (a view into this
+    call's workspace) and must sum it in place in stream order on the
+    current stream (torch.distributed.all_reduce does).  Returns (cores,
+    ranks): cores 1..d-1 in full, core d as this rank's slab."""
+    torch = _torch()
+    d = len(dims)
+    if opts is None:
+        opts = options(storage=_dtype_code(local_tensor))
+    if not local_tensor.is_cuda or not local_tensor.is_contiguous():
+        raise ValueError("local_tensor must be a contiguous CUDA tensor")
+    lo, w, _ = shard_plan(dims, ranks, oversample, q, world, rank, opts)
+    if list(local_tensor.shape) != list(dims[:-1]) + [w]:
+        raise ValueError(f"local_tensor must have shape {list(dims[:-1]) + [w]}")
+    rr, _ = core_sizes(dims, ranks)
+    cores = [torch.empty((rr[k], dims[k] if k < d - 1 else w, rr[k + 1]), dtype=torch.float32,
+                         device=local_tensor.device) for k in range(d)]
+    nb = ctypes.c_size_t()
+    N.check(N.lib().tt_rbki_sharded_workspace_size(N.i64_array(dims), d, N.i64_array(ranks), int(oversample), int(q),
+                                                   ctypes.byref(opts), int(world), int(rank), ctypes.byref(nb)))
+    ws = torch.empty(nb.value, dtype=torch.uint8, device=local_tensor.device)
+    base = ws.data_ptr()
+    errors = []
+
+    def _cb(ptr, count, _stream, _ctx):
+        try:
+            off = int(ptr) - base
+            view = ws[off:off + 4 * int(count)].view(torch.float32)
+            allreduce(view)
+            return 0
+        except Exception as e:          # reported after the call
+            errors.append(e)
+            return 1
+
+    cb = N.ALLREDUCE_FN(_cb)
+    ranks_out = (ctypes.c_int64 * (d + 1))()
+    status = N.lib().tt_rbki_decompose_sharded(
+        ctypes.c_void_p(local_tensor.data_ptr()), N.i64_array(dims), d, N.i64_array(ranks), int(oversample), int(q),
+        ctypes.c_uint64(omega_seed), N.ptr_array([c.data_ptr() for c in cores]), ranks_out,
+        ctypes.c_void_p(base), nb.value, int(world), int(rank), cb, None, _stream_handle(stream), ctypes.byref(opts))
+    if errors:
+        raise errors[0]
+    N.check(status)
+    decompose_sharded.last_workspace = ws
+    return cores, list(ranks_out)
+
+
 def decompose(tensor, ranks, oversample, q, omega_seed=0, omegas=None, opts=None, workspace=None,
               cores=None, stream=None):
     """TT-rBKI of a dense row-major CUDA tensor.

@@ -34,6 +34,15 @@ class TTModePlan(ctypes.Structure):
                 ("fused_power", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class TTShardMode(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n_global", ctypes.c_int64), ("n_local", ctypes.c_int64),
+                ("route", ctypes.c_int32), ("allreduces", ctypes.c_int32), ("allreduce_floats", ctypes.c_int64)]
+
+
+# int32 (*)(float* buf, int64 count, void* stream, void* ctx)
+ALLREDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p)
+
+
 class TTProblem(ctypes.Structure):
     _fields_ = [("tensor", ctypes.c_void_p), ("dims", ctypes.POINTER(ctypes.c_int64)),
                 ("ranks", ctypes.POINTER(ctypes.c_int64)), ("cores_out", ctypes.POINTER(ctypes.c_void_p)),
@@ -72,6 +81,15 @@ _SIGNATURES = {
                                  _vpp, _i64p, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(TTOptions)],
                                 ctypes.c_int),
     "tt_rbki_device_status": ([_vp, _vp, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "tt_rbki_shard_plan": ([_i64p, ctypes.c_int, _i64p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(TTOptions),
+                            ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
+                            ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(TTShardMode), ctypes.c_int], ctypes.c_int),
+    "tt_rbki_sharded_workspace_size": ([_i64p, ctypes.c_int, _i64p, ctypes.c_int, ctypes.c_int,
+                                        ctypes.POINTER(TTOptions), ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "tt_rbki_decompose_sharded": ([_vp, _i64p, ctypes.c_int, _i64p, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                                   _vpp, _i64p, _vp, ctypes.c_size_t, ctypes.c_int32, ctypes.c_int32,
+                                   ALLREDUCE_FN, _vp, _vp, ctypes.POINTER(TTOptions)], ctypes.c_int),
     "tt_rbki_batched_workspace_size": ([ctypes.c_int, ctypes.POINTER(TTProblem), ctypes.POINTER(TTOptions),
                                         ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "tt_rbki_decompose_batched": ([ctypes.c_int, ctypes.POINTER(TTProblem), _vp, ctypes.c_size_t, _vp,

@@ -42,6 +42,9 @@ struct ModePlan {
   bool gram_power = false;   // short unfolding: G = C C^T formed once, each power W = G X
   bool fused_ga = false;     // Gram-apply fused in one pass over C
   bool literal = false;      // the paper's steps taken literally (first-r truncation)
+  int64_t n_global = 0;      // columns of the whole unfolding (n: this rank's slab of them)
+  int allreduces = 0;        // sums over the ranks this mode needs (sharded form)
+  int64_t allreduce_floats = 0;
 };
 
 struct Plan {
@@ -50,6 +53,12 @@ struct Plan {
   tt_options o{};
   int storage = TT_F32, remainder = TT_F32;
   std::vector<ModePlan> modes;
+  // sharded form: this rank's slab [slab_lo, slab_lo + slab_w) of the last
+  // mode (of size nd) and the callback that sums a device buffer over ranks
+  int world = 1, rank = 0;
+  int64_t slab_lo = 0, slab_w = 0, nd = 0;
+  tt_allreduce_fn allreduce = nullptr;
+  void* comm = nullptr;
   // workspace offsets in bytes
   size_t off_status = 0, off_R0 = 0, off_R1 = 0, off_S = 0, off_T = 0, off_part = 0, off_Y = 0,
          off_Q = 0, off_W = 0, off_U = 0, off_G = 0, off_small = 0, off_X = 0, off_Xg = 0, off_B = 0, off_Hd = 0,
@@ -97,12 +106,27 @@ tt_status clamp(const int64_t* dims, int d, const int64_t* ranks, std::vector<in
 }
 
 tt_status build_plan(const int64_t* dims, int d, const int64_t* ranks, int p, int q, const tt_options* opts,
-                     Plan& P) {
+                     Plan& P, int world = 1, int rank = 0) {
   tt_status s = resolve_options(opts, &P.o);
   if (s != TT_OK) return s;
   if (p < 0 || q < 0) return fail(TT_EINVAL, "oversample and q must be >= 0");
   s = clamp(dims, d, ranks, P.rr);
   if (s != TT_OK) return s;
+  if (world < 1 || rank < 0 || rank >= world) return fail(TT_EINVAL, "need 0 <= rank < world");
+  if (world > dims[d - 1]) return fail(TT_EINVAL, "the last mode must have at least one index per rank");
+  if (world > 1 && (P.o.paper_literal || P.o.accurate_rr))
+    return fail(TT_EUNSUPPORTED, "the sharded form takes neither paper_literal nor accurate_rr");
+  P.world = world;
+  P.rank = rank;
+  P.nd = dims[d - 1];
+  {
+    // contiguous slabs, the first ones one larger when I_d is not a multiple
+    // of the world size: slab g = [ceil(g I_d / W), ceil((g + 1) I_d / W))
+    const int64_t lo = ((int64_t)rank * P.nd + world - 1) / world;
+    const int64_t hi = ((int64_t)(rank + 1) * P.nd + world - 1) / world;
+    P.slab_lo = lo;
+    P.slab_w = hi - lo;
+  }
   P.d = d;
   P.p = p;
   P.q = q;
@@ -142,7 +166,7 @@ tt_status build_plan(const int64_t* dims, int d, const int64_t* ranks, int p, in
     M.kq = (int)cols;
     M.gram_route = P.o.exhaust_gram && cols == M.D && M.D == M.m && M.m <= 128;
     M.gram_cols = P.o.exhaust_gram && !M.gram_route && cols == M.D && M.D == M.n && M.n < M.m &&
-                  ttr::eig_top_ok((int)M.n) && !P.o.accurate_rr;
+                  ttr::eig_top_ok((int)M.n) && !P.o.accurate_rr && world == 1;
     if (P.o.accurate_rr && !M.gram_route && M.kq > ttr::RR_SVD_KMAX)
       return fail(TT_EUNSUPPORTED, "options.accurate_rr needs Krylov bases of at most 160 columns");
     if (P.o.paper_literal) {
@@ -174,6 +198,26 @@ tt_status build_plan(const int64_t* dims, int d, const int64_t* ranks, int p, in
     }
     if (!M.gram_route && !M.gram_cols && M.kq > 256)
       return fail(TT_EUNSUPPORTED, "Krylov basis larger than 256 columns");
+    // sharded form (the routes are decided on the whole unfolding above):
+    // this rank's columns, and the sums over ranks — the sketch and every
+    // streamed power (m x b blocks), or the Gram once (m x m) on the Gram
+    // routes; the column-Gram route needs every rank's columns and is off
+    M.n_global = M.n;
+    if (world > 1) {
+      if (M.gram_cols) return fail(TT_EUNSUPPORTED, "internal: column Gram in the sharded form");
+      M.n = M.n / P.nd * P.slab_w;
+      const int powers = (P.o.method == TT_METHOD_RSI) ? M.iters + 1 : (int)M.blocks.size();
+      if (M.gram_route) {
+        M.allreduces = 1;
+        M.allreduce_floats = M.m * M.m;
+      } else if (M.gram_power) {
+        M.allreduces = 2;
+        M.allreduce_floats = M.m * M.b + M.m * M.m;
+      } else {
+        M.allreduces = 1 + powers;
+        M.allreduce_floats = M.m * M.b * (1 + powers);
+      }
+    }
     // sizes
     maxR = std::max(maxR, (size_t)(M.r_out * M.n) * esize(P.remainder));
     if (M.gram_route) {
@@ -266,6 +310,12 @@ tt_status run_mode(const Plan& P, int k, const TIn* C, char* ws, int* status, co
   float* U = (float*)(ws + P.off_U);
   float* small = (float*)(ws + P.off_small);
   const int r = M.r_out;
+  // sharded form: the sum of a partial block over the ranks (a no-op alone)
+  auto sum_ranks = [&](float* buf, int64_t count) -> tt_status {
+    if (P.world <= 1) return TT_OK;
+    if (P.allreduce(buf, count, (void*)st, P.comm) != 0) return fail(TT_ECUDA, "allreduce callback failed");
+    return TT_OK;
+  };
   if (M.gram_route && P.o.accurate_rr) {
     // Alg. 3 steps 6-8 at exhaustion with B = C: the compensated Gram, FP64
     // Cholesky, one-sided Jacobi (rr_svd.cu)
@@ -279,6 +329,10 @@ tt_status run_mode(const Plan& P, int k, const TIn* C, char* ws, int* status, co
       TTR_CUDA(ttr::tc_gram(Cb, M.m, M.n, part, G, status, st));
     else
       TTR_CUDA(ttr::simt_gram<TIn>(C, M.m, M.n, part, G, st));
+    {
+      const tt_status rs = sum_ranks(G, M.m * M.m);
+      if (rs != TT_OK) return rs;
+    }
     if (ttr::eig_top_ok((int)M.m))
       TTR_CUDA(ttr::launch_rr_fast(nullptr, G, M.m, M.m, (int)M.m, r, 1, small, U, core, st));
     else
@@ -316,7 +370,8 @@ tt_status run_mode(const Plan& P, int k, const TIn* C, char* ws, int* status, co
     if (omega_explicit)
       TTR_CUDA(ttr::launch_omega_transpose_any(omega_explicit, M.n, M.b, S, om_dt, st));
     else
-      TTR_CUDA(ttr::launch_omega(seed, k, M.n, M.b, S, om_dt, 1, M.n, st));
+      TTR_CUDA(ttr::launch_omega(seed, k, M.n, M.b, S, om_dt, 1, M.n, st, P.world > 1 ? P.slab_w : 0, P.nd,
+                                 P.slab_lo));
     // sketch Y = C Omega, first basis block (the literal form sketches with
     // the first r columns of Omega: the first r rows of its transpose S)
     const int bw = M.literal ? r : M.b;
@@ -325,6 +380,10 @@ tt_status run_mode(const Plan& P, int k, const TIn* C, char* ws, int* status, co
                           st));
     else
       TTR_CUDA(ttr::simt_cs<TIn>(C, M.m, M.n, S, M.n, bw, part, Y, bw, st));
+    {
+      const tt_status rs = sum_ranks(Y, M.m * bw);
+      if (rs != TT_OK) return rs;
+    }
     const uint64_t rseed = 0x5EEDull * (uint64_t)(k + 1);
     int* flag = status + 1;
     unsigned* ticket = reinterpret_cast<unsigned*>(status + 2);
@@ -366,7 +425,11 @@ tt_status run_mode(const Plan& P, int k, const TIn* C, char* ws, int* status, co
       return TT_OK;
     };
     float* Gp = (float*)(ws + P.off_G);
-    if (M.gram_power) TTR_CUDA(ttr::gram_tiled(C, kBf16 ? 1 : 0, M.m, M.n, part, Gp, status, st));
+    if (M.gram_power) {
+      TTR_CUDA(ttr::gram_tiled(C, kBf16 ? 1 : 0, M.m, M.n, part, Gp, status, st));
+      const tt_status rs = sum_ranks(Gp, M.m * M.m);
+      if (rs != TT_OK) return rs;
+    }
     // one power: Wj = C C^T Xj (cj columns; row stride kq for both)
     auto power = [&](const float* Xj, float* Wj, int cj) -> tt_status {
       if (M.gram_power) {
@@ -387,6 +450,16 @@ tt_status run_mode(const Plan& P, int k, const TIn* C, char* ws, int* status, co
       } else {
         TTR_CUDA((ttr::simt_proj<TIn, float>(C, M.m, M.n, Xj, kq, cj, T, M.n, st, part)));
         TTR_CUDA(ttr::simt_cs<TIn>(C, M.m, M.n, T, M.n, cj, part, Wj, kq, st));
+      }
+      if (P.world > 1 && !M.gram_power) {
+        // the streamed power is a partial sum: add the ranks' blocks (packed
+        // into the sketch buffer, free once the first block is orthonormal)
+        TTR_CUDA(cudaMemcpy2DAsync(Y, sizeof(float) * cj, Wj, sizeof(float) * kq, sizeof(float) * cj, M.m,
+                                   cudaMemcpyDeviceToDevice, st));
+        const tt_status rs = sum_ranks(Y, M.m * cj);
+        if (rs != TT_OK) return rs;
+        TTR_CUDA(cudaMemcpy2DAsync(Wj, sizeof(float) * kq, Y, sizeof(float) * cj, sizeof(float) * cj, M.m,
+                                   cudaMemcpyDeviceToDevice, st));
       }
       return TT_OK;
     };
@@ -501,10 +574,11 @@ tt_status enqueue_problem(const Plan& P, const void* tensor, const float* const*
   }
   // Alg. 3 step 12: last core = last remainder
   const char* Rlast = ws + (((d - 2) % 2 == 0) ? P.off_R0 : P.off_R1);
-  const int64_t last = P.rr[d - 1] * P.dims[d - 1];
+  const int64_t wd = (P.world > 1) ? P.slab_w : P.dims[d - 1];   // this rank's slab of the last mode
+  const int64_t last = P.rr[d - 1] * wd;
   TTR_CUDA(ttr::launch_last_core(Rlast, P.remainder, last, cores_out[d - 1], status, st));
   for (int k = 0; k < d; ++k)
-    TTR_CUDA(ttr::launch_check_finite(cores_out[k], P.rr[k] * P.dims[k] * P.rr[k + 1], status, st));
+    TTR_CUDA(ttr::launch_check_finite(cores_out[k], P.rr[k] * (k == d - 1 ? wd : P.dims[k]) * P.rr[k + 1], status, st));
   return TT_OK;
 }
 
@@ -1063,6 +1137,68 @@ tt_status tt_sym_eig_top(const float* H, int64_t ldh, int k, int r, float* V, fl
   if (ldh < k) return fail(TT_EINVAL, "ldh < k");
   if (!workspace || ws_bytes < need) return fail(TT_ENOMEM, "workspace too small");
   TTR_CUDA(ttr::launch_eig_top(H, ldh, k, r, V, (float*)workspace, evals, (cudaStream_t)stream));
+  return TT_OK;
+}
+
+// Sharded form: this rank's slab of the last mode; the sums over ranks go
+// through the caller's callback (see include/tt_rbki.h).
+tt_status tt_rbki_shard_plan(const int64_t* dims, int d, const int64_t* ranks, int oversample, int q,
+                             const tt_options* opts, int32_t world, int32_t rank, int64_t* slab_lo, int64_t* slab_w,
+                             tt_shard_mode* modes, int max_modes) {
+  if (!slab_lo || !slab_w || !modes) return fail(TT_EINVAL, "slab_lo, slab_w and modes must not be NULL");
+  Plan P;
+  tt_status s = build_plan(dims, d, ranks, oversample, q, opts, P, world, rank);
+  if (s != TT_OK) return s;
+  if (max_modes < d - 1) return fail(TT_EINVAL, "max_modes must be >= d - 1");
+  *slab_lo = P.slab_lo;
+  *slab_w = P.slab_w;
+  for (int k = 0; k < d - 1; ++k) {
+    const ModePlan& M = P.modes[k];
+    tt_shard_mode& o = modes[k];
+    std::memset(&o, 0, sizeof(o));
+    o.m = M.m;
+    o.n_global = M.n_global;
+    o.n_local = M.n;
+    o.route = M.gram_route ? TT_ROUTE_GRAM_ROWS : M.gram_power ? TT_ROUTE_GRAM_POWER : TT_ROUTE_KRYLOV;
+    o.allreduces = M.allreduces;
+    o.allreduce_floats = M.allreduce_floats;
+  }
+  return TT_OK;
+}
+
+tt_status tt_rbki_sharded_workspace_size(const int64_t* dims, int d, const int64_t* ranks, int oversample, int q,
+                                         const tt_options* opts, int32_t world, int32_t rank, size_t* bytes) {
+  if (!bytes) return fail(TT_EINVAL, "bytes is NULL");
+  Plan P;
+  tt_status s = build_plan(dims, d, ranks, oversample, q, opts, P, world, rank);
+  if (s != TT_OK) return s;
+  *bytes = P.total;
+  return TT_OK;
+}
+
+tt_status tt_rbki_decompose_sharded(const void* local_tensor, const int64_t* dims, int d, const int64_t* ranks,
+                                    int oversample, int q, uint64_t omega_seed, float* const* cores_out,
+                                    int64_t* ranks_out, void* workspace, size_t ws_bytes, int32_t world, int32_t rank,
+                                    tt_allreduce_fn allreduce, void* ctx, void* stream, const tt_options* opts) {
+  Plan P;
+  tt_status s = build_plan(dims, d, ranks, oversample, q, opts, P, world, rank);
+  if (s != TT_OK) return s;
+  if (world > 1 && !allreduce) return fail(TT_EINVAL, "allreduce is NULL");
+  P.allreduce = allreduce;
+  P.comm = ctx;
+  s = check_problem(P, local_tensor, nullptr, cores_out);
+  if (s != TT_OK) return s;
+  if (!workspace) return fail(TT_EINVAL, "workspace is NULL");
+  if (((uintptr_t)workspace & 255) != 0) return fail(TT_EINVAL, "workspace must be 256-byte aligned");
+  if (ws_bytes < P.total) return fail(TT_ENOMEM, "workspace too small");
+  cudaStream_t st = (cudaStream_t)stream;
+  char* ws = (char*)workspace;
+  int* status = (int*)(ws + P.off_status);
+  TTR_CUDA(cudaMemsetAsync(status, 0, 256, st));
+  s = enqueue_problem(P, local_tensor, nullptr, omega_seed, cores_out, ws, status, st);
+  if (s != TT_OK) return s;
+  if (ranks_out)
+    for (int k = 0; k <= d; ++k) ranks_out[k] = P.rr[k];
   return TT_OK;
 }
 

@@ -163,7 +163,7 @@ cudaError_t launch_check_finite(const float* p, int64_t count, int* status, cuda
 
 // ---- inputs (misc.cu)
 cudaError_t launch_omega(uint64_t seed, int mode, int64_t n, int b, void* out, int dtype, int64_t si,
-                         int64_t sc, cudaStream_t st);
+                         int64_t sc, cudaStream_t st, int64_t slab_w = 0, int64_t slab_nd = 0, int64_t slab_lo = 0);
 cudaError_t launch_omega_transpose_any(const float* src, int64_t n, int b, void* dst, int dtype, cudaStream_t st);
 cudaError_t launch_permute(const void* src, int sdt, void* dst, int ddt, const int64_t* dims,
                            const int64_t* sstrides, const int* perm, int d, cudaStream_t st);

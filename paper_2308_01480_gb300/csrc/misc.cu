@@ -34,10 +34,13 @@ __device__ __forceinline__ float2 box_muller(uint32_t a, uint32_t b) {
   return make_float2(rad * c, rad * s);
 }
 
-// Omega_k entry (i, c) written at out[i * si + c * sc], i < n, c < b.
+// Omega_k entry (i, c) written at out[i * si + c * sc], i < n, c < b.  With
+// a slab (w > 0) the n local rows are the rows (i / w) nd + lo + i % w of
+// the full Omega_k: the columns of the unfolding whose last index lies in
+// [lo, lo + w) of a last mode of size nd, in their order.
 template <typename T>
 __global__ void k_omega(uint64_t seed, uint32_t mode, int64_t n, int b, T* __restrict__ out, int64_t si,
-                        int64_t sc) {
+                        int64_t sc, int64_t w, int64_t nd, int64_t lo) {
   const int groups = (b + 3) >> 2;
   const int64_t total = n * groups;
   const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
@@ -45,7 +48,9 @@ __global__ void k_omega(uint64_t seed, uint32_t mode, int64_t n, int b, T* __res
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = e % n;            // consecutive threads -> consecutive rows
     const int g = (int)(e / n);
-    const uint4 x = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)((uint64_t)i >> 32), (uint32_t)g, mode), k0, k1);
+    const int64_t gi = (w > 0) ? (i / w) * nd + lo + i % w : i;   // row of the full Omega_k
+    const uint4 x =
+        philox4x32_10(make_uint4((uint32_t)gi, (uint32_t)((uint64_t)gi >> 32), (uint32_t)g, mode), k0, k1);
     const float2 z01 = box_muller(x.x, x.y);
     const float2 z23 = box_muller(x.z, x.w);
     const float z[4] = {z01.x, z01.y, z23.x, z23.y};
@@ -58,15 +63,17 @@ __global__ void k_omega(uint64_t seed, uint32_t mode, int64_t n, int b, T* __res
 }
 
 cudaError_t launch_omega(uint64_t seed, int mode, int64_t n, int b, void* out, int dtype, int64_t si,
-                         int64_t sc, cudaStream_t st) {
+                         int64_t sc, cudaStream_t st, int64_t slab_w, int64_t slab_nd, int64_t slab_lo) {
   const int64_t total = n * ((b + 3) / 4);
   const int blocks = (int)imin(ceil_div(total, 256), 152 * 16);
   ProfScope prof("omega_philox", st, (double)n * b * (dtype == TT_BF16 ? 2 : 4), 0);
   note_launch("omega_philox");
   if (dtype == TT_BF16)
-    k_omega<__nv_bfloat16><<<blocks, 256, 0, st>>>(seed, (uint32_t)mode, n, b, (__nv_bfloat16*)out, si, sc);
+    k_omega<__nv_bfloat16><<<blocks, 256, 0, st>>>(seed, (uint32_t)mode, n, b, (__nv_bfloat16*)out, si, sc, slab_w,
+                                                   slab_nd, slab_lo);
   else
-    k_omega<float><<<blocks, 256, 0, st>>>(seed, (uint32_t)mode, n, b, (float*)out, si, sc);
+    k_omega<float><<<blocks, 256, 0, st>>>(seed, (uint32_t)mode, n, b, (float*)out, si, sc, slab_w, slab_nd,
+                                           slab_lo);
   return cudaGetLastError();
 }
 
