@@ -426,7 +426,12 @@ tt_status run_mode(const Plan& P, int k, const TIn* C, char* ws, int* status, co
     };
     float* Gp = (float*)(ws + P.off_G);
     if (M.gram_power) {
-      TTR_CUDA(ttr::gram_tiled(C, kBf16 ? 1 : 0, M.m, M.n, part, Gp, status, st));
+      // short BF16 unfoldings (m <= 128): the one-tile tcgen05 Gram pass;
+      // taller ones: the tiled Gram (tensor cores for BF16, SIMT for FP32)
+      if (use_tc && M.m <= 128)
+        TTR_CUDA(ttr::tc_gram(Cb, M.m, M.n, part, Gp, status, st));
+      else
+        TTR_CUDA(ttr::gram_tiled(C, kBf16 ? 1 : 0, M.m, M.n, part, Gp, status, st));
       const tt_status rs = sum_ranks(Gp, M.m * M.m);
       if (rs != TT_OK) return rs;
     }
