@@ -62,7 +62,7 @@ struct Plan {
   // workspace offsets in bytes
   size_t off_status = 0, off_R0 = 0, off_R1 = 0, off_S = 0, off_T = 0, off_part = 0, off_Y = 0,
          off_Q = 0, off_W = 0, off_U = 0, off_G = 0, off_small = 0, off_X = 0, off_Xg = 0, off_B = 0, off_Hd = 0,
-         off_dfp = 0, total = 0;
+         off_dfp = 0, off_part2 = 0, total = 0;
 };
 
 tt_status resolve_options(const tt_options* in, tt_options* out) {
@@ -138,7 +138,7 @@ tt_status build_plan(const int64_t* dims, int d, const int64_t* ranks, int p, in
   for (int k = 0; k < d; ++k) total *= dims[k];
   int64_t n = total;
   size_t maxR = 0, maxS = 0, maxT = 0, maxPart = 0, maxY = 0, maxQ = 0, maxU = 0, maxG = 0, maxSmall = 0,
-         maxX = 0, maxXg = 0, maxB = 0, maxHd = 0, maxDf = 0;
+         maxX = 0, maxXg = 0, maxB = 0, maxHd = 0, maxDf = 0, maxPart2 = 0;
   for (int k = 0; k < d - 1; ++k) {
     ModePlan& M = P.modes[k];
     n /= dims[k];
@@ -262,6 +262,10 @@ tt_status build_plan(const int64_t* dims, int d, const int64_t* ranks, int p, in
     if (M.gram_power) {
       maxG = std::max(maxG, (size_t)(M.m * M.m));
       maxPart = std::max(maxPart, ttr::gram_tiled_partials(M.m, M.n, cdt == TT_BF16 ? 1 : 0));
+      // the Gram's own partials when it runs beside the sketch
+      maxPart2 = std::max(maxPart2, (cdt == TT_BF16 && ttr::tc_shape_ok(M.m, M.n) && M.m <= 128)
+                                        ? (size_t)ttr::tc_gram_partials(M.m, M.n)
+                                        : ttr::gram_tiled_partials(M.m, M.n, cdt == TT_BF16 ? 1 : 0));
       // padded copy of the current block for the power
       maxXg = std::max(maxXg, (size_t)M.m * (size_t)((M.b + 3) & ~3));
     }
@@ -294,13 +298,38 @@ tt_status build_plan(const int64_t* dims, int d, const int64_t* ranks, int p, in
   P.off_B = take(maxB * 4);
   P.off_Hd = take(maxHd * 8);
   P.off_dfp = take(maxDf * 8);
+  P.off_part2 = take(maxPart2 * 4);
   P.total = off;
   return TT_OK;
 }
 
+// A second stream (and its fork/join events) per host thread and device,
+// created on first use and kept: work forked onto it is always joined back
+// into the caller's stream before the call returns, so a capture in progress
+// stays well formed.
+struct AuxStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+AuxStream* aux_stream() {
+  thread_local std::map<int, AuxStream> per_device;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  AuxStream& a = per_device[dev];
+  if (!a.s) {
+    if (cudaStreamCreateWithFlags(&a.s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&a.join, cudaEventDisableTiming) != cudaSuccess) {
+      a = AuxStream{};
+      return nullptr;
+    }
+  }
+  return &a;
+}
+
 template <typename TIn>
 tt_status run_mode(const Plan& P, int k, const TIn* C, char* ws, int* status, const float* omega_explicit,
-                   uint64_t seed, float* core, cudaStream_t st) {
+                   uint64_t seed, float* core, cudaStream_t st, bool fork_ok) {
   const ModePlan& M = P.modes[k];
   constexpr bool kBf16 = std::is_same<TIn, __nv_bfloat16>::value;
   const bool use_tc = kBf16 && ttr::tc_shape_ok(M.m, M.n);
@@ -372,6 +401,37 @@ tt_status run_mode(const Plan& P, int k, const TIn* C, char* ws, int* status, co
     else
       TTR_CUDA(ttr::launch_omega(seed, k, M.n, M.b, S, om_dt, 1, M.n, st, P.world > 1 ? P.slab_w : 0, P.nd,
                                  P.slab_lo));
+    // Gram-power route: G = C C^T does not depend on the sketch, so on the
+    // single-problem path it runs on a second stream beside the sketch and
+    // the first block's orthonormalisation (tensor-bound Gram next to the
+    // HBM-bound sketch), joined before the first power
+    float* Gp = (float*)(ws + P.off_G);
+    const bool fork = M.gram_power && fork_ok && P.world == 1;
+    AuxStream* ax = fork ? aux_stream() : nullptr;
+    if (fork && !ax) return fail(TT_ECUDA, "could not create the auxiliary stream");
+    if (M.gram_power) {
+      cudaStream_t gst = st;
+      float* gpart = part;
+      if (fork) {
+        TTR_CUDA(cudaEventRecord(ax->fork, st));
+        TTR_CUDA(cudaStreamWaitEvent(ax->s, ax->fork, 0));
+        gst = ax->s;
+        gpart = (float*)(ws + P.off_part2);
+      }
+      // short BF16 unfoldings (m <= 128): the one-tile tcgen05 Gram pass;
+      // taller ones: the tiled Gram (tensor cores for BF16, SIMT for FP32)
+      if (use_tc && M.m <= 128)
+        TTR_CUDA(ttr::tc_gram(Cb, M.m, M.n, gpart, Gp, status, gst));
+      else
+        TTR_CUDA(ttr::gram_tiled(C, kBf16 ? 1 : 0, M.m, M.n, gpart, Gp, status, gst));
+      if (fork) TTR_CUDA(cudaEventRecord(ax->join, ax->s));
+      const tt_status rs = sum_ranks(Gp, M.m * M.m);
+      if (rs != TT_OK) return rs;
+    }
+    auto join_gram = [&]() -> tt_status {
+      if (fork) TTR_CUDA(cudaStreamWaitEvent(st, ax->join, 0));
+      return TT_OK;
+    };
     // sketch Y = C Omega, first basis block (the literal form sketches with
     // the first r columns of Omega: the first r rows of its transpose S)
     const int bw = M.literal ? r : M.b;
@@ -424,17 +484,6 @@ tt_status run_mode(const Plan& P, int k, const TIn* C, char* ws, int* status, co
       }
       return TT_OK;
     };
-    float* Gp = (float*)(ws + P.off_G);
-    if (M.gram_power) {
-      // short BF16 unfoldings (m <= 128): the one-tile tcgen05 Gram pass;
-      // taller ones: the tiled Gram (tensor cores for BF16, SIMT for FP32)
-      if (use_tc && M.m <= 128)
-        TTR_CUDA(ttr::tc_gram(Cb, M.m, M.n, part, Gp, status, st));
-      else
-        TTR_CUDA(ttr::gram_tiled(C, kBf16 ? 1 : 0, M.m, M.n, part, Gp, status, st));
-      const tt_status rs = sum_ranks(Gp, M.m * M.m);
-      if (rs != TT_OK) return rs;
-    }
     // one power: Wj = C C^T Xj (cj columns; row stride kq for both)
     auto power = [&](const float* Xj, float* Wj, int cj) -> tt_status {
       if (M.gram_power) {
@@ -472,6 +521,7 @@ tt_status run_mode(const Plan& P, int k, const TIn* C, char* ws, int* status, co
       // Q = orth((C C^T)^s C W(:, 1:r)): orthonormalise after every power
       // (the same leading-column spans as the literal QRs); Q is the core
       tt_status os = orth(Y, r, r, 0, r, rseed);
+      if (os == TT_OK) os = join_gram();
       if (os != TT_OK) return os;
       for (int it = 0; it < M.iters; ++it) {
         os = power(Q, W, r);
@@ -483,6 +533,7 @@ tt_status run_mode(const Plan& P, int k, const TIn* C, char* ws, int* status, co
       TTR_CUDA(cudaMemcpyAsync(core, Q, sizeof(float) * (size_t)M.m * r, cudaMemcpyDeviceToDevice, st));
     } else {
     tt_status os = orth(Y, M.b, M.b, 0, M.blocks[0], rseed);
+    if (os == TT_OK) os = join_gram();
     if (os != TT_OK) return os;
     if (P.o.method == TT_METHOD_RSI) {
       // Alg. 4 steps 6-11: Q <- orth(C C^T Q), q times; then one more power
@@ -557,7 +608,7 @@ tt_status check_problem(const Plan& P, const void* tensor, const float* const* o
 // holds P.total bytes (its own status area unused); `status` points to the
 // problem's 256-byte status area, cleared by the caller.
 tt_status enqueue_problem(const Plan& P, const void* tensor, const float* const* omegas, uint64_t seed,
-                          float* const* cores_out, char* ws, int* status, cudaStream_t st) {
+                          float* const* cores_out, char* ws, int* status, cudaStream_t st, bool fork_ok = true) {
   tt_status s = TT_OK;
   const int d = P.d;
   for (int k = 0; k < d - 1; ++k) {
@@ -572,9 +623,9 @@ tt_status enqueue_problem(const Plan& P, const void* tensor, const float* const*
     }
     const float* om = omegas ? omegas[k] : nullptr;
     if (dt == TT_BF16)
-      s = run_mode<__nv_bfloat16>(P, k, (const __nv_bfloat16*)C, ws, status, om, seed, cores_out[k], st);
+      s = run_mode<__nv_bfloat16>(P, k, (const __nv_bfloat16*)C, ws, status, om, seed, cores_out[k], st, fork_ok);
     else
-      s = run_mode<float>(P, k, (const float*)C, ws, status, om, seed, cores_out[k], st);
+      s = run_mode<float>(P, k, (const float*)C, ws, status, om, seed, cores_out[k], st, fork_ok);
     if (s != TT_OK) return s;
   }
   // Alg. 3 step 12: last core = last remainder
@@ -740,8 +791,10 @@ tt_status enqueue_batch(const BatchLayout& L, const tt_problem* pr, char* ws, cu
       if (j >= L.order[w].size()) continue;
       const int i = L.order[w][j];
       int* status = (int*)(ws + (size_t)i * 256);
+      // a side stream per problem only when one worker runs them all (it
+      // would order the workers' Grams after one another otherwise)
       err = enqueue_problem(L.plans[i], pr[i].tensor, nullptr, pr[i].omega_seed, pr[i].cores_out,
-                            ws + L.worker_off[w], status, W->streams[w]);
+                            ws + L.worker_off[w], status, W->streams[w], L.workers == 1);
     }
   // always join, so that a capture in progress stays well formed
   for (int w = 0; w < L.workers; ++w) {
