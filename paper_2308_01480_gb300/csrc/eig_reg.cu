@@ -36,6 +36,7 @@ namespace ttr {
 namespace {
 
 constexpr int ER_KTMAX = 5;
+constexpr int ER_TRI_WARPS = 8;          // warps of the tridiagonalisation CTA (16 measured slower)
 
 // Compile-time loop: f(integral_constant<int, 0>) ... f(<N - 1>), so that
 // register-tile indices are constants however large the unrolled body.
@@ -226,42 +227,43 @@ __device__ __forceinline__ float lane_transpose_sum(float (&x)[NV]) {
 //      to its entries of the trailing block.
 // Tiles of finished rows (32-row blocks) and columns (8-column slots) are
 // skipped at compile time: the column loop is split into 32-column segments.
-template <int KR>
-__global__ void __launch_bounds__(256, 1) k_eig_tridiag8(const float* __restrict__ Hin, int64_t ldh, int k,
+template <int KR, int NW>
+__global__ void __launch_bounds__(NW * 32, 1) k_eig_tridiag8(const float* __restrict__ Hin, int64_t ldh, int k,
                                                         float* __restrict__ Vg, float* __restrict__ tau_g,
                                                         float* __restrict__ d_g, float* __restrict__ e_g) {
-  constexpr int KC = 4 * KR;
+  constexpr int SPS = 32 / NW;            // column slots per warp in a 32-column segment
+  constexpr int KC = SPS * KR;
   constexpr int KM = 32 * KR;
   constexpr int NV = (KC + 1 <= 8) ? 8 : (KC + 1 <= 16) ? 16 : 32;
   __shared__ __align__(16) float vs[KM];
   __shared__ __align__(16) float ps[KM];
-  __shared__ float wsum[8];
+  __shared__ float wsum[NW];
   __shared__ float scal[2];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
 
-  float A[KR][KC];   // A[a][c] = H[lane + 32 a][w + 8 c]
+  float A[KR][KC];   // A[a][c] = H[lane + 32 a][w + NW c]
   sfor<KR>([&](auto a) {
     sfor<KC>([&](auto c) {
-      const int i = lane + 32 * a, j = w + 8 * c;
+      const int i = lane + 32 * a, j = w + NW * c;
       A[a][c] = (i < k && j < k) ? 0.5f * (Hin[(int64_t)i * ldh + j] + Hin[(int64_t)j * ldh + i]) : 0.f;
     });
   });
   const int z0 = (k >= 2) ? (k - 2) * k : 0;
-  for (int x = z0 + tid; x < k * k; x += 256) Vg[x] = 0.f;
+  for (int x = z0 + tid; x < k * k; x += NW * 32) Vg[x] = 0.f;
   sfor<KR>([&](auto seg) {
     constexpr int S = decltype(seg)::value;
     const int jend = min(32 * S + 32, k - 2);
     for (int j = 32 * S; j < jend; ++j) {
-      // R: the reflector of column j (slot cj in warp j & 7)
-      if (w == (j & 7)) {
-        const int t = (j >> 3) - 4 * S;   // 0..3
+      // R: the reflector of column j (slot j / NW in warp j % NW)
+      if (w == (j % NW)) {
+        const int t = (j / NW) - SPS * S;   // 0 .. SPS - 1
         float colv[KR];
         sfor<KR>([&](auto a) {
           float x = 0.f;
           if constexpr (a >= S) {
-            sfor<4>([&](auto u) {
-              if constexpr (4 * S + u < KC)
-                if (t == u) x = A[a][4 * S + u];
+            sfor<SPS>([&](auto u) {
+              if constexpr (SPS * S + u < KC)
+                if (t == u) x = A[a][SPS * S + u];
             });
           }
           colv[a] = x;
@@ -305,11 +307,11 @@ __global__ void __launch_bounds__(256, 1) k_eig_tridiag8(const float* __restrict
       // M: (H v)_c for this thread's live columns, its share of v^T H v
       float vr[KR], vc[KC];
       sfor<KR>([&](auto a) { vr[a] = (a >= S) ? vs[lane + 32 * a] : 0.f; });
-      sfor<KC>([&](auto c) { vc[c] = (c >= 4 * S) ? vs[w + 8 * c] : 0.f; });
+      sfor<KC>([&](auto c) { vc[c] = (c >= SPS * S) ? vs[w + NW * c] : 0.f; });
       float xv[NV];
       sfor<NV>([&](auto c) { xv[c] = 0.f; });
       sfor<KC>([&](auto c) {
-        if constexpr (c >= 4 * S) {
+        if constexpr (c >= SPS * S) {
           float acc = 0.f;
           sfor<KR>([&](auto a) {
             if constexpr (a >= S) acc = fmaf(A[a][c], vr[a], acc);
@@ -324,7 +326,7 @@ __global__ void __launch_bounds__(256, 1) k_eig_tridiag8(const float* __restrict
         const int vi = lane >> shift;
         if ((lane & ((1 << shift) - 1)) == 0) {
           if (vi < KC) {
-            const int col = w + 8 * vi;
+            const int col = w + NW * vi;
             if (col < KM) ps[col] = (col > j && col < k) ? tau * tot : 0.f;
           } else if (vi == KC) {
             wsum[w] = tot;
@@ -335,15 +337,15 @@ __global__ void __launch_bounds__(256, 1) k_eig_tridiag8(const float* __restrict
       // U: rank-2 update of the live tiles
       float vhv = 0.f;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) vhv += wsum[q];
+      for (int q = 0; q < NW; ++q) vhv += wsum[q];
       const float K = 0.5f * tau * tau * vhv;
       float wr[KR], wc[KC];
       sfor<KR>([&](auto a) { wr[a] = (a >= S) ? fmaf(-K, vr[a], ps[lane + 32 * a]) : 0.f; });
-      sfor<KC>([&](auto c) { wc[c] = (c >= 4 * S) ? fmaf(-K, vc[c], ps[w + 8 * c]) : 0.f; });
+      sfor<KC>([&](auto c) { wc[c] = (c >= SPS * S) ? fmaf(-K, vc[c], ps[w + NW * c]) : 0.f; });
       sfor<KR>([&](auto a) {
         if constexpr (a >= S) {
           sfor<KC>([&](auto c) {
-            if constexpr (c >= 4 * S) A[a][c] -= fmaf(vr[a], wc[c], wr[a] * vc[c]);
+            if constexpr (c >= SPS * S) A[a][c] -= fmaf(vr[a], wc[c], wr[a] * vc[c]);
           });
         }
       });
@@ -352,7 +354,7 @@ __global__ void __launch_bounds__(256, 1) k_eig_tridiag8(const float* __restrict
   // trailing 2 x 2 (or 1 x 1) block, written by the owners of its entries
   sfor<KR>([&](auto a) {
     sfor<KC>([&](auto c) {
-      const int i = lane + 32 * a, jj = w + 8 * c;
+      const int i = lane + 32 * a, jj = w + NW * c;
       if (k >= 2 && i == k - 2 && jj == k - 2) d_g[k - 2] = A[a][c];
       if (k >= 2 && i == k - 1 && jj == k - 2) e_g[k - 2] = A[a][c];
       if (i == k - 1 && jj == k - 1) d_g[k - 1] = A[a][c];
@@ -777,7 +779,7 @@ static cudaError_t launch_kt(const float* H, int64_t ldh, int k, int r, float* V
   float* tau = Vg + (size_t)k * k;
   float* d = tau + k;
   float* e = d + k;
-  k_eig_tridiag8<KT><<<1, 256, 0, st>>>(H, ldh, k, Vg, tau, d, e);
+  k_eig_tridiag8<KT, ER_TRI_WARPS><<<1, ER_TRI_WARPS * 32, 0, st>>>(H, ldh, k, Vg, tau, d, e);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   const size_t smem = er_smem_floats(32 * KT, k, r) * 4;
