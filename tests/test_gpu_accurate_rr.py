@@ -90,12 +90,16 @@ def test_accurate_bf16_error_criterion(tt, case):
 
 def test_accurate_rr_below_fp32_floor(tt):
     """30^4 power function (h = 5), r = 12, p = 2, q = 2: the FP64 oracle's
-    error is 4.6e-5, the singular values at the cut ~1e-5 of the largest."""
+    error is 4.6e-5, the singular values at the cut ~1e-5 of the largest.
+    The first mode's Gram C C^T (30 x 30) is singular to FP64 accuracy
+    (condition ~1e23), so this case also checks that the Cholesky of the
+    Gram pivots and stops at its numerical rank: unpivoted, rounding-size
+    pivots scatter the error between 1.0 and 1.25 times the oracle's."""
     A = W.power_tensor_h((30, 30, 30, 30), 5.0)
     ranks = (12, 12, 12)
     eps_ref = oracle.tt_error(A, oracle.tt_rbki(A, ranks, 2, 2, seed=1))
     got = _run(tt, A, ranks, 2, 2, seed=1, accurate_rr=True)
-    assert oracle.tt_error(A, got) <= 1.1 * eps_ref
+    assert oracle.tt_error(A, got) <= 1.02 * eps_ref
 
 
 def test_accurate_rank_deficient_stays_orthonormal(tt):
