@@ -364,6 +364,43 @@ TT_API tt_status tt_pass(int op, const void* C, int c_dtype, int64_t m, int64_t 
                   void* stream);
 
 /*
+ * Tuning table of the BF16 tensor-core passes' launch shapes (the passes of
+ * Alg. 3 steps 3, 4 and 10 and the exhaustion / Gram-power Gram).  Host-only
+ * calls; process-wide state guarded by a lock.  An entry changes only how a
+ * pass is launched, never what it computes (results differ at most by the
+ * order of FP32 partial sums), and never the workspace sizes.
+ *
+ * Key:   op     TT_PASS_* of the pass;
+ *        rows   row bucket of the unfolding: m rounded up to a multiple of
+ *               16 for m <= 128, else 256, 512, 1024 or 4096 (m > 1024);
+ *               the Gram takes rows <= 128 only;
+ *        npad   the MMA width: b rounded up to a multiple of 16 (the Gram:
+ *               m rounded; the projection at b <= 32 splits X into BF16
+ *               high and low parts and has npad = 64);
+ *        nclass 0 for n < 16,384 columns, 1 for n < 262,144, else 2.
+ * Entry: stages     ring depth cap, 2..8;
+ *        per_sm     CTAs per SM wanted, 1 or 2 (2 is taken only where three
+ *                   stages fit half of the shared memory);
+ *        kb         the Gram: 64-column boxes per stage, 1, 2, 4 or 8; else 0;
+ *        chunk_rows the projection of unfoldings taller than 128 rows: rows
+ *                   per streamed chunk, 64 or 128, or 0 for the built-in
+ *                   rule; else 0.
+ * An entry whose ring would keep fewer than two stages is ignored where it
+ * applies (the built-in rules then hold).  tt_tune_set / tt_tune_get return
+ * TT_EINVAL on an invalid key or entry (get: also on a missing key).
+ * tt_tune_load replaces the whole table from a text file, one entry per
+ * line: "op rows npad nclass stages per_sm kb chunk_rows", further text on
+ * the line ignored, '#' lines and blank lines skipped; on a missing file or
+ * any bad line it returns TT_EINVAL and leaves the table unchanged.
+ */
+TT_API tt_status tt_tune_set(int op, int rows, int npad, int nclass, int stages, int per_sm, int kb,
+                             int chunk_rows);
+TT_API tt_status tt_tune_get(int op, int rows, int npad, int nclass, int* entry4);
+TT_API tt_status tt_tune_clear(void);
+TT_API int tt_tune_entries(void);
+TT_API tt_status tt_tune_load(const char* path);
+
+/*
  * One Krylov power through a formed Gram matrix (Alg. 3 step 4 on the
  * Gram-power route): W = G X.
  *   G      device, m x m float32 row-major, symmetric (G = C C^T).

@@ -14,7 +14,7 @@ from ._native import (TT_BF16, TT_F32, TT_METHOD_RBKI, TT_METHOD_RSI, TT_PASS_GR
 __all__ = ["decompose", "tt_svd", "workspace_size", "core_sizes", "omega_generate", "permute_convert",
            "tt_pass", "gram_power", "device_status", "options", "plan_modes", "profile_begin", "profile_end", "TTError", "TT_F32",
            "TT_BF16", "Problem", "batched_workspace_size", "decompose_batched", "batched_device_status",
-           "BatchGraph"]
+           "BatchGraph", "tune_key", "tune_set", "tune_get", "tune_clear", "tune_entries", "tune_load"]
 
 
 def _torch():
@@ -322,6 +322,50 @@ def tt_pass(op, C, b=None, x=None, y_dtype=None, stream=None, workspace=None, ou
                             ctypes.c_void_p(out.data_ptr()), _dtype_code(out),
                             ctypes.c_void_p(workspace.data_ptr()), workspace.numel(), _stream_handle(stream)))
     return out
+
+
+def tune_key(op, m, n, b=0):
+    """The tuning-table key (op, rows, npad, nclass) of a BF16 tensor-core
+    pass over an m x n unfolding with b columns (see tt_tune_set in the
+    header): the same bucketing the library applies."""
+    m, n, b = int(m), int(n), int(b)
+    if m <= 128:
+        rows = (m + 15) // 16 * 16
+    else:
+        rows = 256 if m <= 256 else 512 if m <= 512 else 1024 if m <= 1024 else 4096
+    if op == N.TT_PASS_GRAM:
+        npad = (m + 15) // 16 * 16
+    elif op == N.TT_PASS_PROJECT and b <= 32:
+        npad = 64
+    else:
+        npad = (b + 15) // 16 * 16
+    return (int(op), rows, npad, 0 if n < 16384 else 1 if n < 262144 else 2)
+
+
+def tune_set(key, stages, per_sm, kb=0, chunk_rows=0):
+    """Sets the launch-shape entry of `key` (from tune_key)."""
+    N.check(N.lib().tt_tune_set(*[int(v) for v in key], int(stages), int(per_sm), int(kb), int(chunk_rows)))
+
+
+def tune_get(key):
+    """The entry (stages, per_sm, kb, chunk_rows) of `key`, or None."""
+    out = (ctypes.c_int * 4)()
+    if N.lib().tt_tune_get(*[int(v) for v in key], out) != N.TT_OK:
+        return None
+    return tuple(out)
+
+
+def tune_clear():
+    N.check(N.lib().tt_tune_clear())
+
+
+def tune_entries():
+    return int(N.lib().tt_tune_entries())
+
+
+def tune_load(path):
+    """Replaces the table from a text file (format in the header)."""
+    N.check(N.lib().tt_tune_load(str(path).encode()))
 
 
 def gram_power(G, X, stream=None, out=None):

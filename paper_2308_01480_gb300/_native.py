@@ -125,7 +125,16 @@ _SIGNATURES = {
                             ctypes.c_int),
     "tt_pass": ([ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, _vp, _vp,
                  ctypes.c_int, _vp, ctypes.c_size_t, _vp], ctypes.c_int),
+    "tt_tune_set": ([ctypes.c_int] * 8, ctypes.c_int),
+    "tt_tune_get": ([ctypes.c_int] * 4 + [ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "tt_tune_clear": ([], ctypes.c_int),
+    "tt_tune_entries": ([], ctypes.c_int),
+    "tt_tune_load": ([ctypes.c_char_p], ctypes.c_int),
 }
+
+# The launch-shape table the offline sweep (autotune.py) wrote for this
+# part; loaded with the library.
+TUNE_TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tune_table.txt")
 
 
 def exported_names():
@@ -146,6 +155,8 @@ def lib():
             f = getattr(L, name)
             f.argtypes = args
             f.restype = res
+        if os.path.exists(TUNE_TABLE) and L.tt_tune_load(TUNE_TABLE.encode()) != TT_OK:
+            raise RuntimeError(f"invalid tuning table {TUNE_TABLE}")
         _lib = L
     return _lib
 

@@ -54,6 +54,17 @@ cudaError_t launch_reduce_partials(const float* P, int S, int64_t rows, int cols
 cudaError_t launch_reduce_partials_grouped(const float* P, int per, int groups, int64_t rows, int cols,
                                            int64_t group_rows, float* out, int64_t ldo, cudaStream_t st);
 
+// ---- tuning table of the streaming passes' launch shapes (tune.cu)
+struct TuneEntry {
+  int stages;      // ring depth cap (2 .. 8)
+  int per_sm;      // CTAs per SM wanted (1 or 2; 2 only where three stages fit half the shared memory)
+  int kb;          // Gram: 64-column boxes per stage (1, 2, 4, 8); 0 elsewhere
+  int chunk_rows;  // projection of unfoldings taller than 128 rows: rows per chunk (64, 128); 0 = rule
+};
+int tune_row_bucket(int64_t m);
+int tune_n_class(int64_t n);
+bool tune_lookup(int op, int64_t m, int npad, int64_t n, TuneEntry* out);
+
 // ---- tensor-core streaming passes on BF16 unfoldings (stream_tc.cu)
 bool tc_shape_ok(int64_t m, int64_t n);
 int64_t tc_gram_partials(int64_t m, int64_t n);

@@ -687,6 +687,19 @@ int choose_residency(TcParams& p, int maxst, bool allow_two = true) {
   return 1;
 }
 
+// A tuning-table entry's ring depth and residency on a copy of p (two CTAs
+// per SM only where the entry asks for them, `allow_two` permits and three
+// stages fit half the shared memory); taken only if the ring keeps at least
+// two stages.  Returns whether p changed.
+bool apply_tuned(TcParams& p, int& per_sm, const TcParams& q0, const TuneEntry& e, bool allow_two) {
+  TcParams q = q0;
+  const int per = choose_residency(q, e.stages, allow_two && e.per_sm == 2);
+  if (q.stages < 2) return false;
+  p = q;
+  per_sm = per;
+  return true;
+}
+
 template <int OP>
 cudaError_t launch_tc(const CUtensorMap& mc, const CUtensorMap& mb, const TcParams& p, int ctas, cudaStream_t st) {
   const size_t smem = tc_smem_bytes(p);
@@ -754,11 +767,21 @@ TcShape gram_shape(int64_t m, int64_t n) {
   p.tiles = ceil_div(n, 64 * p.kb);
   p.row_groups = 1;
   t.per_sm = choose_residency(p, 8);
+  TuneEntry e;
+  if (tune_lookup(TT_PASS_GRAM, m, p.npad, n, &e)) {
+    TcParams q = p;
+    q.kb = e.kb;
+    q.stage_bytes = q.kb * q.c_box_bytes;
+    q.tiles = ceil_div(n, 64 * q.kb);
+    apply_tuned(p, t.per_sm, q, e, true);
+  }
   t.ctas = (int)imin(p.tiles, (int64_t)num_sms() * t.per_sm);
   return t;
 }
 
-int64_t tc_gram_partials(int64_t m, int64_t n) { return (int64_t)gram_shape(m, n).ctas * m * m; }
+// Partial sums for any launch shape (at most two CTAs per SM, tiles of at
+// least 64 columns), so that workspace sizes do not depend on the tuning table.
+int64_t tc_gram_partials(int64_t m, int64_t n) { return imin(ceil_div(n, 64), 2 * (int64_t)num_sms()) * m * m; }
 
 cudaError_t tc_gram(const __nv_bfloat16* C, int64_t m, int64_t n, float* partials, float* out, int* status,
                     cudaStream_t st) {
@@ -791,12 +814,18 @@ TcShape cs_shape(int64_t m, int64_t n, int b) {
   p.slack_bytes = 16384;
   p.tiles = ceil_div(n, 64);
   t.per_sm = choose_residency(p, 8);
+  TuneEntry e;
+  if (tune_lookup(TT_PASS_SKETCH, m, p.npad, n, &e)) apply_tuned(p, t.per_sm, p, e, true);
   const int64_t per = imax(1, imin(p.tiles, (int64_t)num_sms() * t.per_sm / p.row_groups));
   t.ctas = (int)(per * p.row_groups);
   return t;
 }
 
-int64_t tc_cs_partials(int64_t m, int64_t n, int b) { return (int64_t)cs_shape(m, n, b).ctas * m * b; }
+int64_t tc_cs_partials(int64_t m, int64_t n, int b) {
+  const int64_t groups = ceil_div(m, 512);
+  const int64_t per = imax(1, imin(ceil_div(n, 64), 2 * (int64_t)num_sms() / groups));
+  return per * groups * m * b;
+}
 
 cudaError_t tc_cs(const __nv_bfloat16* C, int64_t m, int64_t n, const __nv_bfloat16* S, int64_t lds, int b,
                   float* partials, float* out, int64_t ldo, int* status, cudaStream_t st) {
@@ -838,18 +867,27 @@ TcShape proj_shape(int64_t m, int64_t n, int b, int split, int o_bytes) {
   p.lo_off = split ? 32 : 0;
   p.npad = split ? 64 : pad16(b);
   p.kb = 2; p.mb = 1; p.row_groups = 1;
+  p.x_box_bytes = p.npad * 128;
+  p.tiles = ceil_div(n, 128);
+  auto set_chunks = [&](TcParams& q, int rows) {
+    q.chunk_rows = box_rows_for(m, rows);
+    q.nchunks = (int)ceil_div(m, q.chunk_rows);
+    q.x_resident = q.nchunks == 1 ? 1 : 0;
+    q.mpad = (int)ceil_div(q.chunk_rows, 64) * 64;
+    q.c_box_rows = q.chunk_rows; q.c_box_bytes = q.chunk_rows * 128;
+    q.x_res_bytes = q.x_resident ? (q.mpad / 64) * q.x_box_bytes : 0;
+    q.stage_bytes = (2 * q.c_box_bytes + (q.x_resident ? 0 : 2 * q.x_box_bytes) + 1023) / 1024 * 1024;
+  };
   // unfoldings taller than one chunk stream 64-row chunks: the smaller ring
   // stages let two CTAs share an SM
-  p.chunk_rows = box_rows_for(m, m > 128 ? 64 : 128);
-  p.nchunks = (int)ceil_div(m, p.chunk_rows);
-  p.x_resident = p.nchunks == 1 ? 1 : 0;
-  p.mpad = (int)ceil_div(p.chunk_rows, 64) * 64;
-  p.c_box_rows = p.chunk_rows; p.c_box_bytes = p.chunk_rows * 128;
-  p.x_box_bytes = p.npad * 128;
-  p.x_res_bytes = p.x_resident ? (p.mpad / 64) * p.x_box_bytes : 0;
-  p.stage_bytes = (2 * p.c_box_bytes + (p.x_resident ? 0 : 2 * p.x_box_bytes) + 1023) / 1024 * 1024;
-  p.tiles = ceil_div(n, 128);
+  set_chunks(p, m > 128 ? 64 : 128);
   t.per_sm = choose_residency(p, 8);
+  TuneEntry e;
+  if (tune_lookup(TT_PASS_PROJECT, m, p.npad, n, &e)) {
+    TcParams q = p;
+    if (m > 128 && e.chunk_rows) set_chunks(q, e.chunk_rows);
+    apply_tuned(p, t.per_sm, q, e, true);
+  }
   t.ctas = (int)imin(p.tiles, (int64_t)num_sms() * t.per_sm);
   return t;
 }
@@ -909,6 +947,8 @@ TcShape ga_shape(int64_t m, int64_t n, int b) {
   p.stage_bytes = 2 * p.c_box_bytes;
   // 512 TMEM columns (128 + mb npad > 256) leave room for one CTA per SM
   t.per_sm = choose_residency(p, 8, 128 + p.mb * p.npad <= 256);
+  TuneEntry e;
+  if (tune_lookup(TT_PASS_GRAMAPPLY, m, p.npad, n, &e)) apply_tuned(p, t.per_sm, p, e, 128 + p.mb * p.npad <= 256);
   t.ctas = (int)imin(p.tiles, (int64_t)num_sms() * t.per_sm);
   return t;
 }
@@ -925,7 +965,9 @@ size_t tc_ga_scratch_bytes(int64_t m, int b) {
   return (size_t)pad16(b) * ldt * 2 + 256;
 }
 
-int64_t tc_ga_partials(int64_t m, int64_t n, int b) { return (int64_t)ga_shape(m, n, b).ctas * m * b; }
+int64_t tc_ga_partials(int64_t m, int64_t n, int b) {
+  return imin(ceil_div(n, 128), 2 * (int64_t)num_sms()) * m * b;
+}
 
 cudaError_t tc_ga(const __nv_bfloat16* C, int64_t m, int64_t n, const float* X, int64_t ldx, int b, float* partials,
                   float* out, int64_t ldo, void* scratch, int* status, cudaStream_t st) {
