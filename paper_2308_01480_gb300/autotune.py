@@ -144,7 +144,7 @@ def sweep(reps=10, gain=0.03, log=sys.stdout):
         gb = (m * n * 2) / (best_us * 1e3)
         print(f"{NAME[op]:10s} {m:5d} x {n:8d} b={b:3d} key={key}: built-in {base:8.1f} us, best {best_us:8.1f} us "
               f"{best}", file=log, flush=True)
-        what = f"{NAME[op]} {m} x {n}, b = {b}: built-in {base:.1f} us, tuned {best_us:.1f} us ({gb:.2f} TB/s of C)"
+        what = f"{NAME[op]} {m} x {n}, b = {b}: built-in {base:.1f} us, tuned {best_us:.1f} us ({gb:.0f} GB/s of C)"
         if best is not None and best_us < (1.0 - gain) * base:
             lines.append((key, best, what))
         else:
