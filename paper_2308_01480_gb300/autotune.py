@@ -3,9 +3,11 @@
 For each tuning key (pass, row bucket, MMA width, n class; see tt_tune_set
 in include/tt_rbki.h) one representative unfolding is timed under every
 candidate entry: ring depth, CTAs per SM, and the Gram's stage width or the
-tall projection's chunk height.  Times are per-launch CUDA events of the
-library's own profiler (the pass kernel alone), the mean of `--reps`
-launches after two warm-up launches, on seeded Gaussian BF16 data.  An
+tall projection's chunk height.  A time is that of the whole pass (every
+kernel of the call: operand preparation, the pass, the sum of its per-CTA
+partials, whose count follows the grid): `--reps` calls captured in one
+CUDA graph, replayed twice untimed and then timed by CUDA events around
+three replays, on seeded Gaussian BF16 data.  An
 entry is written only where the fastest candidate beats the built-in rules
 by more than `--gain` (3%); every candidate's output is first checked
 against the built-in shape's output (same pass, so the difference is the
@@ -26,8 +28,6 @@ import torch
 import paper_2308_01480_gb300 as tt
 from paper_2308_01480_gb300 import _native as N
 
-FAMILY = {N.TT_PASS_SKETCH: "cs_tc", N.TT_PASS_GRAMAPPLY: "gram_apply_tc", N.TT_PASS_PROJECT: "proj_tc",
-          N.TT_PASS_GRAM: "gram_tc"}
 NAME = {N.TT_PASS_SKETCH: "sketch", N.TT_PASS_GRAMAPPLY: "gram_apply", N.TT_PASS_PROJECT: "project",
         N.TT_PASS_GRAM: "gram"}
 
@@ -79,17 +79,27 @@ def _inputs(op, m, n, b, g):
 
 
 def _time(op, C, X, out, ws, reps):
+    """Microseconds per call of the whole pass, from a graph of `reps` calls."""
     kw = dict(y_dtype=torch.bfloat16) if op == N.TT_PASS_PROJECT else {}
-    for _ in range(2):
-        tt.tt_pass(op, C, x=X, out=out, workspace=ws, **kw)
-    torch.cuda.synchronize()
-    tt.profile_begin(event_timing=True)
-    for _ in range(reps):
-        tt.tt_pass(op, C, x=X, out=out, workspace=ws, **kw)
-    torch.cuda.synchronize()
-    st = tt.profile_end()
-    s = st[FAMILY[op]]
-    return 1000.0 * s["ms"] / s["launches"]
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        tt.tt_pass(op, C, x=X, out=out, workspace=ws, stream=s, **kw)     # shapes and maps built once
+        s.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            for _ in range(reps):
+                tt.tt_pass(op, C, x=X, out=out, workspace=ws, stream=s, **kw)
+        for _ in range(2):
+            g.replay()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(3):
+            g.replay()
+        e1.record(s)
+        s.synchronize()
+    del g
+    return 1000.0 * e0.elapsed_time(e1) / (3 * reps)
 
 
 def _bound(op, C, X):

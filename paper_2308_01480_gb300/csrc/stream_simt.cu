@@ -273,44 +273,68 @@ __global__ void __launch_bounds__(256) k_gram(const TIn* __restrict__ C, int64_t
 
 // ---------------------------------------------------------------- reduce
 // out[r * ldo + c] = sum_{s < S} P[s][r][c] (fixed order), r < rows, c < cols.
-// Sum of n values at p[0], p[stride], ..., in eight interleaved partial
-// sums (eight loads in flight), combined in a fixed order.
-__device__ __forceinline__ float strided_sum(const float* __restrict__ p, int n, int64_t stride) {
-  float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  int k = 0;
-  for (; k + 8 <= n; k += 8) {
-#pragma unroll
-    for (int u = 0; u < 8; ++u) a[u] += p[(int64_t)(k + u) * stride];
+// A block takes 32 consecutive elements (lane = element, each load of a warp
+// one 128-byte row of a partial); warp w sums the partials w, w + 8, ... in
+// four interleaved chains, and the eight warp sums are added in a fixed
+// tree: every element sees the same order whatever the grid, so reruns are
+// bit-identical, and a short element range still spreads over eight warps.
+constexpr int RED_WARPS = 8;
+
+__device__ __forceinline__ float strided_sum_warp(const float* __restrict__ p, int n, int64_t stride, int w) {
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+  int k = w;
+  for (; k + 3 * RED_WARPS < n; k += 4 * RED_WARPS) {
+    a0 += p[(int64_t)k * stride];
+    a1 += p[(int64_t)(k + RED_WARPS) * stride];
+    a2 += p[(int64_t)(k + 2 * RED_WARPS) * stride];
+    a3 += p[(int64_t)(k + 3 * RED_WARPS) * stride];
   }
-  for (; k < n; ++k) a[0] += p[(int64_t)k * stride];
-  return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+  for (; k < n; k += RED_WARPS) a0 += p[(int64_t)k * stride];
+  return (a0 + a1) + (a2 + a3);
 }
 
-__global__ void k_reduce_partials(const float* __restrict__ P, int S, int64_t rows, int cols,
-                                  float* __restrict__ out, int64_t ldo) {
-  const int64_t E = rows * cols;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const float s = strided_sum(P + e, S, E);
-    int64_t r = e / cols;
-    int c = (int)(e % cols);
-    out[r * ldo + c] = s;
+// base(e) + k * stride is partial k of element e (k < n); out[e] = the sum.
+template <typename Base>
+__device__ __forceinline__ void reduce_elements(Base base, int n, int64_t stride, int64_t E, int cols,
+                                                float* __restrict__ out, int64_t ldo) {
+  __shared__ float red[RED_WARPS][33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int64_t e0 = (int64_t)blockIdx.x * 32; e0 < E; e0 += (int64_t)gridDim.x * 32) {
+    const int64_t e = e0 + lane;
+    red[w][lane] = (e < E) ? strided_sum_warp(base(e), n, stride, w) : 0.f;
+    __syncthreads();
+    if (w == 0 && e < E) {
+      const float t = ((red[0][lane] + red[1][lane]) + (red[2][lane] + red[3][lane])) +
+                      ((red[4][lane] + red[5][lane]) + (red[6][lane] + red[7][lane]));
+      out[(e / cols) * ldo + e % cols] = t;
+    }
+    __syncthreads();
   }
+}
+
+struct PartialsFlat {
+  const float* P;
+  __device__ const float* operator()(int64_t e) const { return P + e; }
+};
+struct PartialsGrouped {   // element e's row group g = e / cols / group_rows starts at slot g
+  const float* P;
+  int64_t E, cols, group_rows;
+  __device__ const float* operator()(int64_t e) const { return P + (e / cols / group_rows) * E + e; }
+};
+
+__global__ void __launch_bounds__(32 * RED_WARPS) k_reduce_partials(const float* __restrict__ P, int S, int64_t rows,
+                                                                    int cols, float* __restrict__ out, int64_t ldo) {
+  const int64_t E = rows * cols;
+  reduce_elements(PartialsFlat{P}, S, E, E, cols, out, ldo);
 }
 
 // out[r][c] = sum over the CTAs of r's row group (slot j * groups + g) of
 // their partials; the CTAs of a group write only that group's rows.
-__global__ void k_reduce_grouped(const float* __restrict__ P, int per, int groups, int64_t rows, int cols,
-                                 int64_t group_rows, float* __restrict__ out, int64_t ldo) {
+__global__ void __launch_bounds__(32 * RED_WARPS) k_reduce_grouped(const float* __restrict__ P, int per, int groups,
+                                                                   int64_t rows, int cols, int64_t group_rows,
+                                                                   float* __restrict__ out, int64_t ldo) {
   const int64_t E = rows * cols;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = e / cols;
-    const int c = (int)(e % cols);
-    const int g = (int)(r / group_rows);
-    const float s = strided_sum(P + (int64_t)g * E + e, per, (int64_t)groups * E);
-    out[r * ldo + c] = s;
-  }
+  reduce_elements(PartialsGrouped{P, E, cols, group_rows}, per, (int64_t)groups * E, E, cols, out, ldo);
 }
 
 // ======================================================================
@@ -321,8 +345,8 @@ static int target_ctas() { return 4 * 152; }
 static void reduce_launch(const float* P, int S, int64_t rows, int cols, float* out, int64_t ldo,
                           cudaStream_t st) {
   int64_t E = rows * cols;
-  int blocks = (int)imin(ceil_div(E, 256), 1024);
-  k_reduce_partials<<<blocks, 256, 0, st>>>(P, S, rows, cols, out, ldo);
+  int blocks = (int)imin(ceil_div(E, 32), 4096);
+  k_reduce_partials<<<blocks, 32 * RED_WARPS, 0, st>>>(P, S, rows, cols, out, ldo);
   note_launch("reduce_partials");
 }
 
@@ -336,8 +360,8 @@ cudaError_t launch_reduce_partials_grouped(const float* P, int per, int groups, 
                                            int64_t group_rows, float* out, int64_t ldo, cudaStream_t st) {
   const int64_t E = rows * cols;
   note_launch("reduce_partials");
-  k_reduce_grouped<<<(int)imin(ceil_div(E, 256), 1024), 256, 0, st>>>(P, per, groups, rows, cols, group_rows, out,
-                                                                       ldo);
+  k_reduce_grouped<<<(int)imin(ceil_div(E, 32), 4096), 32 * RED_WARPS, 0, st>>>(P, per, groups, rows, cols,
+                                                                                group_rows, out, ldo);
   return cudaGetLastError();
 }
 
