@@ -43,7 +43,7 @@ LIBRARY_FAMILIES = ()
 # kernel family; an entry is removed when its kernel changes after the
 # capture.
 NCU_TRAFFIC = {
-    "proj_tc": 127119275.0,
+    "proj_tc": 128750677.0,
 }
 
 
