@@ -35,7 +35,8 @@ __global__ void __launch_bounds__(64) k_tn_partials(const TA* __restrict__ A, in
   float acc[4][4] = {};
   for (int64_t i0 = r0; i0 < r1; i0 += 32) {
     __syncthreads();
-#pragma unroll 4
+    // all sixteen loads of a thread in flight at once
+#pragma unroll
     for (int x = threadIdx.x; x < 32 * 32; x += 64) {
       const int r = x >> 5, c = x & 31;
       const int64_t i = i0 + r;
@@ -64,12 +65,20 @@ __global__ void __launch_bounds__(64) k_tn_partials(const TA* __restrict__ A, in
     }
 }
 
-// out[e] = sum_{c < nparts} P[c][e] (fixed order)
+// out[e] = sum_{c < nparts} P[c][e] (fixed order: four interleaved chains
+// over c mod 4, then ((0 + 1) + (2 + 3)))
 __global__ void k_sum_parts(const float* __restrict__ P, int nparts, int64_t E, float* __restrict__ out) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
-    float s = 0.f;
-    for (int c = 0; c < nparts; ++c) s += P[(int64_t)c * E + e];
-    out[e] = s;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    int c = 0;
+    for (; c + 4 <= nparts; c += 4) {
+      a0 += P[(int64_t)c * E + e];
+      a1 += P[(int64_t)(c + 1) * E + e];
+      a2 += P[(int64_t)(c + 2) * E + e];
+      a3 += P[(int64_t)(c + 3) * E + e];
+    }
+    for (; c < nparts; ++c) a0 += P[(int64_t)c * E + e];
+    out[e] = (a0 + a1) + (a2 + a3);
   }
 }
 
@@ -456,9 +465,10 @@ cudaError_t launch_eig_top(const float* H, int64_t ldh, int k, int r, float* V, 
   return cudaGetLastError();
 }
 
-// Row ranges of the partial products: about 96 rows each, at most 16.
+// Row ranges of the partial products: about 32 rows each (one shared-memory
+// tile per CTA up to m = 2048), at most 64.
 static int rows_split(int64_t m, int64_t* rows_per_split) {
-  const int64_t splits = imax(1, imin(ceil_div(m, 96), 16));
+  const int64_t splits = imax(1, imin(ceil_div(m, 32), 64));
   *rows_per_split = ceil_div(m, splits);
   return (int)ceil_div(m, *rows_per_split);
 }
