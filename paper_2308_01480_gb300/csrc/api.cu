@@ -632,9 +632,13 @@ tt_status enqueue_problem(const Plan& P, const void* tensor, const float* const*
   const char* Rlast = ws + (((d - 2) % 2 == 0) ? P.off_R0 : P.off_R1);
   const int64_t wd = (P.world > 1) ? P.slab_w : P.dims[d - 1];   // this rank's slab of the last mode
   const int64_t last = P.rr[d - 1] * wd;
-  TTR_CUDA(ttr::launch_last_core(Rlast, P.remainder, last, cores_out[d - 1], status, st));
-  for (int k = 0; k < d; ++k)
-    TTR_CUDA(ttr::launch_check_finite(cores_out[k], P.rr[k] * (k == d - 1 ? wd : P.dims[k]) * P.rr[k + 1], status, st));
+  const float* first[ttr::kFinaliseMaxCores];
+  int64_t counts[ttr::kFinaliseMaxCores];
+  for (int k = 0; k < d - 1; ++k) {
+    first[k] = cores_out[k];
+    counts[k] = P.rr[k] * P.dims[k] * P.rr[k + 1];
+  }
+  TTR_CUDA(ttr::launch_finalise(Rlast, P.remainder, last, cores_out[d - 1], first, counts, d - 1, status, st));
   return TT_OK;
 }
 

@@ -169,8 +169,13 @@ template <typename T>
 cudaError_t launch_colgram(const T* C, int64_t m, int n, int r, float* scratch, float* Y, cudaStream_t st);
 cudaError_t launch_rayleigh_ritz(const float* Q, const float* W, int64_t ld, int64_t m, int k, int r,
                                  int identity_q, float* scratch, float* U, float* core, cudaStream_t st);
-cudaError_t launch_last_core(const void* R, int dtype, int64_t count, float* core, int* status, cudaStream_t st);
-cudaError_t launch_check_finite(const float* p, int64_t count, int* status, cudaStream_t st);
+// The last core (the last remainder of dtype TT_F32/TT_BF16, last_count
+// entries) and a non-finite check of it and of cores[0..ncores) (counts[k]
+// entries each), one launch; ncores <= kFinaliseMaxCores.
+constexpr int kFinaliseMaxCores = 63;
+cudaError_t launch_finalise(const void* R, int dtype, int64_t last_count, float* last_core,
+                            const float* const* cores, const int64_t* counts, int ncores, int* status,
+                            cudaStream_t st);
 
 // ---- inputs (misc.cu)
 cudaError_t launch_omega(uint64_t seed, int mode, int64_t n, int b, void* out, int dtype, int64_t si,

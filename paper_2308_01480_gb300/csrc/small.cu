@@ -323,17 +323,35 @@ k_rayleigh_ritz(const float* __restrict__ Q, const float* __restrict__ W, int64_
 }
 
 // ------------------------------------------------------------ last core and checks
-template <typename T>
-__global__ void k_last_core(const T* __restrict__ R, int64_t count, float* __restrict__ core) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
-    core[e] = ld_elem(R, e);
-}
+// Alg. 3 step 12 and the final check in one launch.  Row y = 0 of the grid
+// writes the last core (the last remainder converted to FP32) and checks the
+// values it writes; row y = k + 1 checks core k.  A non-finite core entry is
+// only possible from non-finite input, since every intermediate is a bounded
+// combination of input values.
+struct FinaliseArgs {
+  float* last_core;
+  int64_t last_count;
+  int* status;
+  const float* core[kFinaliseMaxCores];
+  int64_t count[kFinaliseMaxCores];
+};
 
-// Flags a non-finite core entry (only possible from non-finite input, since
-// every intermediate is a bounded combination of input values).
-__global__ void k_check_finite(const float* __restrict__ p, int64_t count, int* status) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
-    if (!isfinite(p[e])) { set_status(status, DEV_NONFINITE); return; }
+template <typename T>
+__global__ void k_finalise(const T* __restrict__ R, const FinaliseArgs a) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  bool bad = false;
+  if (blockIdx.y == 0) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < a.last_count; e += stride) {
+      const float v = ld_elem(R, e);
+      a.last_core[e] = v;
+      bad |= !isfinite(v);
+    }
+  } else {
+    const float* __restrict__ p = a.core[blockIdx.y - 1];
+    const int64_t cnt = a.count[blockIdx.y - 1];
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += stride) bad |= !isfinite(p[e]);
+  }
+  if (bad) set_status(a.status, DEV_NONFINITE);
 }
 
 // ------------------------------------------------------------ launchers
@@ -371,20 +389,26 @@ cudaError_t launch_rayleigh_ritz(const float* Q, const float* W, int64_t ld, int
   return cudaGetLastError();
 }
 
-cudaError_t launch_last_core(const void* R, int dtype, int64_t count, float* core, int* status, cudaStream_t st) {
-  int blocks = (int)imin(ceil_div(count, 256), 1024);
-  note_launch("last_core");
+cudaError_t launch_finalise(const void* R, int dtype, int64_t last_count, float* last_core,
+                            const float* const* cores, const int64_t* counts, int ncores, int* status,
+                            cudaStream_t st) {
+  if (ncores < 0 || ncores > kFinaliseMaxCores || last_count < 0) return cudaErrorInvalidValue;
+  FinaliseArgs a;
+  a.last_core = last_core;
+  a.last_count = last_count;
+  a.status = status;
+  int64_t most = last_count;
+  for (int k = 0; k < kFinaliseMaxCores; ++k) {
+    a.core[k] = k < ncores ? cores[k] : nullptr;
+    a.count[k] = k < ncores ? counts[k] : 0;
+    most = imax(most, a.count[k]);
+  }
+  const dim3 grid((unsigned)imax(1, imin(ceil_div(most, 256), 1024)), (unsigned)(ncores + 1));
+  note_launch("finalise");
   if (dtype == TT_BF16)
-    k_last_core<__nv_bfloat16><<<blocks, 256, 0, st>>>((const __nv_bfloat16*)R, count, core);
+    k_finalise<__nv_bfloat16><<<grid, 256, 0, st>>>((const __nv_bfloat16*)R, a);
   else
-    k_last_core<float><<<blocks, 256, 0, st>>>((const float*)R, count, core);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_check_finite(const float* p, int64_t count, int* status, cudaStream_t st) {
-  int blocks = (int)imin(ceil_div(count, 256), 1024);
-  note_launch("check_finite");
-  k_check_finite<<<blocks, 256, 0, st>>>(p, count, status);
+    k_finalise<float><<<grid, 256, 0, st>>>((const float*)R, a);
   return cudaGetLastError();
 }
 

@@ -38,16 +38,31 @@ __global__ void __launch_bounds__(256) k_proj(const TIn* __restrict__ C, int64_t
   for (int v = 0; v < VB; ++v)
 #pragma unroll
     for (int u = 0; u < 4; ++u) acc[v][u] = 0.f;
+  constexpr int NC = RC * TN / 256, NX = RC * 16 * VB / 256;   // tile entries per thread
   for (int64_t i0 = rbeg; i0 < rend; i0 += RC) {
-    for (int e = threadIdx.x; e < RC * TN; e += 256) {
-      int r = e / TN, c = e % TN;
-      int64_t gi = i0 + r, gc = col0 + c;
-      Cs[r][c] = (gi < rend && gc < n) ? ld_elem(C, gi * n + gc) : 0.f;
+    // every load of the chunk in flight before the first store
+    float cl[NC], xl[NX];
+#pragma unroll
+    for (int u = 0; u < NC; ++u) {
+      const int e = threadIdx.x + 256 * u, r = e / TN, c = e % TN;
+      const int64_t gi = i0 + r, gc = col0 + c;
+      cl[u] = (gi < rend && gc < n) ? ld_elem(C, gi * n + gc) : 0.f;
     }
-    for (int e = threadIdx.x; e < RC * 16 * VB; e += 256) {
-      int r = e / (16 * VB), c = e % (16 * VB);
-      int64_t gi = i0 + r;
-      Xs[r][c] = (gi < rend && c < b) ? X[gi * ldx + c] : 0.f;
+#pragma unroll
+    for (int u = 0; u < NX; ++u) {
+      const int e = threadIdx.x + 256 * u, r = e / (16 * VB), c = e % (16 * VB);
+      const int64_t gi = i0 + r;
+      xl[u] = (gi < rend && c < b) ? X[gi * ldx + c] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < NC; ++u) {
+      const int e = threadIdx.x + 256 * u;
+      Cs[e / TN][e % TN] = cl[u];
+    }
+#pragma unroll
+    for (int u = 0; u < NX; ++u) {
+      const int e = threadIdx.x + 256 * u;
+      Xs[e / (16 * VB)][e % (16 * VB)] = xl[u];
     }
     __syncthreads();
 #pragma unroll 8
@@ -377,9 +392,10 @@ __global__ void k_sum_splits(const float* __restrict__ P, int splits, int b, int
   }
 }
 
+// Row splits of the tall-thin form: one 32-row chunk per CTA (at most 64).
 int64_t simt_proj_splits(int64_t m, int64_t n) {
   if (n > 512 || m < 256) return 1;
-  return imin(ceil_div(m, 64), 64);
+  return imin(ceil_div(m, 32), 64);
 }
 
 template <typename TIn, typename TOut>
