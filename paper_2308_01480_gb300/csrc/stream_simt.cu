@@ -386,8 +386,17 @@ __global__ void k_sum_splits(const float* __restrict__ P, int splits, int b, int
                              int64_t lds) {
   const int64_t E = (int64_t)b * n;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+    // eight loads in flight, added in split order
     float acc = 0.f;
-    for (int y = 0; y < splits; ++y) acc += P[(int64_t)y * E + e];
+    int y = 0;
+    for (; y + 8 <= splits; y += 8) {
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = P[(int64_t)(y + u) * E + e];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc += v[u];
+    }
+    for (; y < splits; ++y) acc += P[(int64_t)y * E + e];
     st_elem(S, (e / n) * lds + e % n, acc);
   }
 }
