@@ -422,22 +422,46 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eig_top(const float* __restrict
 }
 
 // U (m x r) = Q (m x k, ld ldq) V (k x r); also written to core (same layout).
+// V and the CTA's rows of Q are staged in shared memory with sixteen loads
+// of each thread in flight at a time; each U entry is then one FMA chain over
+// t = 0..k-1.
 template <typename TQ>
 __global__ void __launch_bounds__(256) k_apply_basis(const TQ* __restrict__ Q, int64_t ldq, int64_t m, int k,
                                                      const float* __restrict__ V, int r, float* __restrict__ U,
                                                      float* __restrict__ core, int64_t rows_per_cta) {
+  constexpr int NT = 256, NL = 16;
   extern __shared__ float sm[];
-  float* Vs = sm;   // [k][r]
-  for (int x = threadIdx.x; x < k * r; x += blockDim.x) Vs[x] = V[x];
-  __syncthreads();
+  float* Vs = sm;                     // [k][r]
+  float* Qs = sm + (size_t)k * r;     // [rows][k]
   const int64_t r0 = (int64_t)blockIdx.x * rows_per_cta;
   const int64_t r1 = imin(m, r0 + rows_per_cta);
-  for (int64_t x = threadIdx.x; x < (r1 - r0) * r; x += blockDim.x) {
+  const int nv = k * r, nq = (int)(r1 - r0) * k;
+  for (int base = threadIdx.x; base < nv; base += NT * NL) {
+    float v[NL];
+#pragma unroll
+    for (int u = 0; u < NL; ++u) v[u] = (base + NT * u < nv) ? V[base + NT * u] : 0.f;
+#pragma unroll
+    for (int u = 0; u < NL; ++u)
+      if (base + NT * u < nv) Vs[base + NT * u] = v[u];
+  }
+  for (int base = threadIdx.x; base < nq; base += NT * NL) {
+    float v[NL];
+#pragma unroll
+    for (int u = 0; u < NL; ++u) {
+      const int x = base + NT * u;
+      v[u] = (x < nq) ? ld_elem(Q + (r0 + x / k) * ldq, x % k) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < NL; ++u)
+      if (base + NT * u < nq) Qs[base + NT * u] = v[u];
+  }
+  __syncthreads();
+  for (int64_t x = threadIdx.x; x < (r1 - r0) * r; x += NT) {
     const int64_t i = r0 + x / r;
     const int j = (int)(x % r);
-    const TQ* qi = Q + i * ldq;
+    const float* qi = Qs + (x / r) * k;
     float s = 0.f;
-    for (int t = 0; t < k; ++t) s = fmaf(ld_elem(qi, t), Vs[t * r + j], s);
+    for (int t = 0; t < k; ++t) s = fmaf(qi[t], Vs[t * r + j], s);
     U[i * r + j] = s;
     if (core) core[i * r + j] = s;
   }
@@ -500,7 +524,7 @@ static cudaError_t apply_basis_t(const TQ* Q, int64_t ldq, int64_t m, int k, con
                                  float* core, cudaStream_t st) {
   int64_t rpc = 8;
   const int ctas = (int)ceil_div(m, rpc);
-  const size_t smem = sizeof(float) * (size_t)k * r;
+  const size_t smem = sizeof(float) * ((size_t)k * r + (size_t)rpc * k);
   raise_smem_limit(k_apply_basis<TQ>);
   ProfScope prof("apply_basis", st, 0, 2.0 * m * k * r);
   note_launch("apply_basis");
