@@ -115,3 +115,22 @@ def test_literal_plan_counts_powers():
         modes = tt.plan_modes(dims, ranks, 10, q, tt.options(storage=tt.TT_BF16, method=method, paper_literal=True))
         assert all(e["powers"] == want and e["basis_cols"] == e["r_out"] for e in modes)
         assert all(e["route"] in ("krylov", "gram_power") for e in modes)
+
+
+def test_bench_algorithmic_bytes_per_decomposition():
+    """The roofline numerator bench.py reports: per mode, (q_eff + 2) reads of
+    the unfolding (sketch, q_eff Krylov steps, projection), one read of Omega
+    and one write of the remainder, q_eff capped by the Krylov dimension.
+    For the 40^5 workload by hand (entries): mode 1 40 x 2,560,000, q_eff 1:
+    3 * 102.4M + 30 * 2.56M + 20 * 2.56M = 435.2M; mode 2 800 x 64,000,
+    q_eff 4: 6 * 51.2M + 50 * 64,000 = 310.4M; mode 3 800 x 1,600: 7.76M;
+    mode 4 800 x 40, q_eff 1: 98,000; in all 753.458M entries, 1506.916 MB
+    in BF16.  The other two single-GPU workloads likewise."""
+    import bench
+    from paper_2308_01480_gb300 import workloads as W
+    want = {(3, 2): 1506.916e6, (3, 4): 3013.832e6, (4, 2): 1573.40096e6, (4, 4): 3146.80192e6,
+            (2, 4): 861.543552e6, (2, 2): 430.771776e6}
+    for (cfg, e), nbytes in want.items():
+        code = tt.TT_BF16 if e == 2 else tt.TT_F32
+        got = bench.algorithmic_bytes(tt, W.CONFIGS[cfg], tt.options(storage=code, remainder=code), e)
+        assert got == pytest.approx(nbytes, rel=1e-12), (cfg, e, got)
