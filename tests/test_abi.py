@@ -248,3 +248,23 @@ def test_struct_layouts_match_header(tmp_path):
             assert (field.offset, field.size) == (int(off), int(size)), (cname, fname)
         seen += 1
     assert seen == sum(len(c._fields_) + 1 for c in mirrors.values())
+
+
+def test_order_limit_and_noalloc_arguments_rejected_on_host(L):
+    """The order limit (d <= 64: the final kernel checks the other d - 1
+    cores in one launch) and the allocation-free Gram-apply's argument and
+    size checks, all taken before any CUDA call."""
+    nb = ctypes.c_size_t()
+    for d, want in ((64, N.TT_OK), (65, N.TT_EINVAL)):
+        dims, ranks = [1] * (d - 2) + [3, 4], [1] * (d - 1)
+        assert L.tt_rbki_workspace_size(N.i64_array(dims), d, N.i64_array(ranks), 1, 1, None,
+                                        ctypes.byref(nb)) == want
+    p = ctypes.c_void_p(256)
+    cases = [((None, N.TT_F32, 10, 64, 8), N.TT_EINVAL, b"NULL"),
+             ((p, 7, 10, 64, 8), N.TT_EINVAL, b"c_dtype"),
+             ((p, N.TT_F32, 0, 64, 8), N.TT_EINVAL, b">= 1"),
+             ((p, N.TT_BF16, 257, 64, 8), N.TT_EUNSUPPORTED, b"m <= 256"),
+             ((p, N.TT_BF16, 10, 64, 49), N.TT_EUNSUPPORTED, b"b <= 48")]
+    for (C, dt, m, n, b), want, msg in cases:
+        assert L.tt_gram_apply_noalloc(C, dt, m, n, b, p, p, None) == want
+        assert msg in L.tt_rbki_last_error()
