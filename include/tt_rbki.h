@@ -138,11 +138,12 @@ TT_API tt_status tt_rbki_default_options(tt_options* opts);
 
 /*
  * Rank clamp and core sizes (Def. 2; Alg. 3 input).
- *   dims       host, d mode sizes I_1..I_d, each >= 1; d >= 2.
+ *   dims       host, d mode sizes I_1..I_d, each >= 1; 2 <= d <= 64.
  *   ranks      host, d-1 target ranks r_1..r_{d-1}, each >= 1.
  *   ranks_out  host, d+1 entries: r_0' = 1, r_1'..r_{d-1}', r_d' = 1.
  *   core_elems host, d entries: r_{k-1}' I_k r_k' (may be NULL).
- * Errors: TT_EINVAL on d < 2, a dimension or rank < 1, or overflow.
+ * Errors: TT_EINVAL on d outside [2, 64], a dimension or rank < 1, or
+ *         overflow.
  */
 TT_API tt_status tt_rbki_core_sizes(const int64_t* dims, int d, const int64_t* ranks,
                              int64_t* ranks_out, int64_t* core_elems);
@@ -263,7 +264,7 @@ typedef struct {
                                 tt_rbki_decompose                              */
   int64_t* ranks_out;        /* host, d+1 entries, or NULL                     */
   uint64_t omega_seed;       /* seed of this problem's Omega_k                 */
-  int32_t d;                 /* order >= 2                                     */
+  int32_t d;                 /* order, 2..64                                   */
   int32_t oversample;        /* p >= 0                                         */
   int32_t q;                 /* Krylov depth >= 0                              */
   int32_t reserved;          /* must be zero                                   */
