@@ -231,6 +231,25 @@ def test_tt_full_matches_generator_contraction():
     assert abs(oracle.tt_distance(cores, cores2) - brute2) < 1e-14
 
 
+@pytest.mark.parametrize("dims,ranks,want", [
+    ((1, 5, 6, 4), (3, 3, 2), [1, 1, 3, 2, 1]),    # first mode of size one
+    ((5, 1, 6, 4), (2, 2, 3), [1, 2, 2, 3, 1]),    # a middle mode of size one
+    ((4, 5, 1), (3, 1), [1, 3, 1, 1]),             # last mode of size one
+    ((7, 8, 9), (1, 1), [1, 1, 1, 1]),             # rank one
+])
+def test_exact_recovery_degenerate_shapes(dims, ranks, want):
+    """Modes of size one and rank one.  Def. 2's clamp bounds each bond by
+    the product of the modes on either side (r_1' = 1 next to a first mode
+    of size one, whatever r_1 asks for).  A tensor of that TT rank is
+    recovered exactly, with no oversampling and no power as well as with
+    both, and every core has the clamped shape."""
+    A = rand_tt(dims, want[1:-1], 11)
+    for p, q in ((0, 0), (2, 1)):
+        cores = oracle.tt_rbki(A, ranks, p, q, seed=4)
+        assert [c.shape for c in cores] == [(want[k], dims[k], want[k + 1]) for k in range(len(dims))]
+        assert oracle.tt_error(A, cores) < 1e-12
+
+
 def test_clamp_ranks():
     assert oracle.clamp_ranks((16, 16, 16, 16), (4, 4, 4)) == [1, 4, 4, 4, 1]
     assert oracle.clamp_ranks((3, 5, 4), (10, 10)) == [1, 3, 4, 1]
