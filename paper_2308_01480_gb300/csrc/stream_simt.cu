@@ -401,7 +401,8 @@ __global__ void k_sum_splits(const float* __restrict__ P, int splits, int b, int
   }
 }
 
-// Row splits of the tall-thin form: one 32-row chunk per CTA (at most 64).
+// Row splits of the tall-thin form: 32 rows (one tile chunk) per CTA, at most
+// 64 splits.
 int64_t simt_proj_splits(int64_t m, int64_t n) {
   if (n > 512 || m < 256) return 1;
   return imin(ceil_div(m, 32), 64);
