@@ -2,8 +2,8 @@
 
 TEST INFRASTRUCTURE ONLY.  This package is a plain, slow, obviously correct
 restatement of the paper's algorithms in float64 numpy.  Only ``tests/``,
-``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may import
-it.  It shares no code, tables, constants or helpers with the CUDA library in
+``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg and reference
+arm may import it.  It shares no code, tables, constants or helpers with the CUDA library in
 ``paper_2308_01480_gb300/``; neither imports the other.
 
 Modules

@@ -1,8 +1,9 @@
 """Plain float64 restatement of TT-SVD (Alg. 1), TT-rBKI (Alg. 3) and
 TT-rSI (Alg. 4); TT-rSVD (Alg. 2) is TT-rBKI with q = 0.
 
-TEST INFRASTRUCTURE ONLY: used by tests/, __graft_entry__.smoke() and the
-CPU-baseline leg of bench.py.  Never imported by the CUDA library.
+TEST INFRASTRUCTURE ONLY: used by tests/, __graft_entry__.smoke() and
+bench.py's CPU-baseline leg and reference arm (both time it on the host
+cores).  Never imported by the CUDA library.
 
 Notation follows the paper: a tensor A of order d with mode sizes I_1..I_d,
 TT ranks r_0 = r_d = 1 (Def. 2).  Tensors are row-major with i_1 the slowest
